@@ -1,0 +1,129 @@
+"""Dense brute-force MSFV forward map for tiny meshes, differentiable by complex step.
+
+TEST INFRASTRUCTURE ONLY (pins the oracle; shares no code with it).
+
+It works from the definitions with a different organisation than the oracle:
+instead of one local solve per entity it forms, for each level k = 1..d, the
+global "tangential" operator of all cells with exactly k off-vertex axes and
+solves one dense system for all basis functions at once (Sec. 3.2,
+Eq. multiscaleBasis_step3 -- the block-diagonal structure over entities is not
+used).  Then P, A_c = R A P, the pinned reduced solve and the data follow densely
+(Sec. 3.1, Eq. fwdProbRed).  All arithmetic is written so that a complex model
+m + i*eps*v flows through analytically (exp, harmonic means and dense solves are
+analytic), which gives J v = Im(d(m + i eps v)) / eps to machine precision with no
+derivative code at all.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _coords(n):
+    N = int(np.prod(n))
+    out = np.zeros((N, len(n)), dtype=np.int64)
+    rem = np.arange(N)
+    for a, v in enumerate(n):
+        out[:, a] = rem % v
+        rem //= v
+    return out
+
+
+def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec):
+    """Predicted data (Ns, Nr) for model m (real or complex), dense linear algebra."""
+    n = tuple(int(v) for v in n)
+    d = len(n)
+    N = int(np.prod(n))
+    X = _coords(n)
+    stride = [int(np.prod(n[:a])) for a in range(d)]
+    sig = np.exp(m)
+    dt = np.result_type(sig.dtype, np.float64)
+    # fine operator, face by face
+    A = np.zeros((N, N), dtype=dt)
+    Tface = {}
+    for a in range(d):
+        area = 1.0
+        for b in range(d):
+            if b != a:
+                area *= 1.0 / n[b]
+        geo = area * n[a]
+        for x in range(N):
+            if X[x, a] + 1 < n[a]:
+                y = x + stride[a]
+                t = geo * 2.0 * sig[x] * sig[y] / (sig[x] + sig[y])
+                Tface[(x, y)] = t
+                Tface[(y, x)] = t
+                A[x, x] += t
+                A[y, y] += t
+                A[x, y] -= t
+                A[y, x] -= t
+    half = c // 2
+    isvert = (X - half) % c == 0          # per axis: coordinate is a vertex coordinate
+    level = (~isvert).sum(axis=1)         # number of off-vertex axes
+    nc = tuple(v // c for v in n)
+    Nc = int(np.prod(nc))
+    cstride = [int(np.prod(nc[:a])) for a in range(d)]
+    Phi = np.zeros((N, Nc), dtype=dt)
+    for x in np.nonzero(level == 0)[0]:
+        J = sum(((X[x, a] - half) // c) * cstride[a] for a in range(d))
+        Phi[x, J] = 1.0
+    for k in range(1, d + 1):
+        rows = np.nonzero(level == k)[0]
+        if len(rows) == 0:
+            continue
+        M = np.zeros((len(rows), N), dtype=dt)
+        for r, x in enumerate(rows):
+            for a in range(d):
+                if isvert[x, a]:
+                    continue                  # only fluxes along off-vertex axes
+                for s in (-1, 1):
+                    ca = X[x, a] + s
+                    if 0 <= ca < n[a]:
+                        y = x + s * stride[a]
+                        t = Tface[(x, y)]
+                        M[r, x] += t
+                        M[r, y] -= t
+        known = np.nonzero(level < k)[0]
+        rhs = -M[:, known] @ Phi[known]
+        Phi[rows] = np.linalg.solve(M[:, rows], rhs)
+    # restriction, coarse operator, pinned solve
+    R = np.zeros((Nc, N))
+    for x in range(N):
+        I = sum((X[x, a] // c) * cstride[a] for a in range(d))
+        R[I, x] = 1.0
+    Ac = R @ A @ Phi
+    Ns = len(src_pos)
+    out = np.zeros((Ns, len(rec)), dtype=dt)
+    for j in range(Ns):
+        q = np.zeros(N)
+        q[src_pos[j]] += src_amp[j]
+        q[src_neg[j]] -= src_amp[j]
+        b = R @ q
+        t = np.zeros(Nc, dtype=dt)
+        t[1:] = np.linalg.solve(Ac[1:, 1:], b[1:])
+        u = Phi @ t
+        out[j] = u[np.asarray(rec)]
+    return out, Phi, Ac
+
+
+def data(m, prob):
+    d, _, _ = forward_dense(m, prob.n, prob.coarsen, prob.src_pos, prob.src_neg,
+                            prob.src_amp, prob.rec_cell)
+    return d
+
+
+def jvec_complex_step(m, prob, v, eps=1e-30):
+    """J v by complex step: Im(d(m + i eps v)) / eps."""
+    mc = np.asarray(m, dtype=np.complex128) + 1j * eps * np.asarray(v)
+    return np.imag(data(mc, prob)) / eps
+
+
+def misfit_gradient_complex_step(m, prob, d_obs, eps=1e-30):
+    """Gradient of 1/2 ||d(m) - d_obs||^2, one complex-step evaluation per cell."""
+    N = len(m)
+    r = np.real(data(np.asarray(m, dtype=np.complex128), prob)) - d_obs
+    g = np.zeros(N)
+    for k in range(N):
+        e = np.zeros(N)
+        e[k] = 1.0
+        g[k] = np.sum(r * jvec_complex_step(m, prob, e, eps))
+    return g
