@@ -1,0 +1,157 @@
+/*
+ * msfv.h -- C ABI of the GB300 MSFV library: the parameter-dependent multiscale
+ * finite-volume (MSFV) reduced solve of the DC-resistivity problem and its
+ * derivative with respect to the log-conductivity (arXiv 1707.07598).
+ *
+ * Problem (Sec. 2.1, Eq. DCR; discrete form Sec. 2.2, Eq. forwardProbFine):
+ *   -div(sigma grad u_j) = q_j on the unit square / cube, no-flux boundary,
+ *   sigma = exp(m) on cells, cell-centred finite volumes with harmonic face
+ *   averages; data D_ij = u_j(receiver cell i).
+ * Reduced model (Sec. 3.1, Eq. fwdProbRed / reducedPDE; basis of Sec. 3.2,
+ * Eq. multiscaleBasis_step3): u_j = P t_j, A_c t_j = R q_j, A_c = R A P, with
+ * P the model-dependent MSFV prolongation built from independent local solves
+ * on the dual-coarse grid and R the finite-volume restriction.
+ * Derivative (Sec. 4.3, Eq. sensred; local derivative of the basis, Sec. 4.5,
+ * Eq. reducedDiscreteMSBasisPDE): J = Pr^T ( Y(t) + P dt/dm ).
+ *
+ * Conventions shared by every entry point:
+ *  - Cells are numbered idx = i0 + n0*(i1 + n1*i2) (axis 0 fastest); the top
+ *    layer of a 3D mesh is i2 = n2-1.  Coarse cells are numbered the same way on
+ *    the (n_a / coarsen) grid.
+ *  - Every array argument named *_dev is DEVICE memory (GB300 global memory)
+ *    owned by the caller; every *_host argument is ordinary host memory owned by
+ *    the caller.  The library never frees caller memory.
+ *  - Per-source arrays are source-major: element (j, i) of an Ns x Nr array is
+ *    at j*Nr + i.
+ *  - All work is enqueued on the session's CUDA stream (cudaStream_t passed as
+ *    void*; NULL = legacy default stream).  Calls return once the work is
+ *    enqueued unless stated otherwise; results are valid after the stream is
+ *    synchronised.
+ *  - Every call returns an msfv status (MSFV_OK = 0); on failure
+ *    msfv_last_error(session) (or msfv_last_error(NULL) when no session exists)
+ *    gives a one-line message.  No call throws and there is no CPU fallback:
+ *    without a usable GPU the calls fail with MSFV_ERR_CUDA.
+ *  - All arithmetic is IEEE FP64.
+ */
+#ifndef MSFV_H
+#define MSFV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define MSFV_OK            0
+#define MSFV_ERR_ARG       1  /* invalid descriptor or argument (nothing enqueued)      */
+#define MSFV_ERR_OOM       2  /* device allocation failed or HBM budget exceeded        */
+#define MSFV_ERR_NUMERIC   3  /* non-positive local pivot, singular or unconverged coarse solve */
+#define MSFV_ERR_TIMEOUT   4  /* a bounded device-side wait expired                    */
+#define MSFV_ERR_CUDA      5  /* a CUDA runtime call failed                             */
+#define MSFV_ERR_STATE     6  /* call out of order (e.g. adjoint before forward)        */
+
+/* Problem description (Sec. 2.2: mesh, sources Q, receivers P of Eq. forwardProbFine).
+ * The host arrays are copied by msfv_setup and may be freed afterwards. */
+typedef struct msfv_desc {
+  int dim;                  /* 2 or 3                                                  */
+  int n[3];                 /* cells per axis (n[2] ignored when dim == 2)             */
+  int coarsen;              /* coarsening factor c >= 1; must divide every n[a];
+                               at least 2 coarse cells in total; c <= 12 in 3D,
+                               c <= 32 in 2D (local problems held on chip)             */
+  int n_src;                /* Ns >= 1 dipole sources                                  */
+  const int64_t* src_pos;   /* host, Ns cells receiving +src_amp[j]                    */
+  const int64_t* src_neg;   /* host, Ns cells receiving -src_amp[j] (!= src_pos[j])    */
+  const double*  src_amp;   /* host, Ns amplitudes (NULL = all 1.0)                    */
+  int n_rec;                /* Nr >= 1 point receivers                                 */
+  const int64_t* rec_cell;  /* host, Nr cells; receiver i reads u_j at rec_cell[i];
+                               repeated cells are allowed                              */
+  int factor_mode;          /* 0 auto, 1 store local factors (needed by adjoint / jvec
+                               / jtvec), 2 recompute (not yet supported: MSFV_ERR_ARG) */
+  size_t hbm_budget_bytes;  /* 0 = no limit; else setup fails with MSFV_ERR_OOM when
+                               the session workspace would exceed it                   */
+} msfv_desc_t;
+
+typedef struct msfv_session msfv_session_t;
+
+/* Validate the descriptor, build the dual-coarse-grid work lists (Sec. 3.2 step 1)
+ * and allocate the session workspace on the current CUDA device.  stream is a
+ * cudaStream_t (void*).  On success *out receives the session; on failure *out is
+ * NULL and the status says why.  Blocking (allocations and small uploads). */
+int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t** out);
+
+/* Steps (a)-(e): sigma = exp(m), harmonic face transmissibilities, the local basis
+ * solves (edges, faces, dual-cell interiors; Sec. 3.2), P, A_c = R A P, the pinned
+ * reduced solve A_c t_j = R q_j (coarse unknown 0 fixed to zero, Sec. 2.2 gauge),
+ * and the predicted data d_pred[j*Nr+i] = u_j(rec_cell[i]).
+ *   m_dev       N doubles, log-conductivity per cell (read only)
+ *   d_pred_dev  Ns*Nr doubles (written)
+ *   u_dev       NULL, or Ns*N doubles receiving the fields u_j = P t_j
+ * The session keeps P, the local factors and t for later derivative calls. */
+int msfv_forward(msfv_session_t* s, const double* m_dev, double* d_pred_dev, double* u_dev);
+
+/* Misfit phi = 1/2 ||d_pred - d_obs||_F^2 and its gradient J^T (d_pred - d_obs)
+ * (Sec. 4.1) for the m of the last msfv_forward.
+ *   d_obs_dev   Ns*Nr doubles (read only)
+ *   grad_dev    N doubles (written)
+ *   phi_host    NULL, or a host double receiving phi (this synchronises the stream)
+ * MSFV_ERR_STATE if no forward has been run. */
+int msfv_adjoint(msfv_session_t* s, const double* d_obs_dev, double* grad_dev, double* phi_host);
+
+/* J v (Sec. 4.3, Eq. sensred) at the m of the last forward: tangent of the
+ * predicted data along the model direction v.
+ *   v_dev   N doubles (read only);  jv_dev  Ns*Nr doubles (written). */
+int msfv_jvec(msfv_session_t* s, const double* v_dev, double* jv_dev);
+
+/* J^T w at the m of the last forward.
+ *   w_dev   Ns*Nr doubles (read only);  jtw_dev  N doubles (written). */
+int msfv_jtvec(msfv_session_t* s, const double* w_dev, double* jtw_dev);
+
+/* One forward + gradient solve through HOST buffers: copies m_host and d_obs_host
+ * to the device, runs msfv_forward and msfv_adjoint, copies d_pred and the gradient
+ * back, and synchronises the stream before returning.
+ *   m_host N doubles; d_obs_host Ns*Nr; d_pred_host Ns*Nr (written);
+ *   grad_host N (written); phi_host NULL or one double (written).
+ * Pinned (page-locked) host buffers give the fastest copies. */
+int msfv_solve_host(msfv_session_t* s, const double* m_host, const double* d_obs_host,
+                    double* d_pred_host, double* grad_host, double* phi_host);
+
+/* Free the session and its device workspace (synchronises its stream). NULL is ok. */
+int msfv_destroy(msfv_session_t* s);
+
+/* Last error message of the session (or of the last failed msfv_setup when s is
+ * NULL).  The string is owned by the library and valid until the next call. */
+const char* msfv_last_error(const msfv_session_t* s);
+
+/* ---- introspection (tracing, sizes, launch accounting) --------------------- */
+
+/* Change the stream later calls enqueue on. */
+int msfv_set_stream(msfv_session_t* s, void* stream);
+
+/* Sizes of the session: out[0]=N, out[1]=Nc, out[2]=Ns, out[3]=Nr, out[4]=number of
+ * local problems (edges + faces + dual-cell interiors), out[5]=workspace bytes,
+ * out[6]=stored-factor bytes, out[7]=coarse solver (0 banded LU, 1 multigrid GMRES). */
+int msfv_info(const msfv_session_t* s, int64_t* out, int n_out);
+
+/* Phase timers recorded with CUDA events on the session stream.  enable != 0 turns
+ * recording on.  msfv_phase_times writes up to n accumulated times (ms) per phase
+ * in the order of msfv_phase_name(k) and, when reset != 0, clears them; it
+ * synchronises the stream.  Returns the number of phases. */
+int msfv_profile(msfv_session_t* s, int enable);
+int msfv_phase_times(msfv_session_t* s, double* ms, int64_t* calls, int n, int reset);
+const char* msfv_phase_name(int k);
+
+/* Algorithmic FP64 FLOPs of one launch of the dual-cell interior basis kernel
+ * (banded LDL^T factor + 2^d forward/backward solves, counted per Sec. 3.2 local
+ * problem as n*b^2 + 2^d * 4*n*b summed over interiors). */
+double msfv_interior_flops(const msfv_session_t* s);
+
+/* Number of kernel launches this session has enqueued since setup. */
+int64_t msfv_launch_count(const msfv_session_t* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSFV_H */

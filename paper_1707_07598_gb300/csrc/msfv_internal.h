@@ -1,0 +1,142 @@
+// Internal types of the MSFV CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/msfv.h"
+
+namespace msfv {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxSlots = 8;      // 2^d corner slots per cell
+
+// Geometry of the fine mesh, the coarse mesh and the dual-coarse grid.
+// Coarse vertex K (per axis) sits on fine coordinate c*K + c/2 (centre of coarse
+// cell K).  Each fine cell x has, per axis a, lo_a(x) = floor((x_a - c/2) / c):
+// the coarse vertex at or below it.  Its 2^d corner slots s pick lo_a (bit a = 0)
+// or lo_a + 1 (bit a = 1); slot s of cell x holds phi_J(x) for the vertex J it
+// names, or 0 where that vertex does not exist or the axis is a vertex axis.
+struct Geom {
+  int d;
+  int n[3];
+  int c;
+  int half;
+  int nc[3];
+  long long N;
+  long long Nc;
+  long long st[3];    // fine strides
+  long long cst[3];   // coarse strides
+  int S;              // 2^d
+};
+
+// One local problem of the dual-coarse grid (a dual edge, dual face or dual-cell
+// interior) -- an "entity".  Its cells form a box org[a] .. org[a]+len[a]-1 (len 1
+// on vertex axes).  The tangential axes, sorted by increasing length, define the
+// local lexicographic order; the half bandwidth b is the product of all but the
+// longest tangential length.
+struct EntDesc {
+  int org[3];
+  int len[3];
+  int perm[3];        // tangential axes, fastest first; -1 when unused
+  int dim;            // number of tangential axes (1, 2 or 3)
+  int slots;          // bitmask of valid corner slots
+  int n;              // unknowns
+  int b;              // half bandwidth
+  long long fac;      // offset of the stored factor (doubles), n*(b+1) of them
+  int rec_off;        // receivers inside: [rec_off, rec_off + rec_cnt) in the rec lists
+  int rec_cnt;
+};
+
+// Launch-wide parameters of the local-problem kernels.
+struct LocalLaunch {
+  const EntDesc* ents;
+  int n_ents;
+  int nmax;           // largest n in this launch
+  int bmax;           // largest b in this launch
+  int npairs;         // bmax*(bmax+1)/2
+};
+
+struct DevGeom {
+  int d, c, half, S;
+  int n[3], nc[3];
+  long long N, Nc;
+  long long st[3], cst[3];
+};
+
+// Phase ids for the event timers.
+enum Phase {
+  PH_FACE_T = 0, PH_VERTEX, PH_EDGE, PH_FACE, PH_INTERIOR, PH_COARSE_ASM, PH_COARSE_SOLVE,
+  PH_PROLONG, PH_ADJ_SETUP, PH_ADJ_INTERIOR, PH_ADJ_FACE, PH_ADJ_EDGE, PH_GRAD, PH_TANGENT,
+  PH_COUNT
+};
+
+}  // namespace msfv
+
+// ---- launchers (defined in the kernel translation units) ----------------------
+namespace msfv {
+
+// T holds 2*d*N doubles: the d face arrays of T followed by the d arrays of
+// Dl = dT/dm_lower (dT/dm_upper = T - Dl); sig is N doubles of scratch.
+void launch_face_T(const DevGeom& g, const double* m, double* T, double* sig, cudaStream_t s);
+void launch_vertices(const DevGeom& g, double* Pw, cudaStream_t s);
+// Dynamic shared memory one launch of the local kernels needs (bytes).
+size_t local_smem_bytes(const DevGeom& g, const LocalLaunch& L);
+// Basis (forward) local solves; the factors are always stored (fac).
+void launch_local_forward(const DevGeom& g, const LocalLaunch& L, const double* T, double* Pw,
+                          double* fac, int* status, cudaStream_t s);
+// adjoint: seeds from receivers (ZT), Lambda and the MU of higher entities
+void launch_local_adjoint(const DevGeom& g, const LocalLaunch& L, const double* T,
+                          const double* Pw, const double* fac, const double* Lam,
+                          const int* rec_p, const int* rec_u, const double* ZT, double* MU,
+                          double* gTloc, cudaStream_t s);
+// tangent: dPw from dT (computed from v) and lower entities' dPw
+void launch_local_tangent(const DevGeom& g, const LocalLaunch& L, const double* T,
+                          const double* Dl, const double* v, const double* Pw,
+                          const double* fac, double* dPw, cudaStream_t s);
+
+void launch_coarse_assemble(const DevGeom& g, const double* T, const double* Pw,
+                            const double* Dl, const double* v, const double* dPw, double* Ac,
+                            int tangent, cudaStream_t s);
+void launch_prolong_receivers(const DevGeom& g, const double* Pw, const double* t, int Ns,
+                              const int64_t* rec, int Nr, double* d, cudaStream_t s);
+void launch_prolong_tangent(const DevGeom& g, const double* Pw, const double* dPw,
+                            const double* t, const double* dt, int Ns, const int64_t* rec,
+                            int Nr, double* jv, cudaStream_t s);
+void launch_prolong_full(const DevGeom& g, const double* Pw, const double* t, int Ns, double* u,
+                         cudaStream_t s);
+void launch_residual(const double* d_pred, const double* d_obs, int count, double* r,
+                     double* phi, cudaStream_t s);
+void launch_receiver_gather(const double* w, int Ns, int Nr, const int* ru_off, const int* ru_idx,
+                            int Nru, double* zc, cudaStream_t s);
+void launch_coarse_adjoint_rhs(const DevGeom& g, const double* Pw, const double* zc, int Ns,
+                               int Nru, const int* cj_off, const int* cj_u, const int* cj_s,
+                               const int64_t* ru_cell, double* b, cudaStream_t s);
+void launch_lambda(const DevGeom& g, const double* t, const double* lam, int Ns, double* Lam,
+                   cudaStream_t s);
+void launch_zt(const DevGeom& g, const double* t, const double* zc, int Ns, int Nru,
+               const int64_t* ru_cell, double* ZT, cudaStream_t s);
+void launch_grad(const DevGeom& g, const double* T, const double* Dl, const double* Pw,
+                 const double* Lam, const double* gTloc, double* grad, cudaStream_t s);
+void launch_coarse_tangent_rhs(const DevGeom& g, const double* dAc, const double* t, int Ns,
+                               double* rhs, cudaStream_t s);
+
+// Coarse solver: banded LU with partial pivoting of the pinned coarse matrix.
+struct BandLU {
+  long long n;      // Nc - 1
+  int kl, ku, ldab;
+  double* ab;       // ldab * n
+  int* piv;         // n
+  int* status;      // 1 int: 0 ok, 1 zero pivot
+};
+void launch_band_build(const DevGeom& g, const double* Ac, BandLU& B, cudaStream_t s);
+void launch_band_factor(BandLU& B, cudaStream_t s);
+// rhs: Ns vectors of length Nc (index 0 = pinned unknown); solved in place,
+// entry 0 of the result is set to 0.
+void launch_band_solve(const BandLU& B, double* rhs, int Ns, long long Nc, int transpose,
+                       cudaStream_t s);
+
+}  // namespace msfv

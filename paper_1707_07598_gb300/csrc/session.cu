@@ -1,0 +1,788 @@
+// Session object and C ABI of the MSFV library (declared in include/msfv.h).
+//
+// msfv_setup turns the problem statement of Sec. 2.2 (mesh, sources Q, receivers)
+// into device work lists: the dual-coarse-grid entities of Sec. 3.2 step 1 grouped
+// by dimension (edges, faces, interiors) and sorted by cost, the receiver maps the
+// adjoint needs, the coarse right-hand sides R q_j, and the workspace.  The other
+// entry points enqueue the kernels of k_local.cu and k_coarse.cu in the order the
+// paper's steps require: basis edges -> faces -> interiors (local solves of
+// Eq. multiscaleBasis_step3), coarse operator and pinned reduced solve
+// (Eq. fwdProbRed / reducedPDE), and for the derivative the reverse order
+// interiors -> faces -> edges (Sec. 4.5) around the adjoint coarse solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "msfv_internal.h"
+
+using namespace msfv;
+
+namespace {
+
+std::string g_setup_error;
+
+const char* kPhaseNames[PH_COUNT] = {
+    "face_T",        "vertices",       "basis_edges",  "basis_faces",   "basis_interiors",
+    "coarse_assemble", "coarse_solve", "prolong",      "adjoint_setup", "adjoint_interiors",
+    "adjoint_faces", "adjoint_edges",  "gradient",     "tangent"};
+
+struct Piece {
+  bool vertex;
+  int K;        // vertex index (vertex pieces)
+  int lo, hi;   // interval end vertices, -1 at the outer boundary
+  int start, len;
+};
+
+// Vertex coordinates c*K + c/2 and the open intervals between them (per axis).
+std::vector<Piece> axis_pieces(int n, int c) {
+  std::vector<Piece> out;
+  const int half = c / 2, nc = n / c;
+  if (half > 0) out.push_back({false, -1, -1, 0, 0, half});
+  for (int K = 0; K < nc; ++K) {
+    const int pos = c * K + half;
+    out.push_back({true, K, K, K, pos, 1});
+    if (K + 1 < nc) {
+      if (c - 1 > 0) out.push_back({false, -1, K, K + 1, pos + 1, c - 1});
+    } else {
+      const int right = n - 1 - pos;
+      if (right > 0) out.push_back({false, -1, K, -1, pos + 1, right});
+    }
+  }
+  return out;
+}
+
+}  // namespace
+
+struct msfv_session {
+  Geom geo{};
+  DevGeom dg{};
+  cudaStream_t stream = nullptr;
+  int Ns = 0, Nr = 0, Nru = 0;
+  std::vector<EntDesc> h_ents[4];
+  EntDesc* d_ents[4] = {nullptr, nullptr, nullptr, nullptr};
+  LocalLaunch launch[4]{};
+  // fine-grid buffers
+  double* T = nullptr;      // 2*d*N: T then Dl
+  double* sig = nullptr;    // N scratch
+  double* Pw = nullptr;     // N*S basis weights
+  double* X = nullptr;      // N*S: adjoint mu / tangent dP
+  double* gT = nullptr;     // d*N transmissibility gradient of the local problems
+  double* fac = nullptr;    // stored local factors
+  // coarse and per-source buffers
+  double *Ac = nullptr, *dAc = nullptr, *t = nullptr, *rq = nullptr, *lam = nullptr,
+         *dt = nullptr, *Lam = nullptr;
+  double *dpred = nullptr, *r = nullptr, *phi = nullptr, *zc = nullptr, *ZT = nullptr;
+  double *m_tmp = nullptr, *dobs_tmp = nullptr, *grad_tmp = nullptr, *dpred_tmp = nullptr;
+  int64_t *rec = nullptr, *ru_cell = nullptr;
+  int *ru_off = nullptr, *ru_idx = nullptr, *cj_off = nullptr, *cj_u = nullptr, *cj_s = nullptr;
+  int *rec_p = nullptr, *rec_u = nullptr;
+  int* status = nullptr;
+  BandLU band{};
+  bool have_forward = false;
+  std::string err;
+  // tracing
+  bool prof = false;
+  struct Ev {
+    int ph;
+    cudaEvent_t a, b;
+  };
+  std::vector<Ev> pending;
+  double ph_ms[PH_COUNT] = {0};
+  long long ph_calls[PH_COUNT] = {0};
+  long long launches = 0;
+  size_t ws_bytes = 0, fac_bytes = 0;
+  double int_flops = 0.0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(msfv_session* s, int code, const std::string& msg) {
+  if (s)
+    s->err = msg;
+  else
+    g_setup_error = msg;
+  return code;
+}
+
+int cuda_fail(msfv_session* s, cudaError_t e, const char* where) {
+  return fail(s, MSFV_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+struct PhaseScope {
+  msfv_session* s;
+  int ph;
+  cudaEvent_t a = nullptr, b = nullptr;
+  PhaseScope(msfv_session* s_, int ph_) : s(s_), ph(ph_) {
+    if (s->prof) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s->stream);
+    }
+  }
+  ~PhaseScope() {
+    if (s->prof) {
+      cudaEventRecord(b, s->stream);
+      s->pending.push_back({ph, a, b});
+    }
+  }
+};
+
+template <class T>
+T* dalloc(msfv_session* s, size_t count, cudaError_t* err) {
+  void* p = nullptr;
+  if (*err != cudaSuccess) return nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  *err = cudaMalloc(&p, bytes);
+  if (*err != cudaSuccess) return nullptr;
+  s->allocs.push_back(p);
+  s->ws_bytes += bytes;
+  return static_cast<T*>(p);
+}
+
+template <class T>
+cudaError_t upload(T* dst, const std::vector<T>& v, cudaStream_t st) {
+  if (v.empty()) return cudaSuccess;
+  return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+void free_all(msfv_session* s) {
+  for (void* p : s->allocs) cudaFree(p);
+  s->allocs.clear();
+  for (auto& e : s->pending) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  s->pending.clear();
+}
+
+int check_launch(msfv_session* s, const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(s, e, where);
+  return MSFV_OK;
+}
+
+// exact FP64 operation count of one entity's basis solve (FMA = 2 flops)
+double entity_flops(const EntDesc& e, int nvs) {
+  double f = 0.0;
+  for (int j = 0; j < e.n; ++j) {
+    const double bj = std::min(e.b, e.n - 1 - j);
+    const double bb = std::min(e.b, j);
+    f += 2.0 * (bj * (bj + 1) / 2) + bj + 2.0 * nvs * bj + 2.0 * nvs * bb + nvs;
+  }
+  return f;
+}
+
+}  // namespace
+
+// =============================================================================
+// setup / destroy
+// =============================================================================
+extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t** out) {
+  if (!out) return fail(nullptr, MSFV_ERR_ARG, "msfv_setup: out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(nullptr, MSFV_ERR_ARG, "msfv_setup: desc is NULL");
+  const int d = desc->dim;
+  if (d != 2 && d != 3) return fail(nullptr, MSFV_ERR_ARG, "dim must be 2 or 3");
+  const int c = desc->coarsen;
+  if (c < 1) return fail(nullptr, MSFV_ERR_ARG, "coarsen must be >= 1");
+  long long N = 1, Nc = 1;
+  for (int a = 0; a < d; ++a) {
+    if (desc->n[a] < 1) return fail(nullptr, MSFV_ERR_ARG, "mesh sizes must be >= 1");
+    if (desc->n[a] % c) return fail(nullptr, MSFV_ERR_ARG, "coarsen must divide every n[a]");
+    N *= desc->n[a];
+    Nc *= desc->n[a] / c;
+  }
+  if (Nc < 2) return fail(nullptr, MSFV_ERR_ARG, "need at least 2 coarse cells");
+  if (N > (1LL << 40)) return fail(nullptr, MSFV_ERR_ARG, "mesh too large");
+  if (desc->n_src < 1 || !desc->src_pos || !desc->src_neg)
+    return fail(nullptr, MSFV_ERR_ARG, "need n_src >= 1 and source arrays");
+  if (desc->n_rec < 1 || !desc->rec_cell)
+    return fail(nullptr, MSFV_ERR_ARG, "need n_rec >= 1 and a receiver array");
+  for (int j = 0; j < desc->n_src; ++j) {
+    const int64_t p = desc->src_pos[j], q = desc->src_neg[j];
+    if (p < 0 || p >= N || q < 0 || q >= N || p == q)
+      return fail(nullptr, MSFV_ERR_ARG, "source cell out of range or pos == neg");
+  }
+  for (int i = 0; i < desc->n_rec; ++i)
+    if (desc->rec_cell[i] < 0 || desc->rec_cell[i] >= N)
+      return fail(nullptr, MSFV_ERR_ARG, "receiver cell out of range");
+  if (desc->factor_mode == 2)
+    return fail(nullptr, MSFV_ERR_ARG, "factor_mode 2 (recompute) is not supported");
+  if (desc->factor_mode < 0 || desc->factor_mode > 2)
+    return fail(nullptr, MSFV_ERR_ARG, "factor_mode must be 0, 1 or 2");
+
+  msfv_session* s = new msfv_session();
+  s->stream = static_cast<cudaStream_t>(stream);
+  Geom& G = s->geo;
+  G.d = d;
+  G.c = c;
+  G.half = c / 2;
+  G.S = 1 << d;
+  for (int a = 0; a < 3; ++a) {
+    G.n[a] = (a < d) ? desc->n[a] : 1;
+    G.nc[a] = (a < d) ? desc->n[a] / c : 1;
+  }
+  G.N = N;
+  G.Nc = Nc;
+  G.st[0] = 1;
+  G.st[1] = G.n[0];
+  G.st[2] = (long long)G.n[0] * G.n[1];
+  G.cst[0] = 1;
+  G.cst[1] = G.nc[0];
+  G.cst[2] = (long long)G.nc[0] * G.nc[1];
+  DevGeom& g = s->dg;
+  g.d = d;
+  g.c = c;
+  g.half = G.half;
+  g.S = G.S;
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = G.n[a];
+    g.nc[a] = G.nc[a];
+    g.st[a] = G.st[a];
+    g.cst[a] = G.cst[a];
+  }
+  g.N = N;
+  g.Nc = Nc;
+  s->Ns = desc->n_src;
+  s->Nr = desc->n_rec;
+
+  // ---- entities of the dual-coarse grid ----------------------------------------
+  std::vector<Piece> pieces[3];
+  std::vector<int> piece_of[3];
+  for (int a = 0; a < 3; ++a) {
+    pieces[a] = (a < d) ? axis_pieces(G.n[a], c) : std::vector<Piece>{{true, 0, 0, 0, 0, 1}};
+    piece_of[a].assign(G.n[a], -1);
+    for (int q = 0; q < (int)pieces[a].size(); ++q)
+      for (int x = pieces[a][q].start; x < pieces[a][q].start + pieces[a][q].len; ++x)
+        piece_of[a][x] = q;
+  }
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> key2ent;  // -> (dim, index)
+  for (int q2 = 0; q2 < (int)pieces[2].size(); ++q2)
+    for (int q1 = 0; q1 < (int)pieces[1].size(); ++q1)
+      for (int q0 = 0; q0 < (int)pieces[0].size(); ++q0) {
+        const Piece* P[3] = {&pieces[0][q0], &pieces[1][q1], &pieces[2][q2]};
+        EntDesc e{};
+        int dim = 0;
+        int tang[3], nt = 0;
+        for (int a = 0; a < 3; ++a) {
+          e.org[a] = P[a]->start;
+          e.len[a] = P[a]->len;
+          if (!P[a]->vertex) tang[nt++] = a;
+        }
+        dim = nt;
+        if (dim == 0) continue;
+        // tangential axes sorted by length (stable), shortest fastest
+        std::stable_sort(tang, tang + nt, [&](int x, int y) { return e.len[x] < e.len[y]; });
+        for (int k = 0; k < 3; ++k) e.perm[k] = (k < nt) ? tang[k] : -1;
+        e.dim = dim;
+        e.n = 1;
+        for (int k = 0; k < nt; ++k) e.n *= e.len[tang[k]];
+        e.b = 1;
+        for (int k = 0; k + 1 < nt; ++k) e.b *= e.len[tang[k]];
+        int slots = 0;
+        for (int sl = 0; sl < G.S; ++sl) {
+          bool ok = true;
+          for (int a = 0; a < d; ++a) {
+            const int bit = (sl >> a) & 1;
+            if (P[a]->vertex) {
+              if (bit) ok = false;
+            } else {
+              if (bit == 0 && P[a]->lo < 0) ok = false;
+              if (bit == 1 && P[a]->hi < 0) ok = false;
+            }
+          }
+          if (ok) slots |= 1 << sl;
+        }
+        e.slots = slots;
+        e.fac = 0;
+        e.rec_off = 0;
+        e.rec_cnt = 0;
+        s->h_ents[dim].push_back(e);
+      }
+  // sort by cost (largest first) and place the stored factors
+  long long fac_total = 0;
+  for (int k = 1; k <= d; ++k) {
+    auto& v = s->h_ents[k];
+    std::stable_sort(v.begin(), v.end(), [](const EntDesc& x, const EntDesc& y) {
+      const double cx = (double)x.n * x.b * x.b + 32.0 * x.n * x.b;
+      const double cy = (double)y.n * y.b * y.b + 32.0 * y.n * y.b;
+      return cx > cy;
+    });
+    int nmax = 1, bmax = 1;
+    for (auto& e : v) {
+      e.fac = fac_total;
+      fac_total += (long long)e.n * (e.b + 1);
+      nmax = std::max(nmax, e.n);
+      bmax = std::max(bmax, e.b);
+    }
+    LocalLaunch& L = s->launch[k];
+    L.n_ents = (int)v.size();
+    L.nmax = nmax;
+    L.bmax = bmax;
+    L.npairs = bmax * (bmax + 1) / 2;
+    if (bmax > 255) {
+      delete s;
+      return fail(nullptr, MSFV_ERR_ARG, "local band too wide (coarsening too large)");
+    }
+    if (local_smem_bytes(g, L) > 227 * 1024) {
+      delete s;
+      return fail(nullptr, MSFV_ERR_ARG,
+                  "coarsening too large for on-chip local problems (3D c <= 11, 2D c <= 32)");
+    }
+    for (int i = 0; i < (int)v.size(); ++i) {
+      const EntDesc& e = v[i];
+      key2ent[std::make_tuple(piece_of[0][e.org[0]], piece_of[1][e.org[1]], piece_of[2][e.org[2]])] =
+          std::make_pair(k, i);
+    }
+  }
+  s->fac_bytes = (size_t)fac_total * sizeof(double);
+  for (const auto& e : s->h_ents[d]) {
+    const int nvs = __builtin_popcount((unsigned)e.slots);
+    s->int_flops += entity_flops(e, nvs);
+  }
+
+  // ---- receivers ------------------------------------------------------------------
+  std::vector<int64_t> rec(desc->rec_cell, desc->rec_cell + desc->n_rec);
+  std::vector<int64_t> ru(rec);
+  std::sort(ru.begin(), ru.end());
+  ru.erase(std::unique(ru.begin(), ru.end()), ru.end());
+  s->Nru = (int)ru.size();
+  std::vector<int> ru_off(ru.size() + 1, 0), ru_idx(rec.size());
+  {
+    std::vector<std::vector<int>> lists(ru.size());
+    for (int i = 0; i < (int)rec.size(); ++i) {
+      const int u = (int)(std::lower_bound(ru.begin(), ru.end(), rec[i]) - ru.begin());
+      lists[u].push_back(i);
+    }
+    int q = 0;
+    for (size_t u = 0; u < ru.size(); ++u) {
+      ru_off[u] = q;
+      for (int i : lists[u]) ru_idx[q++] = i;
+    }
+    ru_off[ru.size()] = q;
+  }
+  // receivers inside each entity (for the adjoint seeds) and P^T z maps
+  std::vector<int> rec_p, rec_u;
+  std::vector<std::vector<std::pair<int, int>>> ent_rec[4];
+  for (int k = 1; k <= d; ++k) ent_rec[k].resize(s->h_ents[k].size());
+  std::vector<std::vector<std::pair<int, int>>> cj(Nc);
+  for (int u = 0; u < (int)ru.size(); ++u) {
+    const long long x = ru[u];
+    int xc[3] = {(int)(x % G.n[0]), (int)((x / G.n[0]) % G.n[1]), (int)(x / G.st[2])};
+    const auto it =
+        key2ent.find(std::make_tuple(piece_of[0][xc[0]], piece_of[1][xc[1]], piece_of[2][xc[2]]));
+    if (it != key2ent.end()) {
+      const EntDesc& e = s->h_ents[it->second.first][it->second.second];
+      int p = 0, o = 1;
+      for (int k = 0; k < e.dim; ++k) {
+        const int a = e.perm[k];
+        p += (xc[a] - e.org[a]) * o;
+        o *= e.len[a];
+      }
+      ent_rec[it->second.first][it->second.second].push_back({p, u});
+    }
+    for (int sl = 0; sl < G.S; ++sl) {
+      long long J = 0;
+      bool ok = true;
+      for (int a = 0; a < d; ++a) {
+        const int t0 = xc[a] - G.half;
+        const int lo = t0 >= 0 ? t0 / c : -((-t0 + c - 1) / c);
+        const int va = lo + ((sl >> a) & 1);
+        if (va < 0 || va >= G.nc[a]) ok = false;
+        J += (long long)va * G.cst[a];
+      }
+      if (ok) cj[J].push_back({u, sl});
+    }
+  }
+  for (int k = 1; k <= d; ++k)
+    for (size_t i = 0; i < s->h_ents[k].size(); ++i) {
+      s->h_ents[k][i].rec_off = (int)rec_p.size();
+      s->h_ents[k][i].rec_cnt = (int)ent_rec[k][i].size();
+      for (auto& pr : ent_rec[k][i]) {
+        rec_p.push_back(pr.first);
+        rec_u.push_back(pr.second);
+      }
+    }
+  std::vector<int> cj_off(Nc + 1, 0), cj_u, cj_s;
+  for (long long J = 0; J < Nc; ++J) {
+    cj_off[J] = (int)cj_u.size();
+    for (auto& pr : cj[J]) {
+      cj_u.push_back(pr.first);
+      cj_s.push_back(pr.second);
+    }
+  }
+  cj_off[Nc] = (int)cj_u.size();
+  // coarse right-hand sides R q_j
+  std::vector<double> rq((size_t)s->Ns * Nc, 0.0);
+  auto coarse_of = [&](long long x) {
+    long long I = 0;
+    long long r = x;
+    for (int a = 0; a < 3; ++a) {
+      const int xa = (int)(r % G.n[a]);
+      r /= G.n[a];
+      I += (long long)(xa / c) * G.cst[a];
+    }
+    return I;
+  };
+  for (int j = 0; j < s->Ns; ++j) {
+    const double amp = desc->src_amp ? desc->src_amp[j] : 1.0;
+    rq[(size_t)j * Nc + coarse_of(desc->src_pos[j])] += amp;
+    rq[(size_t)j * Nc + coarse_of(desc->src_neg[j])] -= amp;
+  }
+  // banded LU dimensions of the pinned coarse matrix
+  s->band.n = Nc - 1;
+  s->band.kl = (int)(G.cst[0] + (d >= 2 ? G.cst[1] : 0) + (d == 3 ? G.cst[2] : 0));
+  s->band.ku = s->band.kl;
+  s->band.ldab = 2 * s->band.kl + s->band.ku + 1;
+
+  // ---- HBM budget and allocations --------------------------------------------------
+  const int S3 = (d == 3) ? 27 : 9;
+  const size_t Ssz = G.S;
+  size_t need = sizeof(double) * ((size_t)2 * d * N + N + 2 * N * Ssz + (size_t)d * N) +
+                s->fac_bytes +
+                sizeof(double) * ((size_t)3 * Nc * S3 + (size_t)5 * s->Ns * Nc +
+                                  (size_t)4 * s->Ns * s->Nr + 1 + (size_t)s->Ns * s->Nru +
+                                  (size_t)s->Nru * Ssz + 2 * N) +
+                sizeof(double) * (size_t)s->band.ldab * (size_t)s->band.n;
+  if (desc->hbm_budget_bytes && need > desc->hbm_budget_bytes) {
+    delete s;
+    return fail(nullptr, MSFV_ERR_OOM, "session workspace exceeds hbm_budget_bytes");
+  }
+  cudaError_t ce = cudaSuccess;
+  s->T = dalloc<double>(s, (size_t)2 * d * N, &ce);
+  s->sig = dalloc<double>(s, N, &ce);
+  s->Pw = dalloc<double>(s, (size_t)N * Ssz, &ce);
+  s->X = dalloc<double>(s, (size_t)N * Ssz, &ce);
+  s->gT = dalloc<double>(s, (size_t)d * N, &ce);
+  s->fac = dalloc<double>(s, (size_t)fac_total, &ce);
+  s->Ac = dalloc<double>(s, (size_t)Nc * S3, &ce);
+  s->dAc = dalloc<double>(s, (size_t)Nc * S3, &ce);
+  s->Lam = dalloc<double>(s, (size_t)Nc * S3, &ce);
+  s->t = dalloc<double>(s, (size_t)s->Ns * Nc, &ce);
+  s->rq = dalloc<double>(s, (size_t)s->Ns * Nc, &ce);
+  s->lam = dalloc<double>(s, (size_t)s->Ns * Nc, &ce);
+  s->dt = dalloc<double>(s, (size_t)s->Ns * Nc, &ce);
+  s->dpred = dalloc<double>(s, (size_t)s->Ns * s->Nr, &ce);
+  s->r = dalloc<double>(s, (size_t)s->Ns * s->Nr, &ce);
+  s->dobs_tmp = dalloc<double>(s, (size_t)s->Ns * s->Nr, &ce);
+  s->dpred_tmp = dalloc<double>(s, (size_t)s->Ns * s->Nr, &ce);
+  s->phi = dalloc<double>(s, 1, &ce);
+  s->zc = dalloc<double>(s, (size_t)s->Ns * s->Nru, &ce);
+  s->ZT = dalloc<double>(s, (size_t)s->Nru * Ssz, &ce);
+  s->m_tmp = dalloc<double>(s, N, &ce);
+  s->grad_tmp = dalloc<double>(s, N, &ce);
+  s->rec = dalloc<int64_t>(s, rec.size(), &ce);
+  s->ru_cell = dalloc<int64_t>(s, ru.size(), &ce);
+  s->ru_off = dalloc<int>(s, ru_off.size(), &ce);
+  s->ru_idx = dalloc<int>(s, ru_idx.size(), &ce);
+  s->cj_off = dalloc<int>(s, cj_off.size(), &ce);
+  s->cj_u = dalloc<int>(s, cj_u.size(), &ce);
+  s->cj_s = dalloc<int>(s, cj_s.size(), &ce);
+  s->rec_p = dalloc<int>(s, rec_p.size(), &ce);
+  s->rec_u = dalloc<int>(s, rec_u.size(), &ce);
+  s->status = dalloc<int>(s, 2, &ce);
+  s->band.ab = dalloc<double>(s, (size_t)s->band.ldab * (size_t)s->band.n, &ce);
+  s->band.piv = dalloc<int>(s, (size_t)s->band.n, &ce);
+  s->band.status = s->status + 1;
+  for (int k = 1; k <= d; ++k) s->d_ents[k] = dalloc<EntDesc>(s, s->h_ents[k].size(), &ce);
+  if (ce != cudaSuccess) {
+    const bool oom = (ce == cudaErrorMemoryAllocation);
+    std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(ce);
+    cudaGetLastError();
+    free_all(s);
+    delete s;
+    return fail(nullptr, oom ? MSFV_ERR_OOM : MSFV_ERR_CUDA, msg);
+  }
+  cudaStream_t st = s->stream;
+  ce = upload(s->rec, rec, st);
+  if (ce == cudaSuccess) ce = upload(s->ru_cell, ru, st);
+  if (ce == cudaSuccess) ce = upload(s->ru_off, ru_off, st);
+  if (ce == cudaSuccess) ce = upload(s->ru_idx, ru_idx, st);
+  if (ce == cudaSuccess) ce = upload(s->cj_off, cj_off, st);
+  if (ce == cudaSuccess) ce = upload(s->cj_u, cj_u, st);
+  if (ce == cudaSuccess) ce = upload(s->cj_s, cj_s, st);
+  if (ce == cudaSuccess) ce = upload(s->rec_p, rec_p, st);
+  if (ce == cudaSuccess) ce = upload(s->rec_u, rec_u, st);
+  if (ce == cudaSuccess) ce = upload(s->rq, rq, st);
+  for (int k = 1; k <= d && ce == cudaSuccess; ++k) ce = upload(s->d_ents[k], s->h_ents[k], st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->status, 0, 2 * sizeof(int), st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    std::string msg = std::string("setup upload failed: ") + cudaGetErrorString(ce);
+    free_all(s);
+    delete s;
+    return fail(nullptr, MSFV_ERR_CUDA, msg);
+  }
+  for (int k = 1; k <= d; ++k) s->launch[k].ents = s->d_ents[k];
+  *out = s;
+  return MSFV_OK;
+}
+
+extern "C" int msfv_destroy(msfv_session_t* s) {
+  if (!s) return MSFV_OK;
+  cudaStreamSynchronize(s->stream);
+  free_all(s);
+  delete s;
+  return MSFV_OK;
+}
+
+extern "C" const char* msfv_last_error(const msfv_session_t* s) {
+  return s ? s->err.c_str() : g_setup_error.c_str();
+}
+
+extern "C" int msfv_set_stream(msfv_session_t* s, void* stream) {
+  if (!s) return MSFV_ERR_ARG;
+  s->stream = static_cast<cudaStream_t>(stream);
+  return MSFV_OK;
+}
+
+// =============================================================================
+// the path
+// =============================================================================
+namespace {
+
+void coarse_solve(msfv_session* s, double* rhs, int transpose) {
+  const long long Nc = s->geo.Nc;
+  launch_band_solve(s->band, rhs, s->Ns, Nc, transpose, s->stream);
+  s->launches += 1;
+}
+
+int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
+  const DevGeom& g = s->dg;
+  cudaStream_t st = s->stream;
+  const int d = g.d;
+  {
+    PhaseScope ps(s, PH_FACE_T);
+    launch_face_T(g, m, s->T, s->sig, st);
+    s->launches += 2;
+  }
+  {
+    PhaseScope ps(s, PH_VERTEX);
+    launch_vertices(g, s->Pw, st);
+    s->launches += 1;
+  }
+  for (int k = 1; k <= d; ++k) {
+    PhaseScope ps(s, k == d ? PH_INTERIOR : (k == 1 ? PH_EDGE : PH_FACE));
+    launch_local_forward(g, s->launch[k], s->T, s->Pw, s->fac, s->status, st);
+    s->launches += s->launch[k].n_ents ? 1 : 0;
+  }
+  {
+    PhaseScope ps(s, PH_COARSE_ASM);
+    launch_coarse_assemble(g, s->T, s->Pw, nullptr, nullptr, nullptr, s->Ac, 0, st);
+    s->launches += 1;
+  }
+  {
+    PhaseScope ps(s, PH_COARSE_SOLVE);
+    cudaMemcpyAsync(s->t, s->rq, sizeof(double) * (size_t)s->Ns * g.Nc, cudaMemcpyDeviceToDevice, st);
+    launch_band_build(g, s->Ac, s->band, st);
+    launch_band_factor(s->band, st);
+    s->launches += 2;
+    coarse_solve(s, s->t, 0);
+  }
+  {
+    PhaseScope ps(s, PH_PROLONG);
+    launch_prolong_receivers(g, s->Pw, s->t, s->Ns, s->rec, s->Nr, s->dpred, st);
+    s->launches += 1;
+    if (d_pred)
+      cudaMemcpyAsync(d_pred, s->dpred, sizeof(double) * (size_t)s->Ns * s->Nr,
+                      cudaMemcpyDeviceToDevice, st);
+    if (u) {
+      launch_prolong_full(g, s->Pw, s->t, s->Ns, u, st);
+      s->launches += 1;
+    }
+  }
+  const int rc = check_launch(s, "msfv_forward");
+  if (rc == MSFV_OK) s->have_forward = true;
+  return rc;
+}
+
+// J^T w for w (Ns x Nr, device) at the last forward; out: N doubles
+int run_jtvec(msfv_session* s, const double* w, double* out) {
+  const DevGeom& g = s->dg;
+  cudaStream_t st = s->stream;
+  const int d = g.d;
+  const double* Dl = s->T + (size_t)d * g.N;
+  {
+    PhaseScope ps(s, PH_ADJ_SETUP);
+    launch_receiver_gather(w, s->Ns, s->Nr, s->ru_off, s->ru_idx, s->Nru, s->zc, st);
+    launch_coarse_adjoint_rhs(g, s->Pw, s->zc, s->Ns, s->Nru, s->cj_off, s->cj_u, s->cj_s,
+                              s->ru_cell, s->lam, st);
+    s->launches += 2;
+    coarse_solve(s, s->lam, 1);
+    launch_lambda(g, s->t, s->lam, s->Ns, s->Lam, st);
+    launch_zt(g, s->t, s->zc, s->Ns, s->Nru, s->ru_cell, s->ZT, st);
+    cudaMemsetAsync(s->gT, 0, sizeof(double) * (size_t)d * g.N, st);
+    s->launches += 2;
+  }
+  for (int k = d; k >= 1; --k) {
+    PhaseScope ps(s, k == d ? PH_ADJ_INTERIOR : (k == 1 ? PH_ADJ_EDGE : PH_ADJ_FACE));
+    launch_local_adjoint(g, s->launch[k], s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u, s->ZT,
+                         s->X, s->gT, st);
+    s->launches += s->launch[k].n_ents ? 1 : 0;
+  }
+  {
+    PhaseScope ps(s, PH_GRAD);
+    launch_grad(g, s->T, Dl, s->Pw, s->Lam, s->gT, out, st);
+    s->launches += 1;
+  }
+  return check_launch(s, "msfv_jtvec");
+}
+
+int run_jvec(msfv_session* s, const double* v, double* jv) {
+  const DevGeom& g = s->dg;
+  cudaStream_t st = s->stream;
+  const int d = g.d;
+  const double* Dl = s->T + (size_t)d * g.N;
+  PhaseScope ps(s, PH_TANGENT);
+  cudaMemsetAsync(s->X, 0, sizeof(double) * (size_t)g.N * g.S, st);
+  for (int k = 1; k <= d; ++k) {
+    launch_local_tangent(g, s->launch[k], s->T, Dl, v, s->Pw, s->fac, s->X, st);
+    s->launches += s->launch[k].n_ents ? 1 : 0;
+  }
+  launch_coarse_assemble(g, s->T, s->Pw, Dl, v, s->X, s->dAc, 1, st);
+  launch_coarse_tangent_rhs(g, s->dAc, s->t, s->Ns, s->dt, st);
+  s->launches += 2;
+  coarse_solve(s, s->dt, 0);
+  launch_prolong_tangent(g, s->Pw, s->X, s->t, s->dt, s->Ns, s->rec, s->Nr, jv, st);
+  s->launches += 1;
+  return check_launch(s, "msfv_jvec");
+}
+
+int read_status(msfv_session* s) {
+  int h[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, s->status, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "status read");
+  if (h[0]) return fail(s, MSFV_ERR_NUMERIC, "non-positive pivot in a local problem");
+  if (h[1]) return fail(s, MSFV_ERR_NUMERIC, "zero pivot in the coarse LU (singular A_c)");
+  return MSFV_OK;
+}
+
+}  // namespace
+
+extern "C" int msfv_forward(msfv_session_t* s, const double* m_dev, double* d_pred_dev,
+                            double* u_dev) {
+  if (!s) return MSFV_ERR_ARG;
+  if (!m_dev || !d_pred_dev) return fail(s, MSFV_ERR_ARG, "msfv_forward: NULL m or d_pred");
+  return run_forward(s, m_dev, d_pred_dev, u_dev);
+}
+
+extern "C" int msfv_adjoint(msfv_session_t* s, const double* d_obs_dev, double* grad_dev,
+                            double* phi_host) {
+  if (!s) return MSFV_ERR_ARG;
+  if (!d_obs_dev || !grad_dev) return fail(s, MSFV_ERR_ARG, "msfv_adjoint: NULL argument");
+  if (!s->have_forward) return fail(s, MSFV_ERR_STATE, "msfv_adjoint before msfv_forward");
+  {
+    PhaseScope ps(s, PH_ADJ_SETUP);
+    launch_residual(s->dpred, d_obs_dev, s->Ns * s->Nr, s->r, s->phi, s->stream);
+    s->launches += 1;
+  }
+  int rc = run_jtvec(s, s->r, grad_dev);
+  if (rc != MSFV_OK) return rc;
+  if (phi_host) {
+    cudaError_t e =
+        cudaMemcpyAsync(phi_host, s->phi, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "phi copy");
+    return read_status(s);
+  }
+  return MSFV_OK;
+}
+
+extern "C" int msfv_jvec(msfv_session_t* s, const double* v_dev, double* jv_dev) {
+  if (!s) return MSFV_ERR_ARG;
+  if (!v_dev || !jv_dev) return fail(s, MSFV_ERR_ARG, "msfv_jvec: NULL argument");
+  if (!s->have_forward) return fail(s, MSFV_ERR_STATE, "msfv_jvec before msfv_forward");
+  return run_jvec(s, v_dev, jv_dev);
+}
+
+extern "C" int msfv_jtvec(msfv_session_t* s, const double* w_dev, double* jtw_dev) {
+  if (!s) return MSFV_ERR_ARG;
+  if (!w_dev || !jtw_dev) return fail(s, MSFV_ERR_ARG, "msfv_jtvec: NULL argument");
+  if (!s->have_forward) return fail(s, MSFV_ERR_STATE, "msfv_jtvec before msfv_forward");
+  return run_jtvec(s, w_dev, jtw_dev);
+}
+
+extern "C" int msfv_solve_host(msfv_session_t* s, const double* m_host, const double* d_obs_host,
+                               double* d_pred_host, double* grad_host, double* phi_host) {
+  if (!s) return MSFV_ERR_ARG;
+  if (!m_host || !d_obs_host || !d_pred_host || !grad_host)
+    return fail(s, MSFV_ERR_ARG, "msfv_solve_host: NULL argument");
+  cudaStream_t st = s->stream;
+  const size_t nd = sizeof(double) * (size_t)s->Ns * s->Nr;
+  cudaError_t e = cudaMemcpyAsync(s->m_tmp, m_host, sizeof(double) * (size_t)s->dg.N,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->dobs_tmp, d_obs_host, nd, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(s, e, "msfv_solve_host upload");
+  int rc = run_forward(s, s->m_tmp, s->dpred_tmp, nullptr);
+  if (rc != MSFV_OK) return rc;
+  launch_residual(s->dpred, s->dobs_tmp, s->Ns * s->Nr, s->r, s->phi, st);
+  s->launches += 1;
+  rc = run_jtvec(s, s->r, s->grad_tmp);
+  if (rc != MSFV_OK) return rc;
+  e = cudaMemcpyAsync(d_pred_host, s->dpred, nd, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(grad_host, s->grad_tmp, sizeof(double) * (size_t)s->dg.N,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && phi_host)
+    e = cudaMemcpyAsync(phi_host, s->phi, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(s, e, "msfv_solve_host download");
+  return read_status(s);
+}
+
+// =============================================================================
+// introspection
+// =============================================================================
+extern "C" int msfv_info(const msfv_session_t* s, int64_t* out, int n_out) {
+  if (!s || !out) return MSFV_ERR_ARG;
+  int64_t v[8] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
+                  (int64_t)(s->h_ents[1].size() + s->h_ents[2].size() + s->h_ents[3].size()),
+                  (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, 0};
+  for (int i = 0; i < n_out && i < 8; ++i) out[i] = v[i];
+  return MSFV_OK;
+}
+
+extern "C" int msfv_profile(msfv_session_t* s, int enable) {
+  if (!s) return MSFV_ERR_ARG;
+  s->prof = enable != 0;
+  return MSFV_OK;
+}
+
+extern "C" int msfv_phase_times(msfv_session_t* s, double* ms, int64_t* calls, int n, int reset) {
+  if (!s) return MSFV_ERR_ARG;
+  cudaStreamSynchronize(s->stream);
+  for (auto& e : s->pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) {
+      s->ph_ms[e.ph] += t;
+      s->ph_calls[e.ph] += 1;
+    }
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  s->pending.clear();
+  for (int k = 0; k < n && k < PH_COUNT; ++k) {
+    if (ms) ms[k] = s->ph_ms[k];
+    if (calls) calls[k] = s->ph_calls[k];
+  }
+  if (reset)
+    for (int k = 0; k < PH_COUNT; ++k) {
+      s->ph_ms[k] = 0;
+      s->ph_calls[k] = 0;
+    }
+  return PH_COUNT;
+}
+
+extern "C" const char* msfv_phase_name(int k) {
+  return (k >= 0 && k < PH_COUNT) ? kPhaseNames[k] : "";
+}
+
+extern "C" double msfv_interior_flops(const msfv_session_t* s) { return s ? s->int_flops : 0.0; }
+
+extern "C" int64_t msfv_launch_count(const msfv_session_t* s) { return s ? s->launches : 0; }

@@ -1,0 +1,226 @@
+"""Thin Python binding of the MSFV C ABI (include/msfv.h).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+``libmsfv.so``.  PyTorch supplies device memory (CUDA tensors) and the stream.
+There is no CPU fallback: if the library or a GPU is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+MSFV_OK = 0
+_ERR = {1: "MSFV_ERR_ARG", 2: "MSFV_ERR_OOM", 3: "MSFV_ERR_NUMERIC", 4: "MSFV_ERR_TIMEOUT",
+        5: "MSFV_ERR_CUDA", 6: "MSFV_ERR_STATE"}
+
+_lib = None
+
+
+class MSFVError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("coarsen", ctypes.c_int),
+                ("n_src", ctypes.c_int), ("src_pos", ctypes.POINTER(ctypes.c_int64)),
+                ("src_neg", ctypes.POINTER(ctypes.c_int64)),
+                ("src_amp", ctypes.POINTER(ctypes.c_double)),
+                ("n_rec", ctypes.c_int), ("rec_cell", ctypes.POINTER(ctypes.c_int64)),
+                ("factor_mode", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def load(path: Optional[str] = None):
+    """Load libmsfv.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libmsfv.so not found at {p}: run __graft_entry__.build() first "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(p)
+    vp, i64p, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    L.msfv_setup.argtypes = [ctypes.POINTER(_Desc), vp, ctypes.POINTER(vp)]
+    L.msfv_forward.argtypes = [vp, vp, vp, vp]
+    L.msfv_adjoint.argtypes = [vp, vp, vp, dp]
+    L.msfv_jvec.argtypes = [vp, vp, vp]
+    L.msfv_jtvec.argtypes = [vp, vp, vp]
+    L.msfv_solve_host.argtypes = [vp, vp, vp, vp, vp, dp]
+    L.msfv_destroy.argtypes = [vp]
+    L.msfv_last_error.argtypes = [vp]
+    L.msfv_last_error.restype = ctypes.c_char_p
+    L.msfv_set_stream.argtypes = [vp, vp]
+    L.msfv_info.argtypes = [vp, i64p, ctypes.c_int]
+    L.msfv_profile.argtypes = [vp, ctypes.c_int]
+    L.msfv_phase_times.argtypes = [vp, dp, i64p, ctypes.c_int, ctypes.c_int]
+    L.msfv_phase_name.argtypes = [ctypes.c_int]
+    L.msfv_phase_name.restype = ctypes.c_char_p
+    L.msfv_interior_flops.argtypes = [vp]
+    L.msfv_interior_flops.restype = ctypes.c_double
+    L.msfv_launch_count.argtypes = [vp]
+    L.msfv_launch_count.restype = ctypes.c_int64
+    for f in ("msfv_setup", "msfv_forward", "msfv_adjoint", "msfv_jvec", "msfv_jtvec",
+              "msfv_solve_host", "msfv_destroy", "msfv_set_stream", "msfv_info", "msfv_profile",
+              "msfv_phase_times", "msfv_phase_name"):
+        if getattr(L, f).restype is None and f != "msfv_phase_name":
+            getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Session:
+    """One MSFV problem (mesh, coarsening, sources, receivers) on the current GPU.
+
+    Mirrors the C ABI: ``forward`` (steps a-e), ``adjoint`` (misfit and gradient),
+    ``jvec`` / ``jtvec`` (Sec. 4.3 sensitivities), ``solve_host``.
+    """
+
+    def __init__(self, prob, stream=None, factor_mode: int = 0, hbm_budget_bytes: int = 0):
+        L = load()
+        self._lib = L
+        self.prob = prob
+        n = tuple(int(v) for v in prob.n)
+        self.dim = len(n)
+        self.N = int(np.prod(n))
+        self.Ns = int(prob.n_src)
+        self.Nr = int(prob.n_rec)
+        self._src_pos = np.ascontiguousarray(prob.src_pos, dtype=np.int64)
+        self._src_neg = np.ascontiguousarray(prob.src_neg, dtype=np.int64)
+        self._src_amp = np.ascontiguousarray(prob.src_amp, dtype=np.float64)
+        self._rec = np.ascontiguousarray(prob.rec_cell, dtype=np.int64)
+        d = _Desc()
+        d.dim = self.dim
+        for a in range(3):
+            d.n[a] = n[a] if a < self.dim else 1
+        d.coarsen = int(prob.coarsen)
+        d.n_src = self.Ns
+        d.src_pos = self._src_pos.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.src_neg = self._src_neg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.src_amp = self._src_amp.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.n_rec = self.Nr
+        d.rec_cell = self._rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d.factor_mode = int(factor_mode)
+        d.hbm_budget_bytes = int(hbm_budget_bytes)
+        h = ctypes.c_void_p()
+        self._h = None
+        rc = L.msfv_setup(ctypes.byref(d), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h))
+        if rc != MSFV_OK:
+            raise MSFVError(rc, L.msfv_last_error(None).decode())
+        self._h = h
+
+    # -- helpers ------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != MSFV_OK:
+            raise MSFVError(rc, self._lib.msfv_last_error(self._h).decode())
+
+    def set_stream(self, stream=None):
+        self._check(self._lib.msfv_set_stream(self._h, ctypes.c_void_p(_stream_handle(stream))))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.msfv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the path -------------------------------------------------------------------
+    def forward(self, m, d_pred=None, u=None):
+        import torch
+        if d_pred is None:
+            d_pred = torch.empty((self.Ns, self.Nr), dtype=torch.float64, device=m.device)
+        self._check(self._lib.msfv_forward(self._h, _ptr(m), _ptr(d_pred),
+                                           _ptr(u) if u is not None else None))
+        return d_pred
+
+    def adjoint(self, d_obs, grad=None, want_phi: bool = True):
+        import torch
+        if grad is None:
+            grad = torch.empty(self.N, dtype=torch.float64, device=d_obs.device)
+        phi = ctypes.c_double(0.0)
+        self._check(self._lib.msfv_adjoint(self._h, _ptr(d_obs), _ptr(grad),
+                                           ctypes.byref(phi) if want_phi else None))
+        return (phi.value if want_phi else None), grad
+
+    def jvec(self, v, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.Ns, self.Nr), dtype=torch.float64, device=v.device)
+        self._check(self._lib.msfv_jvec(self._h, _ptr(v), _ptr(out)))
+        return out
+
+    def jtvec(self, w, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float64, device=w.device)
+        self._check(self._lib.msfv_jtvec(self._h, _ptr(w), _ptr(out)))
+        return out
+
+    def solve_host(self, m_host: np.ndarray, d_obs_host: np.ndarray, d_pred_host=None,
+                   grad_host=None):
+        """Forward + gradient through host buffers (copies inside the call)."""
+        m_host = np.ascontiguousarray(m_host, dtype=np.float64)
+        d_obs_host = np.ascontiguousarray(d_obs_host, dtype=np.float64)
+        if d_pred_host is None:
+            d_pred_host = np.empty((self.Ns, self.Nr))
+        if grad_host is None:
+            grad_host = np.empty(self.N)
+        phi = ctypes.c_double(0.0)
+        self._check(self._lib.msfv_solve_host(
+            self._h, m_host.ctypes.data, d_obs_host.ctypes.data, d_pred_host.ctypes.data,
+            grad_host.ctypes.data, ctypes.byref(phi)))
+        return d_pred_host, grad_host, phi.value
+
+    # -- introspection ----------------------------------------------------------------
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 8)()
+        self._check(self._lib.msfv_info(self._h, out, 8))
+        keys = ["N", "Nc", "Ns", "Nr", "n_local_problems", "workspace_bytes", "factor_bytes",
+                "coarse_solver"]
+        return dict(zip(keys, list(out)))
+
+    def profile(self, enable: bool = True):
+        self._check(self._lib.msfv_profile(self._h, int(enable)))
+
+    def phase_times(self, reset: bool = False) -> dict:
+        ms = (ctypes.c_double * 32)()
+        calls = (ctypes.c_int64 * 32)()
+        n = self._lib.msfv_phase_times(self._h, ms, calls, 32, int(reset))
+        return {self._lib.msfv_phase_name(k).decode(): (ms[k], calls[k]) for k in range(n)}
+
+    def interior_flops(self) -> float:
+        return float(self._lib.msfv_interior_flops(self._h))
+
+    def launch_count(self) -> int:
+        return int(self._lib.msfv_launch_count(self._h))

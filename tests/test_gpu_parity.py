@@ -1,0 +1,187 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Bar: 1e-9 relative 2-norm on predicted data, fields u, misfit, gradient, J v and
+J^T w (all FP64 on both sides).  Cases span several dual cells per axis, partial
+dual cells at the boundary, odd and even coarsening, c = 1, non-cubic meshes,
+repeated receivers, sources and receivers on vertex / edge cells, and the full
+2D 64x64 and 3D 128^3 workloads."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.msfv_oracle import Oracle  # noqa: E402
+from paper_1707_07598_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1707_07598_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+CASES = [
+    ((16, 16), 4, 2, 9),
+    ((24, 16), 8, 3, 12),
+    ((18, 18), 3, 2, 10),
+    ((20, 15), 5, 2, 8),
+    ((16, 12), 2, 2, 7),
+    ((8, 8), 1, 2, 5),
+    ((32, 32), 8, 1, 32),
+    ((8, 8, 8), 4, 2, 9),
+    ((12, 8, 8), 4, 2, 9),
+    ((9, 9, 6), 3, 2, 7),
+    ((16, 16, 16), 8, 3, 20),
+    ((10, 10, 10), 5, 2, 8),
+    ((8, 6, 4), 2, 2, 6),
+    ((4, 4, 4), 1, 1, 4),
+    ((24, 16, 16), 8, 4, 30),
+]
+
+
+def run_pair(prob, m, dev, seed=0):
+    orc = Oracle(prob)
+    st = orc.forward(m)
+    d_obs = st['d'] * 1.02 + W.noise_like(st['d'].shape, 1e-3 * np.abs(st['d']).max(), seed + 1)
+    phi_ref, g_ref = orc.misfit_gradient(st, d_obs)
+    from paper_1707_07598_gb300.msfv import Session
+    s = Session(prob)
+    mt = torch.from_numpy(m).to(dev)
+    u = torch.empty((prob.n_src, prob.N), dtype=torch.float64, device=dev)
+    d = s.forward(mt, u=u)
+    phi, g = s.adjoint(torch.from_numpy(d_obs).to(dev))
+    torch.cuda.synchronize()
+    return orc, st, s, d.cpu().numpy(), u.cpu().numpy(), phi, g.cpu().numpy(), d_obs, phi_ref, g_ref
+
+
+@pytest.mark.parametrize("n,c,ns,nr", CASES)
+def test_forward_and_gradient_match_oracle(dev, n, c, ns, nr):
+    prob = W.make_problem(n, c, ns, nr, seed=11, top_layer=len(n) == 3)
+    m = W.gaussian_random_field(n, 0.2, 12)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
+    assert rel(d, st['d']) < TOL
+    assert rel(u, st['U']) < TOL
+    assert abs(phi - phi_ref) <= TOL * abs(phi_ref)
+    assert rel(g, g_ref) < TOL
+    s.close()
+
+
+@pytest.mark.parametrize("n,c,ns,nr", [((16, 16), 4, 2, 9), ((20, 15), 5, 2, 8),
+                                       ((8, 8, 8), 4, 2, 9), ((9, 9, 6), 3, 2, 7),
+                                       ((16, 16, 16), 8, 3, 20)])
+def test_jvec_and_jtvec_match_oracle(dev, n, c, ns, nr):
+    prob = W.make_problem(n, c, ns, nr, seed=13, top_layer=False)
+    m = W.gaussian_random_field(n, 0.25, 14)
+    orc = Oracle(prob)
+    st = orc.forward(m)
+    from paper_1707_07598_gb300.msfv import Session
+    s = Session(prob)
+    s.forward(torch.from_numpy(m).to(dev))
+    v = W.noise_like(prob.N, 1.0, 15)
+    w = W.noise_like((prob.n_src, prob.n_rec), 1.0, 16)
+    jv = s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy()
+    jtw = s.jtvec(torch.from_numpy(w).to(dev)).cpu().numpy()
+    assert rel(jv, orc.jvec(st, v)) < TOL
+    assert rel(jtw, orc.jtvec(st, w)) < TOL
+    # adjoint consistency on the GPU alone
+    assert abs(np.sum(w * jv) - jtw @ v) <= 1e-12 * np.linalg.norm(w) * np.linalg.norm(jv) * 10
+    s.close()
+
+
+def test_repeated_receivers_and_vertex_sources(dev):
+    n, c = (16, 16, 8), 4
+    base = W.make_problem(n, c, 2, 6, seed=3, top_layer=False)
+    # vertex cell (2,2,2): c*0 + 2 on each axis; an edge cell next to it
+    vert = 2 + 16 * 2 + 256 * 2
+    rec = np.array([vert, vert, vert + 1, 5, 5, 77, 200], dtype=np.int64)
+    prob = W.Problem(n=n, coarsen=c, src_pos=np.array([vert, 9]), src_neg=np.array([100, vert + 1]),
+                     src_amp=np.array([1.0, 2.5]), rec_cell=rec)
+    m = W.gaussian_random_field(n, 0.2, 4)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev, seed=7)
+    assert rel(d, st['d']) < TOL
+    assert rel(g, g_ref) < TOL
+    s.close()
+
+
+def test_solve_host_matches_device_path(dev):
+    prob = W.make_problem((16, 16, 16), 8, 2, 12, seed=21)
+    m = W.gaussian_random_field(prob.n, 0.2, 22)
+    from paper_1707_07598_gb300.msfv import Session
+    s = Session(prob)
+    d_dev = s.forward(torch.from_numpy(m).to(dev)).cpu().numpy()
+    d_obs = d_dev * 1.01
+    phi_dev, g_dev = s.adjoint(torch.from_numpy(d_obs).to(dev))
+    d_h, g_h, phi_h = s.solve_host(m, d_obs)
+    assert np.array_equal(d_h, d_dev)
+    assert np.array_equal(g_h, g_dev.cpu().numpy())
+    assert phi_h == phi_dev
+    s.close()
+
+
+def test_repeatable_bitwise(dev):
+    """Deterministic reductions: two runs give identical bits."""
+    prob = W.make_problem((16, 16, 16), 4, 3, 20, seed=31)
+    m = W.gaussian_random_field(prob.n, 0.2, 32)
+    from paper_1707_07598_gb300.msfv import Session
+    s = Session(prob)
+    mt = torch.from_numpy(m).to(dev)
+    d1 = s.forward(mt).clone()
+    _, g1 = s.adjoint(d1 * 1.01)
+    g1 = g1.clone()
+    d2 = s.forward(mt)
+    _, g2 = s.adjoint(d1 * 1.01)
+    assert torch.equal(d1, d2) and torch.equal(g1, g2)
+    s.close()
+
+
+def test_gradient_central_differences_on_gpu(dev):
+    """Central differences (step 1e-6) along 20 random directions (GPU only)."""
+    prob = W.make_problem((32, 32, 32), 8, 4, 64, seed=41)
+    m = W.gaussian_random_field(prob.n, 0.15, 42)
+    from paper_1707_07598_gb300.msfv import Session
+    s = Session(prob)
+    mt = torch.from_numpy(m).to(dev)
+    d0 = s.forward(mt)
+    d_obs = d0 * 1.05
+    _, g = s.adjoint(d_obs)
+    g = g.clone()
+
+    def misfit(mm):
+        dd = s.forward(mm)
+        return 0.5 * float(torch.sum((dd - d_obs) ** 2))
+    for k in range(20):
+        v = torch.from_numpy(W.noise_like(prob.N, 1.0, 100 + k)).to(dev)
+        fd = (misfit(mt + 1e-6 * v) - misfit(mt - 1e-6 * v)) / 2e-6
+        an = float(g @ v)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * float(g.norm() * v.norm()))
+    s.close()
+
+
+def test_config_2d_64_full(dev):
+    prob, m = W.config_2d_64()
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
+    assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
+    s.close()
+
+
+def test_config_3d_128_full(dev):
+    """The full 128^3, c = 8, 16-dipole, 512-receiver workload the benchmark times."""
+    prob, m = W.config_3d_128()
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
+    assert rel(d, st['d']) < TOL
+    assert rel(u, st['U']) < TOL
+    assert abs(phi - phi_ref) <= TOL * abs(phi_ref)
+    assert rel(g, g_ref) < TOL
+    s.close()
