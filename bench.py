@@ -228,6 +228,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     phases = sess.phase_times(reset=True)
     sess.profile(False)
+    info = sess.info()
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -298,7 +299,9 @@ def run_ours(args):
                           "l2": "flushed before every timed step (512 MiB write)",
                           "factor_mode": "store"},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk, "phases_ms_per_step": phase_ms}
+               "clocks": clk, "phases_ms_per_step": phase_ms,
+               "coarse": {"solver": "mg-gmres" if info["coarse_solver"] else "banded-lu",
+                          "iters_fwd": info["coarse_iters"], "iters_adj": info["coarse_iters_T"]}}
         print(json.dumps(out))
     sess.close()
     if world > 1:

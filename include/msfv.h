@@ -131,8 +131,20 @@ int msfv_set_stream(msfv_session_t* s, void* stream);
 
 /* Sizes of the session: out[0]=N, out[1]=Nc, out[2]=Ns, out[3]=Nr, out[4]=number of
  * local problems (edges + faces + dual-cell interiors), out[5]=workspace bytes,
- * out[6]=stored-factor bytes, out[7]=coarse solver (0 banded LU, 1 multigrid GMRES). */
+ * out[6]=stored-factor bytes, out[7]=coarse solver (0 banded LU, 1 multigrid GMRES),
+ * out[8] / out[9]=largest number of GMRES iterations over the right-hand sides of the
+ * last coarse solve with A_c / A_c^T (0 for the banded LU; reading them synchronises
+ * the stream), out[10]=thread-block cluster size (CTAs, one per SM) the multigrid
+ * GMRES kernel gives each right-hand side.  n_out may be smaller than 11. */
 int msfv_info(const msfv_session_t* s, int64_t* out, int n_out);
+
+/* Barrier time stamps of the multigrid GMRES coarse solver, recorded only when the
+ * environment variable MSFV_TRACE_COARSE=1 was set at msfv_setup: each entry is
+ * (phase tag << 48) | (ns of the GPU global timer & 2^48-1), for the cluster that
+ * solves right-hand side 0, appended over all solves since the last read.  Copies up
+ * to cap entries to out (host), clears the log, synchronises the stream and returns
+ * the number copied (0 when tracing is off, a negative status on error). */
+int msfv_coarse_trace(msfv_session_t* s, int64_t* out, int cap);
 
 /* Phase timers recorded with CUDA events on the session stream.  enable != 0 turns
  * recording on.  msfv_phase_times writes up to n accumulated times (ms) per phase

@@ -18,11 +18,24 @@ namespace msfv {
 
 namespace {
 
+// cell index -> coordinates; 32-bit arithmetic (setup guarantees N < 2^31)
 __device__ __forceinline__ void coords(const DevGeom& g, long long x, int* xc) {
-  xc[0] = (int)(x % g.n[0]);
-  const long long r = x / g.n[0];
-  xc[1] = (int)(r % g.n[1]);
-  xc[2] = (int)(r / g.n[1]);
+  const unsigned u = (unsigned)x, n0 = (unsigned)g.n[0], n1 = (unsigned)g.n[1];
+  const unsigned r = u / n0;
+  xc[0] = (int)(u - r * n0);
+  const unsigned q = r / n1;
+  xc[1] = (int)(r - q * n1);
+  xc[2] = (int)q;
+}
+
+// coarse index -> coordinates (32-bit)
+__device__ __forceinline__ void ccoords(const DevGeom& g, long long I, int* c) {
+  const unsigned u = (unsigned)I, n0 = (unsigned)g.nc[0], n1 = (unsigned)g.nc[1];
+  const unsigned r = u / n0;
+  c[0] = (int)(u - r * n0);
+  const unsigned q = r / n1;
+  c[1] = (int)(r - q * n1);
+  c[2] = (int)q;
 }
 
 __device__ __forceinline__ int lo_vertex(const DevGeom& g, int xa) {
@@ -102,13 +115,10 @@ void launch_face_T(const DevGeom& g, const double* m, double* T, double* sig, cu
 __global__ void k_vertices(DevGeom g, double* __restrict__ Pw) {
   const long long J = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (J >= g.Nc) return;
-  long long r = J;
+  int Kc[3];
+  ccoords(g, J, Kc);
   long long x = 0;
-  for (int a = 0; a < g.d; ++a) {
-    const int K = (int)(r % g.nc[a]);
-    r /= g.nc[a];
-    x += (long long)(g.c * K + g.half) * g.st[a];
-  }
+  for (int a = 0; a < g.d; ++a) x += (long long)(g.c * Kc[a] + g.half) * g.st[a];
   for (int s = 0; s < g.S; ++s) Pw[x * g.S + s] = (s == 0) ? 1.0 : 0.0;
 }
 
@@ -117,6 +127,8 @@ void launch_vertices(const DevGeom& g, double* Pw, cudaStream_t s) {
 }
 
 // ---- (d) A_c = R A P ---------------------------------------------------------------
+// The coarse operator is stored offset-major: Ac[o * Nc + I] is the coefficient of
+// coarse vertex I + o in row I (o over the 3^d stencil, axis 0 fastest).
 // One thread per (coarse row I, stencil offset o): sum over the fine faces on the
 // boundary of primal coarse cell I of T_f (phi_J(inside) - phi_J(outside)), J = I + o.
 // tangent != 0: d A_c = R dA P + R A dP with dT_f = Dl v_lower + (T - Dl) v_upper.
@@ -127,15 +139,14 @@ __global__ void k_coarse_assemble(DevGeom g, const double* __restrict__ T,
   const int S3 = stencil_size(g);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.Nc * S3) return;
-  const long long I = idx / S3;
-  const int o = (int)(idx - I * S3);
+  // offset-major layout: Ac[o * Nc + I]
+  const int o = (int)(idx / g.Nc);
+  const long long I = idx - (long long)o * g.Nc;
   int Ic[3] = {0, 0, 0}, Jc[3] = {0, 0, 0};
+  ccoords(g, I, Ic);
   {
-    long long r = I;
     int oo = o;
     for (int a = 0; a < g.d; ++a) {
-      Ic[a] = (int)(r % g.nc[a]);
-      r /= g.nc[a];
       Jc[a] = Ic[a] + (oo % 3) - 1;
       oo /= 3;
     }
@@ -349,12 +360,13 @@ __global__ void k_lambda(DevGeom g, const double* __restrict__ t, const double* 
   if (idx >= g.Nc * S3) return;
   const long long v = idx / S3;
   const int o = (int)(idx - v * S3);
-  long long r = v, K = 0;
+  long long K = 0;
   int oo = o;
   bool ok = true;
+  int vc[3];
+  ccoords(g, v, vc);
   for (int a = 0; a < g.d; ++a) {
-    const int va = (int)(r % g.nc[a]);
-    r /= g.nc[a];
+    const int va = vc[a];
     const int ka = va + (oo % 3) - 1;
     oo /= 3;
     if (ka < 0 || ka >= g.nc[a]) ok = false;
@@ -481,12 +493,8 @@ __global__ void k_coarse_tan_rhs(DevGeom g, const double* __restrict__ dAc,
   if (idx >= (long long)Ns * g.Nc) return;
   const int j = (int)(idx / g.Nc);
   const long long I = idx - (long long)j * g.Nc;
-  long long r = I;
   int Ic[3] = {0, 0, 0};
-  for (int a = 0; a < g.d; ++a) {
-    Ic[a] = (int)(r % g.nc[a]);
-    r /= g.nc[a];
-  }
+  ccoords(g, I, Ic);
   double acc = 0.0;
   for (int o = 0; o < S3; ++o) {
     int oo = o;
@@ -498,7 +506,7 @@ __global__ void k_coarse_tan_rhs(DevGeom g, const double* __restrict__ dAc,
       if (ja < 0 || ja >= g.nc[a]) ok = false;
       J += (long long)ja * g.cst[a];
     }
-    if (ok) acc = fma(dAc[I * S3 + o], t[(long long)j * g.Nc + J], acc);
+    if (ok) acc = fma(dAc[(long long)o * g.Nc + I], t[(long long)j * g.Nc + J], acc);
   }
   rhs[idx] = -acc;
 }
@@ -519,13 +527,14 @@ __global__ void k_band_build(DevGeom g, const double* __restrict__ Ac, long long
   const int S3 = stencil_size(g);
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= g.Nc * S3) return;
-  const long long I = idx / S3;
-  const int o = (int)(idx - I * S3);
-  long long r = I, J = 0;
+  const int o = (int)(idx / g.Nc);
+  const long long I = idx - (long long)o * g.Nc;
+  long long J = 0;
   int oo = o;
+  int Icc[3];
+  ccoords(g, I, Icc);
   for (int a = 0; a < g.d; ++a) {
-    const int ia = (int)(r % g.nc[a]);
-    r /= g.nc[a];
+    const int ia = Icc[a];
     const int ja = ia + (oo % 3) - 1;
     oo /= 3;
     if (ja < 0 || ja >= g.nc[a]) return;

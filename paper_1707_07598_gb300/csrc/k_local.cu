@@ -188,6 +188,35 @@ __device__ __forceinline__ double band_entry(const Loc& E, const Smem& sm, int n
   return v;
 }
 
+// Column update Z[i][j + sgn*k] -= col_k * Z[i][j] for k = 1..bj and the nvs
+// right-hand sides (forward: col = column j; backward: column j-k from the ring).
+// Two updates per trip, loads before stores, per-lane trip condition.
+template <int NT>
+__device__ __forceinline__ void sweep_update(const Smem& sm, int nmax, int nvs, int j, int bj,
+                                             int sgn, const double* col, int RB, int B1s,
+                                             int tid) {
+  const int nr = nvs * bj;
+  int it = tid;
+  for (; it + NT < nr; it += 2 * NT) {
+    const int i0 = it / bj, k0 = it - i0 * bj + 1;
+    const int i1 = (it + NT) / bj, k1 = it + NT - i1 * bj + 1;
+    const int o0 = i0 * nmax + j + sgn * k0, o1 = i1 * nmax + j + sgn * k1;
+    const double z0 = sm.Z[o0], z1 = sm.Z[o1];
+    const double x0 = sm.Z[i0 * nmax + j], x1 = sm.Z[i1 * nmax + j];
+    const double c0 = (sgn > 0) ? col[k0] : sm.W[((j - k0) % RB) * B1s + k0];
+    const double c1 = (sgn > 0) ? col[k1] : sm.W[((j - k1) % RB) * B1s + k1];
+    const double n0 = fma(-c0, x0, z0), n1 = fma(-c1, x1, z1);
+    sm.Z[o0] = n0;
+    sm.Z[o1] = n1;
+  }
+  if (it < nr) {
+    const int i0 = it / bj, k0 = it - i0 * bj + 1;
+    const int o0 = i0 * nmax + j + sgn * k0;
+    const double c0 = (sgn > 0) ? col[k0] : sm.W[((j - k0) % RB) * B1s + k0];
+    sm.Z[o0] = fma(-c0, sm.Z[i0 * nmax + j], sm.Z[o0]);
+  }
+}
+
 // Backward substitution L^T x = y (y in Z, already scaled by 1/d): for j = n-1..0,
 // x_j is final and Z[j-k] -= l_{j,j-k} x_j.  Row j of L lives in the b columns
 // before it, so the factor is streamed column by column into a ring of
@@ -214,13 +243,7 @@ __device__ void backward_sweep(const Loc& E, const Smem& sm, int nmax, int bmax,
     cp_wait<PD>();
     gsync<NT>();
     const int bj = min(b, j);
-    const int nr = nvs * bj;
-    for (int it = tid; it < nr; it += NT) {
-      const int i = it / bj, k = it - (it / bj) * bj + 1;
-      const double xj = sm.Z[(long long)i * nmax + j];
-      double* zp = sm.Z + (long long)i * nmax + j - k;
-      *zp = fma(-W[((j - k) % RB) * B1s + k], xj, *zp);
-    }
+    sweep_update<NT>(sm, nmax, nvs, j, bj, -1, nullptr, RB, B1s, tid);
   }
   cp_wait<0>();
   gsync<NT>();
@@ -255,13 +278,7 @@ __device__ void forward_sweep(const Loc& E, const Smem& sm, int nmax, int bmax,
       for (int i = tid; i < nvs; i += NT) sm.Z[(long long)i * nmax + j - 1] *= rdp;
     }
     const int bj = min(b, n - 1 - j);
-    const int nr = nvs * bj;
-    for (int it = tid; it < nr; it += NT) {
-      const int i = it / bj, k = it - (it / bj) * bj + 1;
-      const double zj = sm.Z[(long long)i * nmax + j];
-      double* zp = sm.Z + (long long)i * nmax + j + k;
-      *zp = fma(-Wj[k], zj, *zp);
-    }
+    sweep_update<NT>(sm, nmax, nvs, j, bj, +1, Wj, RB, B1s, tid);
   }
   cp_wait<0>();
   gsync<NT>();
@@ -317,23 +334,54 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short*
       *zp = z * rd;
     }
     gsync<NT>();
-    // phase B: rank-1 window update, fused forward substitution, next column in
+    // phase B: rank-1 window update, fused forward substitution, next column in.
+    // Two updates per trip, both loaded before either is stored; the trip condition
+    // is per lane, so warps whose lanes are all done never issue an FMA.
     const int np = bj * (bj + 1) / 2;
-    for (int it = tid; it < np; it += NT) {
-      const unsigned short pr = tab[it];
-      const int k1 = pr >> 8, k2 = pr & 255;
-      int slot = sj + k2;
-      if (slot >= B1) slot -= B1;
-      double* w = W + slot * B1s + (k1 - k2);
-      const double nw = fma(-sm.lvec[k1], sm.tvec[k2], *w);
-      *w = nw;
-      if (it == 0) sm.misc[(j + 1) & 1] = 1.0 / nw;  // diagonal of column j+1 is now final
+    {
+      int it = tid;
+      for (; it + NT < np; it += 2 * NT) {
+        const unsigned short p0 = tab[it], p1 = tab[it + NT];
+        int s0 = sj + (p0 & 255), s1 = sj + (p1 & 255);
+        if (s0 >= B1) s0 -= B1;
+        if (s1 >= B1) s1 -= B1;
+        const int o0 = s0 * B1s + ((p0 >> 8) - (p0 & 255));
+        const int o1 = s1 * B1s + ((p1 >> 8) - (p1 & 255));
+        const double w0 = W[o0], w1 = W[o1];
+        const double l0 = sm.lvec[p0 >> 8], l1 = sm.lvec[p1 >> 8];
+        const double t0 = sm.tvec[p0 & 255], t1 = sm.tvec[p1 & 255];
+        const double n0 = fma(-l0, t0, w0), n1 = fma(-l1, t1, w1);
+        W[o0] = n0;
+        W[o1] = n1;
+        if (it == 0) sm.misc[(j + 1) & 1] = 1.0 / n0;  // pair (1,1): diagonal of column j+1
+      }
+      if (it < np) {
+        const unsigned short p0 = tab[it];
+        int s0 = sj + (p0 & 255);
+        if (s0 >= B1) s0 -= B1;
+        const int o0 = s0 * B1s + ((p0 >> 8) - (p0 & 255));
+        const double n0 = fma(-sm.lvec[p0 >> 8], sm.tvec[p0 & 255], W[o0]);
+        W[o0] = n0;
+        if (it == 0) sm.misc[(j + 1) & 1] = 1.0 / n0;
+      }
     }
-    const int nr = nvs * bj;
-    for (int it = tid; it < nr; it += NT) {
-      const int i = it / bj, k = it - (it / bj) * bj + 1;
-      double* zp = sm.Z + (long long)i * nmax + j + k;
-      *zp = fma(-sm.lvec[k], sm.zj[i], *zp);
+    {
+      const int nr = nvs * bj;
+      int it = tid;
+      for (; it + NT < nr; it += 2 * NT) {
+        const int i0 = it / bj, k0 = it - i0 * bj + 1;
+        const int i1 = (it + NT) / bj, k1 = it + NT - i1 * bj + 1;
+        const int o0 = i0 * nmax + j + k0, o1 = i1 * nmax + j + k1;
+        const double z0 = sm.Z[o0], z1 = sm.Z[o1];
+        const double n0 = fma(-sm.lvec[k0], sm.zj[i0], z0), n1 = fma(-sm.lvec[k1], sm.zj[i1], z1);
+        sm.Z[o0] = n0;
+        sm.Z[o1] = n1;
+      }
+      if (it < nr) {
+        const int i0 = it / bj, k0 = it - i0 * bj + 1;
+        const int o0 = i0 * nmax + j + k0;
+        sm.Z[o0] = fma(-sm.lvec[k0], sm.zj[i0], sm.Z[o0]);
+      }
     }
     if (j + B1 < n)
       for (int k = tid; k < B1; k += NT) Wj[k] = (k <= b) ? band_entry(E, sm, nmax, j + B1, k) : 0.0;
@@ -367,7 +415,7 @@ __device__ __forceinline__ int mapped_slot(int s, int a, int dir) {
 // Basis (forward) kernel
 // -----------------------------------------------------------------------------
 template <int NT, int G>
-__global__ void __launch_bounds__(NT* G) k_local_fwd(DevGeom g, LocalLaunch L,
+__global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_fwd(DevGeom g, LocalLaunch L,
                                                      const double* __restrict__ T,
                                                      double* __restrict__ Pw,
                                                      double* __restrict__ fac, int* status) {
@@ -435,7 +483,7 @@ __global__ void __launch_bounds__(NT* G) k_local_fwd(DevGeom g, LocalLaunch L,
 // Adjoint kernel
 // -----------------------------------------------------------------------------
 template <int NT, int G>
-__global__ void __launch_bounds__(NT* G) k_local_adj(DevGeom g, LocalLaunch L,
+__global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_adj(DevGeom g, LocalLaunch L,
                                                      const double* __restrict__ T,
                                                      const double* __restrict__ Pw,
                                                      const double* __restrict__ fac,
@@ -555,7 +603,7 @@ __global__ void __launch_bounds__(NT* G) k_local_adj(DevGeom g, LocalLaunch L,
 // Tangent kernel
 // -----------------------------------------------------------------------------
 template <int NT, int G>
-__global__ void __launch_bounds__(NT* G) k_local_tan(DevGeom g, LocalLaunch L,
+__global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_tan(DevGeom g, LocalLaunch L,
                                                      const double* __restrict__ T,
                                                      const double* __restrict__ Dl,
                                                      const double* __restrict__ v,

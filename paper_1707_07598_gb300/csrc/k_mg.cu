@@ -1,0 +1,938 @@
+// Coarse solve of step (e) for larger coarse meshes: right-preconditioned GMRES
+// with a geometric multigrid V-cycle on the 3^d-point coarse operator A_c = R A P.
+//
+// The reduced system of Eq. fwdProbRed / reducedPDE with the gauge "coarse unknown
+// 0 fixed to zero" (Sec. 2.2) is solved as the consistent singular system
+// A_c t = b - (sum b) e_0 followed by t -= t_0 (A_c has constant null vectors on
+// both sides because R sums cells and P reproduces constants), which gives exactly
+// the pinned solution.  The transposed systems of the adjoint use A_c^T the same way.
+//
+// All stencil matrices are stored offset-major (A[s * n + i]), so that row-parallel
+// reads of one offset are contiguous for A and for A^T alike.
+// Multigrid: vertex-centred coarsening by 2 per axis (coarse node K = fine node 2K),
+// (bi/tri)linear prolongation P, restriction P^T, Galerkin levels P^T A P (they keep
+// the 3^d stencil), V(2,2) cycles with damped Jacobi, the coarsest level (<= 2 nodes
+// per axis) solved exactly with a pinned dense inverse.  A_c^T uses the transposed
+// stencils of the same hierarchy.
+//
+// GB300 mapping: one thread-block cluster per right-hand side, one 512-thread CTA per
+// SM; the cluster size (<= 8) is the largest whose co-resident clusters cover all
+// right-hand sides in one wave.  Level 0 is spread over the cluster (hardware cluster
+// barriers, reductions through distributed shared memory, staged halos); levels >= 1
+// run inside CTA 0 from shared memory.  All
+// synchronisation is the hardware cluster barrier (no software spin-waits); dot
+// products are reduced through distributed shared memory in a fixed order, so the
+// result is deterministic.  Vectors live in global memory (L2-resident) and are read
+// with ld.global.cg across CTAs of a cluster.  All arithmetic is FP64.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "msfv_internal.h"
+
+namespace cg = cooperative_groups;
+
+
+namespace msfv {
+
+namespace {
+
+constexpr int NTH = 512;      // threads per CTA (one CTA per SM)
+
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+// 1D interpolation weight of coarse node K at fine node i.
+__device__ __forceinline__ double pw1(int i, int K, int gc, int coarsened) {
+  if (!coarsened) return i == K ? 1.0 : 0.0;
+  if ((i & 1) == 0) return (K == (i >> 1)) ? 1.0 : 0.0;
+  const int lo = (i - 1) >> 1, hi = (i + 1) >> 1;
+  if (hi < gc) return (K == lo || K == hi) ? 0.5 : 0.0;
+  return K == lo ? 1.0 : 0.0;
+}
+
+// index -> coordinates; 32-bit arithmetic (coarse levels hold < 2^31 nodes)
+__device__ __forceinline__ void dec(long long i, const int* g, int* c) {
+  const unsigned u = (unsigned)i, g0 = (unsigned)g[0], g1 = (unsigned)g[1];
+  const unsigned r = u / g0;
+  c[0] = (int)(u - r * g0);
+  const unsigned q = r / g1;
+  c[1] = (int)(r - q * g1);
+  c[2] = (int)q;
+}
+
+__device__ __forceinline__ long long enc(const int* c, const int* g) {
+  return c[0] + (long long)g[0] * (c[1] + (long long)g[1] * c[2]);
+}
+
+}  // namespace
+
+// ---- hierarchy set-up ---------------------------------------------------------------
+// A_{l+1}[K][o] = sum_{i in supp K} P[i,K] sum_{i' in supp(K+o), |i'-i| <= 1} A_l[i][i'-i] P[i',K+o]
+__global__ void k_mg_galerkin(MGLevelDev f, MGLevelDev c, int d) {
+  const int S3 = (d == 3) ? 27 : 9;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= c.n * S3) return;
+  const int oi = (int)(idx / c.n);
+  const long long K = idx - (long long)oi * c.n;
+  int Kc[3], J[3];
+  dec(K, c.g, Kc);
+  {
+    int r = oi;
+    for (int a = 0; a < 3; ++a) {
+      J[a] = Kc[a] + ((a < d) ? (r % 3) - 1 : 0);
+      r /= 3;
+    }
+  }
+  double acc = 0.0;
+  bool ok = true;
+  for (int a = 0; a < 3; ++a)
+    if (J[a] < 0 || J[a] >= c.g[a]) ok = false;
+  if (ok) {
+    int lo[3], hi[3], lj[3], hj[3];
+    for (int a = 0; a < 3; ++a) {
+      if (f.coarsened[a]) {
+        lo[a] = max(0, 2 * Kc[a] - 1);
+        hi[a] = min(f.g[a] - 1, 2 * Kc[a] + 1);
+        lj[a] = max(0, 2 * J[a] - 1);
+        hj[a] = min(f.g[a] - 1, 2 * J[a] + 1);
+      } else {
+        lo[a] = hi[a] = Kc[a];
+        lj[a] = hj[a] = J[a];
+      }
+    }
+    int ic[3], jc[3];
+    for (ic[2] = lo[2]; ic[2] <= hi[2]; ++ic[2])
+      for (ic[1] = lo[1]; ic[1] <= hi[1]; ++ic[1])
+        for (ic[0] = lo[0]; ic[0] <= hi[0]; ++ic[0]) {
+          double wi = 1.0;
+          for (int a = 0; a < 3; ++a) wi *= pw1(ic[a], Kc[a], c.g[a], f.coarsened[a]);
+          if (wi == 0.0) continue;
+          const long long i = enc(ic, f.g);
+          int l2[3], h2[3];
+          for (int a = 0; a < 3; ++a) {
+            l2[a] = max(lj[a], ic[a] - 1);
+            h2[a] = min(hj[a], ic[a] + 1);
+          }
+          for (jc[2] = l2[2]; jc[2] <= h2[2]; ++jc[2])
+            for (jc[1] = l2[1]; jc[1] <= h2[1]; ++jc[1])
+              for (jc[0] = l2[0]; jc[0] <= h2[0]; ++jc[0]) {
+                double wj = 1.0;
+                for (int a = 0; a < 3; ++a) wj *= pw1(jc[a], J[a], c.g[a], f.coarsened[a]);
+                if (wj == 0.0) continue;
+                const int s = (jc[0] - ic[0] + 1) + 3 * (jc[1] - ic[1] + 1) +
+                              ((d == 3) ? 9 * (jc[2] - ic[2] + 1) : 0);
+                acc = fma(wi * wj, f.A[(long long)s * f.n + i], acc);
+              }
+        }
+  }
+  c.A[idx] = acc;
+}
+
+__global__ void k_mg_dinv(MGLevelDev L, int d) {
+  const int S3 = (d == 3) ? 27 : 9, ctr = S3 / 2;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  const double a = L.A[(long long)ctr * L.n + i];
+  L.dinv[i] = (a != 0.0) ? 1.0 / a : 0.0;
+}
+
+// Dense inverses of the pinned coarsest matrix (row 0 replaced by e_0) and of its
+// transposed counterpart (<= 8 unknowns): one warp, lane j holds column j of the
+// augmented matrix [M | I]; Gauss-Jordan with partial pivoting.
+__global__ void k_mg_coarsest(MGLevelDev L, int d, double* inv, double* invT, int* status) {
+  const int lane = threadIdx.x;
+  const int S3 = (d == 3) ? 27 : 9;
+  const int n = (int)L.n;
+  for (int tr = 0; tr < 2; ++tr) {
+    double col[8];
+    for (int i = 0; i < 8; ++i) col[i] = 0.0;
+    if (lane < n) {
+      // column 'lane' of M (or of M^T): entries M[i][lane]
+      for (int i = 0; i < n; ++i) {
+        const int row = tr ? lane : i, cj = tr ? i : lane;  // M^T[i][lane] = M[lane][i]
+        int ic[3];
+        dec(row, L.g, ic);
+        double v = 0.0;
+        for (int s = 0; s < S3; ++s) {
+          int r = s, nb[3];
+          bool in = true;
+          for (int a = 0; a < 3; ++a) {
+            const int oo = (a < d) ? (r % 3) - 1 : 0;
+            r /= 3;
+            nb[a] = ic[a] + oo;
+            if (nb[a] < 0 || nb[a] >= L.g[a]) in = false;
+          }
+          if (in && (int)enc(nb, L.g) == cj) v += L.A[(long long)s * L.n + row];
+        }
+        col[i] = v;
+      }
+      col[0] = (lane == 0) ? 1.0 : 0.0;  // pinned row
+    } else if (lane < 2 * n) {
+      col[lane - n] = 1.0;
+    }
+    for (int k = 0; k < n; ++k) {
+      int p = k;
+      double best = -1.0;
+      if (lane == k)
+        for (int i = k; i < n; ++i)
+          if (fabs(col[i]) > best) {
+            best = fabs(col[i]);
+            p = i;
+          }
+      p = __shfl_sync(0xffffffffu, p, k);
+      best = __shfl_sync(0xffffffffu, best, k);
+      if (best == 0.0) {
+        if (lane == 0) *status = 1;
+        return;
+      }
+      if (p != k) {
+        const double t = col[k];
+        col[k] = col[p];
+        col[p] = t;
+      }
+      const double piv = __shfl_sync(0xffffffffu, col[k], k);
+      const double rp = 1.0 / piv;
+      col[k] *= rp;
+      for (int i = 0; i < n; ++i) {
+        const double fk = __shfl_sync(0xffffffffu, col[i], k);  // entry (i, k)
+        if (i != k) col[i] = fma(-fk, col[k], col[i]);
+      }
+    }
+    double* out = tr ? invT : inv;
+    if (lane >= n && lane < 2 * n)
+      for (int i = 0; i < n; ++i) out[i * 8 + (lane - n)] = col[i];
+  }
+}
+
+// ---- the solver ----------------------------------------------------------------------
+namespace {
+
+constexpr int MAXM = 24;          // GMRES restart length bound
+constexpr int STAGE_CAP = 6144;   // doubles of shared memory for a staged level-0 range
+constexpr int CSM_CAP = 21500;    // doubles of shared memory for levels >= 1 (one CTA)
+
+struct Ctx {
+  int rank;          // CTA rank in its cluster
+  int G;             // CTAs per cluster (one cluster per right-hand side)
+  int tid;
+  double* red;       // 9 x NTH doubles of transpose-reduction scratch (aliases stage)
+  double* stage;     // STAGE_CAP doubles (shared)
+  double* cs;        // CSM_CAP doubles for the coarse levels (shared, rank 0)
+  double* part;      // 2 x 32 partial sums of this CTA (shared, read by the cluster)
+  cg::cluster_group cl;
+  int buf;
+  long long* trace;
+  int trace_cap;
+  int tag;
+  bool trace_on;
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Cluster barrier (hardware; release/acquire at cluster scope, plus a device fence
+// for the global-memory vectors read with ld.global.cg by the other CTAs).
+__device__ __forceinline__ void gsync(Ctx& c) {
+  __threadfence();
+  c.cl.sync();
+  if (c.trace_on && c.tid == 0) {
+    const long long n = c.trace[0];
+    if (n + 1 < c.trace_cap) {
+      c.trace[n + 1] = ((long long)c.tag << 48) | (long long)(gtimer() & 0xffffffffffffULL);
+      c.trace[0] = n + 1;
+    }
+  }
+}
+
+__device__ __forceinline__ void chunk(long long n, int rank, int G, long long& b, long long& e) {
+  const long long per = (n + G - 1) / G;
+  b = min(n, per * rank);
+  e = min(n, b + per);
+}
+
+// A view of a vector: a staged shared-memory copy of [lo, hi) or global memory.
+struct Vec {
+  const double* sm;
+  const double* g;
+  long long lo;
+  __device__ __forceinline__ double operator[](long long j) const {
+    return sm ? sm[j - lo] : ldcg(g + j);
+  }
+};
+
+__device__ __forceinline__ Vec stage_range(Ctx& c, const double* src, long long lo, long long hi,
+                                           long long n, const double* scale = nullptr,
+                                           double om = 0.0) {
+  lo = max(0LL, lo);
+  hi = min(n, hi);
+  Vec v{nullptr, src, lo};
+  __syncthreads();
+  if (hi - lo <= STAGE_CAP && hi > lo) {
+    for (long long j = lo + c.tid; j < hi; j += NTH) {
+      double x = ldcg(src + j);
+      if (scale) x *= om * scale[j];
+      c.stage[j - lo] = x;
+    }
+    __syncthreads();
+    v.sm = c.stage;
+  }
+  return v;
+}
+
+__device__ __forceinline__ long long halo(const MGLevelDev& L) {
+  return (long long)L.g[0] * L.g[1] + L.g[0] + 1;
+}
+
+template <int D, class X>
+__device__ __forceinline__ double apply_row(const MGLevelDev& L, int tr, long long i, const X& x) {
+  constexpr int S3 = (D == 3) ? 27 : 9;
+  int ic[3];
+  dec(i, L.g, ic);
+  const long long sy = L.g[0], sz = (long long)L.g[0] * L.g[1];
+  double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int s = 0; s < S3; ++s) {
+    const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = (D == 3) ? s / 9 - 1 : 0;
+    const bool in = (unsigned)(ic[0] + ox) < (unsigned)L.g[0] &&
+                    (unsigned)(ic[1] + oy) < (unsigned)L.g[1] &&
+                    (D == 2 || (unsigned)(ic[2] + oz) < (unsigned)L.g[2]);
+    if (in) {
+      const long long j = i + ox + oy * sy + oz * sz;
+      const double a = tr ? L.A[(long long)(S3 - 1 - s) * L.n + j] : L.A[(long long)s * L.n + i];
+      acc[s % 3] = fma(a, x[j], acc[s % 3]);
+    }
+  }
+  return (acc[0] + acc[1]) + acc[2];
+}
+
+template <int D, class X>
+__device__ __forceinline__ double restrict_row(const MGLevelDev& L, const MGLevelDev& C,
+                                               long long K, const X& s) {
+  int Kc[3];
+  dec(K, C.g, Kc);
+  const long long sy = L.g[0], sz = (long long)L.g[0] * L.g[1];
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < ((D == 3) ? 27 : 9); ++q) {
+    const int o[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+    int ic[3];
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= D) {
+        ic[a] = 0;
+        continue;
+      }
+      ic[a] = L.coarsened[a] ? 2 * Kc[a] + o[a] : Kc[a] + o[a];
+      if (!L.coarsened[a] && o[a] != 0) in = false;
+      if ((unsigned)ic[a] >= (unsigned)L.g[a]) in = false;
+    }
+    if (in) {
+      double wt = 1.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) wt *= pw1(ic[a], Kc[a], C.g[a], L.coarsened[a]);
+      acc = fma(wt, s[ic[0] + ic[1] * sy + ic[2] * sz], acc);
+    }
+  }
+  return acc;
+}
+
+template <int D, class X>
+__device__ __forceinline__ double prolong_row(const MGLevelDev& L, const MGLevelDev& C,
+                                              long long i, const X& xc) {
+  int ic[3];
+  dec(i, L.g, ic);
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < ((D == 3) ? 8 : 4); ++q) {
+    int K[3];
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= D) {
+        K[a] = 0;
+        continue;
+      }
+      const int bit = (q >> a) & 1;
+      if (L.coarsened[a]) {
+        K[a] = (ic[a] >> 1) + bit;
+        if (bit && !(ic[a] & 1)) in = false;
+      } else {
+        K[a] = ic[a];
+        if (bit) in = false;
+      }
+      if (K[a] >= C.g[a]) in = false;
+    }
+    if (in) {
+      double wt = 1.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) wt *= pw1(ic[a], K[a], C.g[a], L.coarsened[a]);
+      acc = fma(wt, xc[K[0] + (long long)C.g[0] * (K[1] + (long long)C.g[1] * K[2])], acc);
+    }
+  }
+  return acc;
+}
+
+// shared-memory vector view for the coarse levels
+struct SVec {
+  const double* p;
+  __device__ __forceinline__ double operator[](long long j) const { return p[j]; }
+};
+
+// Block-wide sums of NV per-thread values (transposed through shared memory, each
+// partial added once); results land in out[0..NV) for thread k < NV.
+template <int NV>
+__device__ __forceinline__ void block_sums(Ctx& c, const double (&vals)[NV], double* out) {
+  static_assert(NV <= 32, "NV <= 32");
+  constexpr int SEG = NTH / 32;
+#pragma unroll
+  for (int g0 = 0; g0 < NV; g0 += 8) {
+    const int ng = (NV - g0 < 8) ? NV - g0 : 8;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < ng) c.red[k * NTH + c.tid] = vals[g0 + k];
+    __syncthreads();
+    if (c.tid < ng * SEG) {
+      const int k = c.tid / SEG, sg = c.tid - (c.tid / SEG) * SEG;
+      const double* p = c.red + k * NTH + sg * 32;
+      double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 32; q += 2) {
+        s0 += p[q];
+        s1 += p[q + 1];
+      }
+      c.red[8 * NTH + c.tid] = s0 + s1;
+    }
+    __syncthreads();
+    if (c.tid < ng) {
+      const double* p = c.red + 8 * NTH + c.tid * SEG;
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < SEG; ++q) s += p[q];
+      out[g0 + c.tid] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Cluster-wide sums: block sums -> this CTA's shared partials -> cluster barrier ->
+// every CTA adds the G partials in rank order through distributed shared memory
+// (deterministic).  Partial buffers alternate; two reductions apart there is always
+// a barrier.
+template <int NV>
+__device__ __forceinline__ void all_reduce(Ctx& c, const double (&vals)[NV], double* tot) {
+  block_sums<NV>(c, vals, tot);
+  if (c.tid < NV) c.part[c.buf * 32 + c.tid] = tot[c.tid];
+  gsync(c);
+  if (c.tid < NV) {
+    double v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      v[r] = (r < c.G) ? c.cl.map_shared_rank(c.part, r)[c.buf * 32 + c.tid] : 0.0;
+    double sacc = 0.0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sacc += v[r];
+    tot[c.tid] = sacc;
+  }
+  c.buf ^= 1;
+  __syncthreads();
+}
+
+template <int K>
+__device__ __noinline__ void gram_schmidt(Ctx& c, double* V, long long n0, long long b,
+                                          long long e, double* w, double* tot,
+                                          double (*H)[MAXM], double* hn_out) {
+  double hp[K + 1];
+#pragma unroll
+  for (int q = 0; q <= K; ++q) hp[q] = 0.0;
+  for (long long i = b + c.tid; i < e; i += NTH) {
+    const double wi = w[i];
+#pragma unroll
+    for (int q = 0; q <= K; ++q) hp[q] = fma(V[(long long)q * n0 + i], wi, hp[q]);
+  }
+  all_reduce<K + 1>(c, hp, tot);
+  if (c.tid <= K) H[c.tid][K] = tot[c.tid];
+  double h2[K + 2];
+#pragma unroll
+  for (int q = 0; q <= K + 1; ++q) h2[q] = 0.0;
+  for (long long i = b + c.tid; i < e; i += NTH) {
+    double wi = w[i];
+#pragma unroll
+    for (int q = 0; q <= K; ++q) wi = fma(-tot[q], V[(long long)q * n0 + i], wi);
+    w[i] = wi;
+#pragma unroll
+    for (int q = 0; q <= K; ++q) h2[q] = fma(V[(long long)q * n0 + i], wi, h2[q]);
+    h2[K + 1] = fma(wi, wi, h2[K + 1]);
+  }
+  all_reduce<K + 2>(c, h2, tot);
+  if (c.tid <= K) H[c.tid][K] += tot[c.tid];
+  double hh = 0.0;
+#pragma unroll
+  for (int q = 0; q <= K; ++q) hh = fma(tot[q], tot[q], hh);
+  const double hn = sqrt(fmax(tot[K + 1] - hh, 0.0));
+  const double ihn = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (long long i = b + c.tid; i < e; i += NTH) {
+    double wi = w[i];
+#pragma unroll
+    for (int q = 0; q <= K; ++q) wi = fma(-tot[q], V[(long long)q * n0 + i], wi);
+    w[i] = wi * ihn;
+  }
+  *hn_out = hn;
+}
+
+// Levels >= 1 of the V-cycle inside one CTA, vectors in shared memory.
+// in: rs (level-1 right-hand side); out: xs (level-1 correction).
+template <int D>
+__device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV, double* mem) {
+  const int tr = P.transpose;
+  const double om = P.omega;
+  // per level l >= 1: r, x, s at offsets off[l] (3 n_l doubles each)
+  long long off[kMaxLevels];
+  long long o = 0;
+  for (int l = 1; l < P.nlev; ++l) {
+    off[l] = o;
+    o += 3 * LV[l].n;
+  }
+  for (int l = 1; l < P.nlev - 1; ++l) {
+    const MGLevelDev& L = LV[l];
+    double* r = mem + off[l];
+    double* x = r + L.n;
+    double* s = x + L.n;
+    for (long long i = c.tid; i < L.n; i += NTH) s[i] = om * L.dinv[i] * r[i];
+    __syncthreads();
+    for (long long i = c.tid; i < L.n; i += NTH)
+      x[i] = fma(om * L.dinv[i], r[i] - apply_row<D>(L, tr, i, SVec{s}), s[i]);
+    __syncthreads();
+    for (long long i = c.tid; i < L.n; i += NTH) s[i] = r[i] - apply_row<D>(L, tr, i, SVec{x});
+    __syncthreads();
+    const MGLevelDev& C = LV[l + 1];
+    double* rc = mem + off[l + 1];
+    for (long long K = c.tid; K < C.n; K += NTH) rc[K] = restrict_row<D>(L, C, K, SVec{s});
+    __syncthreads();
+  }
+  {
+    const MGLevelDev& L = LV[P.nlev - 1];
+    double* r = mem + off[P.nlev - 1];
+    double* x = r + L.n;
+    const double* inv = tr ? P.invT : P.inv;
+    const int n = (int)L.n;
+    if (c.tid < n) {
+      double acc = 0.0;
+      for (int j = 1; j < n; ++j) acc = fma(inv[c.tid * 8 + j], r[j], acc);
+      x[c.tid] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = P.nlev - 2; l >= 1; --l) {
+    const MGLevelDev& L = LV[l];
+    const MGLevelDev& C = LV[l + 1];
+    double* r = mem + off[l];
+    double* x = r + L.n;
+    double* s = x + L.n;
+    const double* xc = mem + off[l + 1] + C.n;
+    for (long long i = c.tid; i < L.n; i += NTH) x[i] += prolong_row<D>(L, C, i, SVec{xc});
+    __syncthreads();
+    for (long long i = c.tid; i < L.n; i += NTH)
+      s[i] = fma(om * L.dinv[i], r[i] - apply_row<D>(L, tr, i, SVec{x}), x[i]);
+    __syncthreads();
+    for (long long i = c.tid; i < L.n; i += NTH)
+      x[i] = fma(om * L.dinv[i], r[i] - apply_row<D>(L, tr, i, SVec{s}), s[i]);
+    __syncthreads();
+  }
+}
+
+// Full V(2,2) cycle, x_0 ~= M^{-1} r_0.  Level 0 is spread over the group; levels >= 1
+// run inside CTA 0 of the group (shared memory) when they fit, else on the group.
+template <int D>
+__device__ __forceinline__ void vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV,
+                                       const double* r0, double* x0, double* s0, double* x1g) {
+  const int tr = P.transpose;
+  const double om = P.omega;
+  const MGLevelDev& L = P.lev[0];
+  long long b, e;
+  chunk(L.n, c.rank, c.G, b, e);
+  const long long H = halo(L);
+  if (P.nlev == 1) {
+    // coarsest only: dense pinned solve by every CTA of its own rows
+    const double* inv = tr ? P.invT : P.inv;
+    for (long long i = b + c.tid; i < e; i += NTH) {
+      double acc = 0.0;
+      for (int j = 1; j < (int)L.n; ++j) acc = fma(inv[i * 8 + j], ldcg(r0 + j), acc);
+      x0[i] = acc;
+    }
+    c.tag = 1;
+    gsync(c);
+    return;
+  }
+  const MGLevelDev& C = P.lev[1];
+  c.tag = 2;
+  {
+    const Vec y = stage_range(c, r0, b - H, e + H, L.n, L.dinv, om);
+    for (long long i = b + c.tid; i < e; i += NTH) {
+      const double ri = ldcg(r0 + i);
+      x0[i] = fma(om * L.dinv[i], ri - apply_row<D>(L, tr, i, y), y[i]);
+    }
+  }
+  gsync(c);
+  c.tag = 3;
+  {
+    const Vec xv = stage_range(c, x0, b - H, e + H, L.n);
+    for (long long i = b + c.tid; i < e; i += NTH) s0[i] = ldcg(r0 + i) - apply_row<D>(L, tr, i, xv);
+  }
+  gsync(c);
+  // restriction: CTA 0 gathers the whole level-1 right-hand side into shared memory
+  // and runs the coarse levels there
+  c.tag = 4;
+  if (c.rank == 0) {
+    double* r1 = c.cs;
+    for (long long K = c.tid; K < C.n; K += NTH) r1[K] = restrict_row<D>(L, C, K, Vec{nullptr, s0, 0});
+    __syncthreads();
+    coarse_vcycle<D>(c, P, LV, c.cs);
+    const double* x1 = c.cs + C.n;
+    for (long long K = c.tid; K < C.n; K += NTH) x1g[K] = x1[K];
+  }
+  gsync(c);
+  c.tag = 5;
+  {
+    long long clo = 0, chi = 0;
+    if (e > b) {
+      int i0[3], i1[3], c0[3], c1[3];
+      dec(b, L.g, i0);
+      dec(e - 1, L.g, i1);
+      for (int a = 0; a < 3; ++a) {
+        const int lo_f = (a == 2) ? i0[2] : 0, hi_f = (a == 2) ? i1[2] : L.g[a] - 1;
+        c0[a] = L.coarsened[a] ? (lo_f >> 1) : lo_f;
+        c1[a] = L.coarsened[a] ? min(C.g[a] - 1, (hi_f + 1) >> 1) : hi_f;
+      }
+      clo = enc(c0, C.g);
+      chi = enc(c1, C.g) + 1;
+    }
+    const Vec cv = stage_range(c, x1g, clo, chi, C.n);
+    for (long long i = b + c.tid; i < e; i += NTH) x0[i] = ldcg(x0 + i) + prolong_row<D>(L, C, i, cv);
+  }
+  gsync(c);
+  c.tag = 6;
+  {
+    const Vec xv = stage_range(c, x0, b - H, e + H, L.n);
+    for (long long i = b + c.tid; i < e; i += NTH)
+      s0[i] = fma(om * L.dinv[i], ldcg(r0 + i) - apply_row<D>(L, tr, i, xv), xv[i]);
+  }
+  gsync(c);
+  c.tag = 7;
+  {
+    const Vec sv = stage_range(c, s0, b - H, e + H, L.n);
+    for (long long i = b + c.tid; i < e; i += NTH)
+      x0[i] = fma(om * L.dinv[i], ldcg(r0 + i) - apply_row<D>(L, tr, i, sv), sv[i]);
+  }
+  gsync(c);
+}
+
+}  // namespace
+
+#define MSFV_GS_CASE(K)                                                 \
+  case K:                                                               \
+    gram_schmidt<K>(c, V, n0, b, e, w, tot, H, &hn);                    \
+    break;
+
+template <int D>
+__global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
+  extern __shared__ double dyn[];
+  __shared__ double tot[64];
+  __shared__ double part[64];
+  __shared__ double H[MAXM + 1][MAXM];
+  __shared__ double gv[MAXM + 1], cs[MAXM], sn[MAXM], yv[MAXM];
+  Ctx c{0, 0, (int)threadIdx.x, dyn, dyn, dyn + STAGE_CAP, part, cg::this_cluster(), 0,
+        P.trace, P.trace_cap, 0, false};
+  const int G = (int)c.cl.num_blocks();
+  c.rank = (int)c.cl.block_rank();
+  c.G = G;
+  const int grp = blockIdx.x / G, ngrp = gridDim.x / G;
+  c.trace_on = (P.trace != nullptr) && grp == 0 && c.rank == 0;
+  const MGLevelDev& L0 = P.lev[0];
+  const long long n0 = L0.n;
+  const long long H0 = halo(L0);
+  const int m = min(P.m, MAXM);
+  long long b, e;
+  chunk(n0, c.rank, G, b, e);
+  // levels >= 1 for CTA 0: vectors first, then (when they fit) the stencils and
+  // diagonals copied into shared memory
+  MGLevelDev LV[kMaxLevels];
+  {
+    const int S3 = (D == 3) ? 27 : 9;
+    long long vec = 0, mat = 0;
+    for (int l = 0; l < P.nlev; ++l) {
+      LV[l] = P.lev[l];
+      if (l >= 1) {
+        vec += 3 * P.lev[l].n;
+        mat += P.lev[l].n * (S3 + 1);
+      }
+    }
+    if (c.rank == 0 && vec + mat <= CSM_CAP) {
+      double* q = c.cs + vec;
+      for (int l = 1; l < P.nlev; ++l) {
+        const long long na = P.lev[l].n * S3, nd = P.lev[l].n;
+        for (long long t = c.tid; t < na; t += NTH) q[t] = P.lev[l].A[t];
+        for (long long t = c.tid; t < nd; t += NTH) q[na + t] = P.lev[l].dinv[t];
+        LV[l].A = q;
+        LV[l].dinv = q + na;
+        q += na + nd;
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = grp; j < P.Ns; j += ngrp) {
+    double* base = P.ws + (long long)j * P.rhs_stride;
+    double* V = base;                          // (m+1) x n0
+    double* Z = V + (long long)(P.m + 1) * n0; // m x n0
+    double* bh = Z + (long long)P.m * n0;      // n0
+    double* s0 = bh + n0;                      // n0
+    double* x1g = s0 + n0;                     // level-1 correction (n_1)
+    double* x = P.rhs + (long long)j * n0;     // solution, in place of b
+    {
+      double hp[2] = {0.0, 0.0};
+      for (long long i = b + c.tid; i < e; i += NTH) {
+        const double v = x[i];
+        bh[i] = v;
+        hp[0] += v;
+        hp[1] = fma(v, v, hp[1]);
+      }
+      all_reduce<2>(c, hp, tot);
+    }
+    const double sumb = tot[0];
+    const double b0 = ldcg(bh + 0);
+    const double nb = sqrt(fmax(tot[1] - b0 * b0 + (b0 - sumb) * (b0 - sumb), 0.0));
+    c.tag = 0;
+    gsync(c);  // everyone has read bh[0]
+    if (c.rank == 0 && c.tid == 0) bh[0] = b0 - sumb;
+    for (long long i = b + c.tid; i < e; i += NTH) x[i] = 0.0;
+    gsync(c);
+    int status = 0, iters = 0;
+    if (nb > 0.0) {
+      status = 2;
+      for (int cyc = 0; cyc <= P.max_cycles; ++cyc) {
+        {
+          double hp[1] = {0.0};
+          const Vec xv = stage_range(c, x, b - H0, e + H0, n0);
+          for (long long i = b + c.tid; i < e; i += NTH) {
+            const double r = ldcg(bh + i) - apply_row<D>(L0, P.transpose, i, xv);
+            V[i] = r;
+            hp[0] = fma(r, r, hp[0]);
+          }
+          all_reduce<1>(c, hp, tot);
+        }
+        const double beta = sqrt(tot[0]);
+        if (beta <= P.tol_true * nb) {
+          status = 0;
+          break;
+        }
+        if (cyc == P.max_cycles) break;
+        if (c.tid == 0) {
+          gv[0] = beta;
+          for (int k = 1; k <= m; ++k) gv[k] = 0.0;
+        }
+        const double ib = 1.0 / beta;
+        for (long long i = b + c.tid; i < e; i += NTH) V[i] *= ib;
+        c.tag = 80;
+        gsync(c);
+        int kk = 0;
+        for (int k = 0; k < m; ++k) {
+          double* vk = V + (long long)k * n0;
+          double* zk = Z + (long long)k * n0;
+          double* w = V + (long long)(k + 1) * n0;
+          vcycle<D>(c, P, LV, vk, zk, s0, x1g);
+          ++iters;
+          c.tag = 90;
+          {
+            const Vec zv = stage_range(c, zk, b - H0, e + H0, n0);
+            for (long long i = b + c.tid; i < e; i += NTH) w[i] = apply_row<D>(L0, P.transpose, i, zv);
+          }
+          __syncthreads();
+          double hn = 0.0;
+          switch (k) {
+            MSFV_GS_CASE(0) MSFV_GS_CASE(1) MSFV_GS_CASE(2) MSFV_GS_CASE(3) MSFV_GS_CASE(4)
+            MSFV_GS_CASE(5) MSFV_GS_CASE(6) MSFV_GS_CASE(7) MSFV_GS_CASE(8) MSFV_GS_CASE(9)
+            MSFV_GS_CASE(10) MSFV_GS_CASE(11) MSFV_GS_CASE(12) MSFV_GS_CASE(13) MSFV_GS_CASE(14)
+            MSFV_GS_CASE(15) MSFV_GS_CASE(16) MSFV_GS_CASE(17) MSFV_GS_CASE(18) MSFV_GS_CASE(19)
+            MSFV_GS_CASE(20) MSFV_GS_CASE(21) MSFV_GS_CASE(22) MSFV_GS_CASE(23)
+            default:
+              break;
+          }
+          c.tag = 91;
+          gsync(c);  // w = V[k+1] normalised everywhere before the next V-cycle
+          if (c.tid == 0) {
+            H[k + 1][k] = hn;
+            for (int q = 0; q < k; ++q) {
+              const double t = cs[q] * H[q][k] + sn[q] * H[q + 1][k];
+              H[q + 1][k] = -sn[q] * H[q][k] + cs[q] * H[q + 1][k];
+              H[q][k] = t;
+            }
+            const double a = H[k][k], bb = H[k + 1][k];
+            const double rr = sqrt(a * a + bb * bb);
+            cs[k] = rr > 0.0 ? a / rr : 1.0;
+            sn[k] = rr > 0.0 ? bb / rr : 0.0;
+            H[k][k] = rr;
+            H[k + 1][k] = 0.0;
+            gv[k + 1] = -sn[k] * gv[k];
+            gv[k] = cs[k] * gv[k];
+          }
+          __syncthreads();
+          kk = k + 1;
+          if (fabs(gv[k + 1]) <= P.tol * nb || hn == 0.0) break;
+        }
+        if (c.tid == 0) {
+          for (int q = kk - 1; q >= 0; --q) {
+            double t = gv[q];
+            for (int p = q + 1; p < kk; ++p) t = fma(-H[q][p], yv[p], t);
+            yv[q] = t / H[q][q];
+          }
+        }
+        __syncthreads();
+        for (long long i = b + c.tid; i < e; i += NTH) {
+          double xi = x[i];
+          for (int q = 0; q < kk; ++q) xi = fma(yv[q], Z[(long long)q * n0 + i], xi);
+          x[i] = xi;
+        }
+        c.tag = 81;
+        gsync(c);
+      }
+      const double x0v = ldcg(x + 0);
+      gsync(c);
+      for (long long i = b + c.tid; i < e; i += NTH) x[i] -= x0v;
+    }
+    if (c.rank == 0 && c.tid == 0) {
+      if (status) P.status[j] = status;
+      if (P.iters) P.iters[j] = iters;
+    }
+    gsync(c);
+  }
+}
+#undef MSFV_GS_CASE
+
+// ---- host side -------------------------------------------------------------------------
+size_t mg_dyn_smem() { return sizeof(double) * (STAGE_CAP + CSM_CAP); }
+static_assert(9 * NTH <= STAGE_CAP, "reduction scratch must fit in the stage buffer");
+
+void mg_setup_levels(MGHost& H, const DevGeom& g) {
+  H.d = g.d;
+  H.nlev = 0;
+  int gd[3] = {g.nc[0], g.nc[1], g.d == 3 ? g.nc[2] : 1};
+  while (true) {
+    MGLevelDev& L = H.lev[H.nlev];
+    for (int a = 0; a < 3; ++a) L.g[a] = gd[a];
+    L.n = (long long)gd[0] * gd[1] * gd[2];
+    bool more = false;
+    for (int a = 0; a < 3; ++a) {
+      L.coarsened[a] = gd[a] > 2 ? 1 : 0;
+      if (L.coarsened[a]) more = true;
+    }
+    H.nlev++;
+    if (!more || H.nlev == kMaxLevels) {
+      for (int a = 0; a < 3; ++a) L.coarsened[a] = 0;
+      break;
+    }
+    for (int a = 0; a < 3; ++a) gd[a] = L.coarsened[a] ? (gd[a] + 1) / 2 : gd[a];
+  }
+}
+
+bool mg_coarse_fits(const MGHost& H) {
+  long long need = 0;
+  for (int l = 1; l < H.nlev; ++l) need += 3 * H.lev[l].n;
+  return need <= CSM_CAP;
+}
+
+void launch_mg_setup(const MGHost& H, int* status, cudaStream_t s) {
+  const int S3 = H.d == 3 ? 27 : 9;
+  for (int l = 0; l + 1 < H.nlev; ++l) {
+    const long long tot = H.lev[l + 1].n * S3;
+    k_mg_galerkin<<<(int)((tot + 127) / 128), 128, 0, s>>>(H.lev[l], H.lev[l + 1], H.d);
+  }
+  for (int l = 0; l < H.nlev; ++l)
+    k_mg_dinv<<<(int)((H.lev[l].n + 127) / 128), 128, 0, s>>>(H.lev[l], H.d);
+  k_mg_coarsest<<<1, 32, 0, s>>>(H.lev[H.nlev - 1], H.d, H.inv, H.invT, status);
+}
+
+// Largest cluster size <= 8 whose co-resident clusters (one CTA per SM) cover all Ns
+// right-hand sides in one wave; 0 if clusters cannot be launched at all.
+int mg_pick_cluster(int d, int Ns, int* max_clusters) {
+  const void* fn = (d == 3) ? (const void*)k_mg_gmres<3> : (const void*)k_mg_gmres<2>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mg_dyn_smem());
+  int best = 0, bestn = 0;
+  for (int cl = 8; cl >= 1; --cl) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cl, 1, 1);
+    cfg.blockDim = dim3(NTH, 1, 1);
+    cfg.dynamicSmemBytes = mg_dyn_smem();
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (best == 0) {
+      best = cl;
+      bestn = n;
+    }
+    if (n >= Ns) {
+      best = cl;
+      bestn = n;
+      break;
+    }
+  }
+  if (max_clusters) *max_clusters = bestn;
+  return best;
+}
+
+cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose, int* status,
+                            cudaStream_t s) {
+  MGParamsDev P;
+  P.d = H.d;
+  P.nlev = H.nlev;
+  for (int l = 0; l < H.nlev; ++l) P.lev[l] = H.lev[l];
+  P.inv = H.inv;
+  P.invT = H.invT;
+  P.m = H.m;
+  P.max_cycles = H.max_cycles;
+  P.tol = H.tol;
+  P.tol_true = H.tol_true;
+  P.omega = H.omega;
+  P.transpose = transpose;
+  P.ws = H.ws;
+  P.rhs_stride = H.rhs_stride;
+  P.rhs = rhs;
+  P.Ns = Ns;
+  P.status = status;
+  P.iters = H.iters;
+  P.trace = H.trace;
+  P.trace_cap = H.trace_cap;
+  const size_t dyn = mg_dyn_smem();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = H.group;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(H.group * H.ngroups, 1, 1);
+  cfg.blockDim = dim3(NTH, 1, 1);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (H.d == 3) {
+    cudaFuncSetAttribute(k_mg_gmres<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    return cudaLaunchKernelEx(&cfg, k_mg_gmres<3>, P);
+  }
+  cudaFuncSetAttribute(k_mg_gmres<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  return cudaLaunchKernelEx(&cfg, k_mg_gmres<2>, P);
+}
+
+}  // namespace msfv

@@ -139,4 +139,54 @@ void launch_band_factor(BandLU& B, cudaStream_t s);
 void launch_band_solve(const BandLU& B, double* rhs, int Ns, long long Nc, int transpose,
                        cudaStream_t s);
 
+// ---- multigrid-preconditioned GMRES coarse solver (k_mg.cu) -----------------------
+constexpr int kMaxLevels = 12;
+struct MGLevelDev {
+  int g[3];
+  int coarsened[3];     // 1 if this axis is coarsened to the next level
+  long long n;
+  double* A;            // 3^d x n stencil, offset-major: A[s * n + i]
+  double* dinv;         // n
+};
+struct MGHost {
+  int d = 0, nlev = 0;
+  MGLevelDev lev[kMaxLevels];
+  double* inv = nullptr;      // 8 x 8 pinned coarsest inverse
+  double* invT = nullptr;     // same for the transposed operator
+  int m = 24, max_cycles = 4;   // m <= 24 (register-resident Gram-Schmidt)
+  double tol = 1e-15, tol_true = 1e-13, omega = 0.85;
+  double* ws = nullptr;       // per right-hand side: V, Z, b_hat, scratch, level-1 correction
+  long long rhs_stride = 0;
+  int* iters = nullptr;       // per right-hand side: GMRES iterations of the last solve
+  long long* trace = nullptr; // optional: [0] = count, then (tag << 48 | ns) per barrier
+  int trace_cap = 0;
+  int group = 1, ngroups = 1; // cluster size (CTAs per right-hand side), clusters launched
+  int max_clusters = 0;       // co-resident clusters (occupancy API)
+};
+struct MGParamsDev {
+  int d, nlev;
+  MGLevelDev lev[kMaxLevels];
+  const double* inv;
+  const double* invT;
+  int m, max_cycles;
+  double tol, tol_true, omega;
+  int transpose;
+  double* ws;
+  long long rhs_stride;
+  double* rhs;
+  int Ns;
+  int* status;
+  int* iters;
+  long long* trace;
+  int trace_cap;
+};
+void mg_setup_levels(MGHost& H, const DevGeom& g);
+bool mg_coarse_fits(const MGHost& H);
+int mg_pick_cluster(int d, int Ns, int* max_clusters);
+void launch_mg_setup(const MGHost& H, int* status, cudaStream_t s);
+// rhs: Ns x Nc, solved in place (pinned: entry 0 of each solution is zero);
+// status[j] = 2 when right-hand side j did not converge.
+cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose, int* status,
+                            cudaStream_t s);
+
 }  // namespace msfv

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -84,7 +85,10 @@ struct msfv_session {
   int *rec_p = nullptr, *rec_u = nullptr;
   int* status = nullptr;
   BandLU band{};
+  MGHost mg{};
+  bool use_mg = false;
   bool have_forward = false;
+  cudaError_t launch_error = cudaSuccess;
   std::string err;
   // tracing
   bool prof = false;
@@ -163,7 +167,9 @@ void free_all(msfv_session* s) {
 }
 
 int check_launch(msfv_session* s, const char* where) {
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && s->launch_error != cudaSuccess) e = s->launch_error;
+  s->launch_error = cudaSuccess;
   if (e != cudaSuccess) return cuda_fail(s, e, where);
   return MSFV_OK;
 }
@@ -200,7 +206,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     Nc *= desc->n[a] / c;
   }
   if (Nc < 2) return fail(nullptr, MSFV_ERR_ARG, "need at least 2 coarse cells");
-  if (N > (1LL << 40)) return fail(nullptr, MSFV_ERR_ARG, "mesh too large");
+  if (N >= (1LL << 31)) return fail(nullptr, MSFV_ERR_ARG, "mesh too large (N must be < 2^31)");
   if (desc->n_src < 1 || !desc->src_pos || !desc->src_neg)
     return fail(nullptr, MSFV_ERR_ARG, "need n_src >= 1 and source arrays");
   if (desc->n_rec < 1 || !desc->rec_cell)
@@ -442,6 +448,22 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   s->band.ku = s->band.kl;
   s->band.ldab = 2 * s->band.kl + s->band.ku + 1;
 
+  // coarse solver: banded LU while its factorisation is small, else multigrid GMRES
+  {
+    const double band_work = (double)s->band.n * s->band.kl * (s->band.kl + s->band.ku);
+    s->use_mg = band_work > 1e7;
+    const char* env = getenv("MSFV_COARSE_SOLVER");
+    if (env && !strcmp(env, "band")) s->use_mg = false;
+    if (env && !strcmp(env, "mg")) s->use_mg = true;
+    if (s->use_mg) {
+      mg_setup_levels(s->mg, g);
+      if (!mg_coarse_fits(s->mg)) {
+        delete s;
+        return fail(nullptr, MSFV_ERR_ARG,
+                    "coarse mesh too large for the on-chip multigrid levels (Nc <= ~38000)");
+      }
+    }
+  }
   // ---- HBM budget and allocations --------------------------------------------------
   const int S3 = (d == 3) ? 27 : 9;
   const size_t Ssz = G.S;
@@ -450,7 +472,8 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
                 sizeof(double) * ((size_t)3 * Nc * S3 + (size_t)5 * s->Ns * Nc +
                                   (size_t)4 * s->Ns * s->Nr + 1 + (size_t)s->Ns * s->Nru +
                                   (size_t)s->Nru * Ssz + 2 * N) +
-                sizeof(double) * (size_t)s->band.ldab * (size_t)s->band.n;
+                (s->use_mg ? sizeof(double) * ((size_t)s->Ns * (2 * s->mg.m + 3) * Nc + 4 * Nc * S3)
+                           : sizeof(double) * (size_t)s->band.ldab * (size_t)s->band.n);
   if (desc->hbm_budget_bytes && need > desc->hbm_budget_bytes) {
     delete s;
     return fail(nullptr, MSFV_ERR_OOM, "session workspace exceeds hbm_budget_bytes");
@@ -487,10 +510,38 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   s->cj_s = dalloc<int>(s, cj_s.size(), &ce);
   s->rec_p = dalloc<int>(s, rec_p.size(), &ce);
   s->rec_u = dalloc<int>(s, rec_u.size(), &ce);
-  s->status = dalloc<int>(s, 2, &ce);
-  s->band.ab = dalloc<double>(s, (size_t)s->band.ldab * (size_t)s->band.n, &ce);
-  s->band.piv = dalloc<int>(s, (size_t)s->band.n, &ce);
+  s->status = dalloc<int>(s, 2 + (size_t)s->Ns, &ce);
   s->band.status = s->status + 1;
+  if (!s->use_mg) {
+    s->band.ab = dalloc<double>(s, (size_t)s->band.ldab * (size_t)s->band.n, &ce);
+    s->band.piv = dalloc<int>(s, (size_t)s->band.n, &ce);
+  } else {
+    MGHost& H = s->mg;
+    H.lev[0].A = s->Ac;
+    for (int l = 0; l < H.nlev; ++l) {
+      if (l > 0) H.lev[l].A = dalloc<double>(s, (size_t)H.lev[l].n * S3, &ce);
+      H.lev[l].dinv = dalloc<double>(s, (size_t)H.lev[l].n, &ce);
+    }
+    H.inv = dalloc<double>(s, 64, &ce);
+    H.invT = dalloc<double>(s, 64, &ce);
+    const long long n1 = H.nlev > 1 ? H.lev[1].n : 0;
+    H.rhs_stride = (long long)(2 * H.m + 3) * Nc + n1;
+    H.ws = dalloc<double>(s, (size_t)s->Ns * H.rhs_stride, &ce);
+    H.iters = dalloc<int>(s, 2 * (size_t)s->Ns, &ce);
+    const char* tr = getenv("MSFV_TRACE_COARSE");
+    if (tr && atoi(tr) > 0) {
+      H.trace_cap = 1 << 16;
+      H.trace = dalloc<long long>(s, (size_t)H.trace_cap, &ce);
+    }
+    H.group = mg_pick_cluster(d, s->Ns, &H.max_clusters);
+    if (H.group < 1) {
+      cudaGetLastError();
+      free_all(s);
+      delete s;
+      return fail(nullptr, MSFV_ERR_CUDA, "thread-block clusters unavailable for the coarse solver");
+    }
+    H.ngroups = std::max(1, std::min(s->Ns, std::max(1, H.max_clusters)));
+  }
   for (int k = 1; k <= d; ++k) s->d_ents[k] = dalloc<EntDesc>(s, s->h_ents[k].size(), &ce);
   if (ce != cudaSuccess) {
     const bool oom = (ce == cudaErrorMemoryAllocation);
@@ -512,7 +563,10 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   if (ce == cudaSuccess) ce = upload(s->rec_u, rec_u, st);
   if (ce == cudaSuccess) ce = upload(s->rq, rq, st);
   for (int k = 1; k <= d && ce == cudaSuccess; ++k) ce = upload(s->d_ents[k], s->h_ents[k], st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->status, 0, 2 * sizeof(int), st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->status, 0, (2 + s->Ns) * sizeof(int), st);
+  if (ce == cudaSuccess && s->mg.trace)
+    ce = cudaMemsetAsync(s->mg.trace, 0, sizeof(long long) * s->mg.trace_cap, st);
+
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) {
     std::string msg = std::string("setup upload failed: ") + cudaGetErrorString(ce);
@@ -550,8 +604,27 @@ namespace {
 
 void coarse_solve(msfv_session* s, double* rhs, int transpose) {
   const long long Nc = s->geo.Nc;
-  launch_band_solve(s->band, rhs, s->Ns, Nc, transpose, s->stream);
+  if (s->use_mg) {
+    MGHost H = s->mg;
+    H.iters = s->mg.iters + (transpose ? s->Ns : 0);
+    const cudaError_t e = launch_mg_solve(H, rhs, s->Ns, transpose, s->status + 2, s->stream);
+    if (e != cudaSuccess) s->launch_error = e;
+  } else {
+    launch_band_solve(s->band, rhs, s->Ns, Nc, transpose, s->stream);
+  }
   s->launches += 1;
+}
+
+// factorisation (banded LU) or hierarchy (multigrid) of the new A_c
+void coarse_prepare(msfv_session* s) {
+  if (s->use_mg) {
+    launch_mg_setup(s->mg, s->status + 1, s->stream);
+    s->launches += 2 * s->mg.nlev;
+  } else {
+    launch_band_build(s->dg, s->Ac, s->band, s->stream);
+    launch_band_factor(s->band, s->stream);
+    s->launches += 2;
+  }
 }
 
 int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
@@ -581,9 +654,7 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
   {
     PhaseScope ps(s, PH_COARSE_SOLVE);
     cudaMemcpyAsync(s->t, s->rq, sizeof(double) * (size_t)s->Ns * g.Nc, cudaMemcpyDeviceToDevice, st);
-    launch_band_build(g, s->Ac, s->band, st);
-    launch_band_factor(s->band, st);
-    s->launches += 2;
+    coarse_prepare(s);
     coarse_solve(s, s->t, 0);
   }
   {
@@ -656,12 +727,15 @@ int run_jvec(msfv_session* s, const double* v, double* jv) {
 }
 
 int read_status(msfv_session* s) {
-  int h[2] = {0, 0};
-  cudaError_t e = cudaMemcpyAsync(h, s->status, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+  std::vector<int> h(2 + s->Ns, 0);
+  cudaError_t e = cudaMemcpyAsync(h.data(), s->status, sizeof(int) * h.size(),
+                                  cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "status read");
   if (h[0]) return fail(s, MSFV_ERR_NUMERIC, "non-positive pivot in a local problem");
-  if (h[1]) return fail(s, MSFV_ERR_NUMERIC, "zero pivot in the coarse LU (singular A_c)");
+  if (h[1]) return fail(s, MSFV_ERR_NUMERIC, "zero pivot in the coarse solver (singular A_c)");
+  for (int j = 0; j < s->Ns; ++j)
+    if (h[2 + j]) return fail(s, MSFV_ERR_NUMERIC, "coarse GMRES did not converge");
   return MSFV_OK;
 }
 
@@ -741,11 +815,37 @@ extern "C" int msfv_solve_host(msfv_session_t* s, const double* m_host, const do
 // =============================================================================
 extern "C" int msfv_info(const msfv_session_t* s, int64_t* out, int n_out) {
   if (!s || !out) return MSFV_ERR_ARG;
-  int64_t v[8] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
-                  (int64_t)(s->h_ents[1].size() + s->h_ents[2].size() + s->h_ents[3].size()),
-                  (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, 0};
-  for (int i = 0; i < n_out && i < 8; ++i) out[i] = v[i];
+  int64_t it[2] = {0, 0};
+  if (s->use_mg && n_out > 8) {
+    std::vector<int> h(2 * s->Ns, 0);
+    if (cudaMemcpyAsync(h.data(), s->mg.iters, sizeof(int) * h.size(), cudaMemcpyDeviceToHost,
+                        s->stream) == cudaSuccess &&
+        cudaStreamSynchronize(s->stream) == cudaSuccess)
+      for (int j = 0; j < s->Ns; ++j) {
+        it[0] = std::max<int64_t>(it[0], h[j]);
+        it[1] = std::max<int64_t>(it[1], h[s->Ns + j]);
+      }
+  }
+  int64_t v[11] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
+                   (int64_t)(s->h_ents[1].size() + s->h_ents[2].size() + s->h_ents[3].size()),
+                   (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, s->use_mg ? 1 : 0, it[0], it[1],
+                   s->use_mg ? s->mg.group : 0};
+  for (int i = 0; i < n_out && i < 11; ++i) out[i] = v[i];
   return MSFV_OK;
+}
+
+extern "C" int msfv_coarse_trace(msfv_session_t* s, int64_t* out, int cap) {
+  if (!s || !out || cap < 1) return -MSFV_ERR_ARG;
+  if (!s->use_mg || !s->mg.trace) return 0;
+  std::vector<long long> h(s->mg.trace_cap);
+  if (cudaMemcpyAsync(h.data(), s->mg.trace, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost,
+                      s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return -MSFV_ERR_CUDA;
+  const int n = (int)std::min<long long>(h[0], cap);
+  for (int i = 0; i < n; ++i) out[i] = h[i + 1];
+  cudaMemsetAsync(s->mg.trace, 0, sizeof(long long), s->stream);
+  return n;
 }
 
 extern "C" int msfv_profile(msfv_session_t* s, int enable) {

@@ -68,11 +68,12 @@ def load(path: Optional[str] = None):
     L.msfv_phase_name.restype = ctypes.c_char_p
     L.msfv_interior_flops.argtypes = [vp]
     L.msfv_interior_flops.restype = ctypes.c_double
+    L.msfv_coarse_trace.argtypes = [vp, i64p, ctypes.c_int]
     L.msfv_launch_count.argtypes = [vp]
     L.msfv_launch_count.restype = ctypes.c_int64
     for f in ("msfv_setup", "msfv_forward", "msfv_adjoint", "msfv_jvec", "msfv_jtvec",
               "msfv_solve_host", "msfv_destroy", "msfv_set_stream", "msfv_info", "msfv_profile",
-              "msfv_phase_times", "msfv_phase_name"):
+              "msfv_phase_times", "msfv_phase_name", "msfv_coarse_trace"):
         if getattr(L, f).restype is None and f != "msfv_phase_name":
             getattr(L, f).restype = ctypes.c_int
     _lib = L
@@ -204,10 +205,10 @@ class Session:
 
     # -- introspection ----------------------------------------------------------------
     def info(self) -> dict:
-        out = (ctypes.c_int64 * 8)()
-        self._check(self._lib.msfv_info(self._h, out, 8))
+        out = (ctypes.c_int64 * 11)()
+        self._check(self._lib.msfv_info(self._h, out, 11))
         keys = ["N", "Nc", "Ns", "Nr", "n_local_problems", "workspace_bytes", "factor_bytes",
-                "coarse_solver"]
+                "coarse_solver", "coarse_iters", "coarse_iters_T", "coarse_group_ctas"]
         return dict(zip(keys, list(out)))
 
     def profile(self, enable: bool = True):
@@ -218,6 +219,14 @@ class Session:
         calls = (ctypes.c_int64 * 32)()
         n = self._lib.msfv_phase_times(self._h, ms, calls, 32, int(reset))
         return {self._lib.msfv_phase_name(k).decode(): (ms[k], calls[k]) for k in range(n)}
+
+    def coarse_trace(self, cap: int = 65536):
+        """(tag, ns) barrier stamps of the multigrid coarse solver (MSFV_TRACE_COARSE=1)."""
+        buf = (ctypes.c_int64 * cap)()
+        n = self._lib.msfv_coarse_trace(self._h, buf, cap)
+        if n < 0:
+            raise MSFVError(-n, "msfv_coarse_trace failed")
+        return [(int(v) >> 48, int(v) & ((1 << 48) - 1)) for v in buf[:n]]
 
     def interior_flops(self) -> float:
         return float(self._lib.msfv_interior_flops(self._h))
