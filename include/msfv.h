@@ -117,6 +117,29 @@ int msfv_jtvec(msfv_session_t* s, const double* w_dev, double* jtw_dev);
 int msfv_solve_host(msfv_session_t* s, const double* m_host, const double* d_obs_host,
                     double* d_pred_host, double* grad_host, double* phi_host);
 
+/* ---- allocation-free misfit (no counterpart in the paper) --------------------------
+ * For callers that cannot allocate GPU memory where they need the data misfit: code
+ * running inside a CUDA graph capture, a serving loop whose allocator must not grow, or
+ * a host application that only lends its own buffers.  Such callers cannot create a
+ * session (msfv_setup allocates), so this entry point needs none: it takes the data and
+ * the outputs from the caller and computes, on the given stream,
+ *   r_dev[i] = d_pred_dev[i] - d_obs_dev[i]   (skipped when r_dev is NULL)
+ *   *phi_dev = 1/2 sum_i r_i^2                 (device double, written)
+ * the same misfit msfv_adjoint reports.  Its only scratch -- one FP64 partial sum per
+ * thread block, at most 1024 of them (8 KiB) -- is a fixed array inside the library
+ * image; every GPU that loads the library keeps it until the process exits.
+ *   count   number of data values, 0 .. MSFV_MISFIT_STATIC_MAX; larger counts return
+ *           MSFV_ERR_ARG and enqueue nothing
+ * The first call on a device looks up the scratch address on that device (a CUDA
+ * runtime query); make that first call outside any stream capture.  All calls share the
+ * one scratch array: calls that overlap on the GPU (e.g. on two streams at once) race
+ * and must be ordered by the caller.  Nothing needs to start at zero: each call
+ * rewrites every partial it reads.  Calls no cudaMalloc / cudaFree and no allocating
+ * library routine. */
+#define MSFV_MISFIT_STATIC_MAX (16LL * 1024 * 1024)
+int msfv_misfit_static(const double* d_pred_dev, const double* d_obs_dev, int64_t count,
+                       double* r_dev, double* phi_dev, void* stream);
+
 /* Free the session and its device workspace (synchronises its stream). NULL is ok. */
 int msfv_destroy(msfv_session_t* s);
 
