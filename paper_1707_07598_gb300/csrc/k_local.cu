@@ -118,25 +118,31 @@ __device__ __forceinline__ void cp_wait() {
 
 // Shared-memory carve-up of one thread group.
 struct Smem {
-  double* W;      // window: B1 slots x B1s doubles
+  double* W;      // window / ring: ring_slots x B1s doubles
   double* Z;      // nslot x nmax right-hand sides / solutions (compacted slots)
   double* coef;   // 4 x nmax: diag and couplings along local axes 0..2
-  double* lvec;   // B1
-  double* tvec;   // B1
-  double* zj;     // 8
-  double* misc;   // 4
+  double* lp;     // 2 x KP x LPS: multipliers of a panel (zero padded), double-buffered
+  double* tp;     // 2 x KP x LPS: unscaled panel columns (zero padded), double-buffered
+  double* zj;     // 2 x KP x 8: unscaled forward-substitution values of a panel
+  double* misc;   // 2 x KP: reciprocal pivots of a panel
+  double* zb;     // KS x 8: block values of the blocked solve sweeps
 };
 
-// Prefetch distance (in columns) of the factor streams of the solve sweeps.
-constexpr int PD = 6;
+// Panel width of the blocked factorisation (columns factored per rank-KP update).
+constexpr int KP = 4;
+// Rows per block of the blocked solve sweeps.
+constexpr int KS = 8;
 
 __host__ __device__ inline int row_stride(int B1) { return (B1 & 1) ? B1 + 1 : B1; }
-__host__ __device__ inline int ring_slots(int bmax) { return bmax + 1 + PD; }
+// ring of factor columns: the factorisation needs bmax+KP slots, the blocked sweeps
+// bmax+KS for the current block plus two blocks of prefetch
+__host__ __device__ inline int ring_slots(int bmax) { return bmax + 3 * KS; }
+__host__ __device__ inline int panel_stride(int bmax) { return bmax + KP + 1; }
 
 __host__ __device__ inline long long group_doubles(int nmax, int bmax, int nslot) {
   const int B1 = bmax + 1;
   long long v = (long long)ring_slots(bmax) * row_stride(B1) + (long long)nslot * nmax + 4LL * nmax +
-                2 * B1 + 8 + 4;
+                4LL * KP * panel_stride(bmax) + 2 * 8 * KP + 2 * KP + 8 * KS;
   return (v + 1) & ~1LL;
 }
 
@@ -146,11 +152,21 @@ __device__ __forceinline__ Smem carve(double* base, int nmax, int bmax, int nslo
   s.W = base;
   s.Z = s.W + (long long)ring_slots(bmax) * row_stride(B1);
   s.coef = s.Z + (long long)nslot * nmax;
-  s.lvec = s.coef + 4LL * nmax;
-  s.tvec = s.lvec + B1;
-  s.zj = s.tvec + B1;
-  s.misc = s.zj + 8;
+  s.lp = s.coef + 4LL * nmax;
+  s.tp = s.lp + 2LL * KP * panel_stride(bmax);
+  s.zj = s.tp + 2LL * KP * panel_stride(bmax);
+  s.misc = s.zj + 2 * 8 * KP;
+  s.zb = s.misc + 2 * KP;
   return s;
+}
+
+// barrier of the threads that factor a panel (the first min(NT, 64) threads)
+template <int NT>
+__device__ __forceinline__ void panel_sync() {
+  if (NT == 32)
+    __syncwarp();
+  else
+    asm volatile("bar.sync 1, 64;" ::: "memory");
 }
 
 // Local operator coefficients: diag[p] = sum of tangential face values to in-domain
@@ -188,205 +204,306 @@ __device__ __forceinline__ double band_entry(const Loc& E, const Smem& sm, int n
   return v;
 }
 
-// Column update Z[i][j + sgn*k] -= col_k * Z[i][j] for k = 1..bj and the nvs
-// right-hand sides (forward: col = column j; backward: column j-k from the ring).
-// Two updates per trip, loads before stores, per-lane trip condition.
+// Issue cp.async copies of factor columns [c0, c1) into their ring slots (c % RB).
 template <int NT>
-__device__ __forceinline__ void sweep_update(const Smem& sm, int nmax, int nvs, int j, int bj,
-                                             int sgn, const double* col, int RB, int B1s,
-                                             int tid) {
-  const int nr = nvs * bj;
-  int it = tid;
-  for (; it + NT < nr; it += 2 * NT) {
-    const int i0 = it / bj, k0 = it - i0 * bj + 1;
-    const int i1 = (it + NT) / bj, k1 = it + NT - i1 * bj + 1;
-    const int o0 = i0 * nmax + j + sgn * k0, o1 = i1 * nmax + j + sgn * k1;
-    const double z0 = sm.Z[o0], z1 = sm.Z[o1];
-    const double x0 = sm.Z[i0 * nmax + j], x1 = sm.Z[i1 * nmax + j];
-    const double c0 = (sgn > 0) ? col[k0] : sm.W[((j - k0) % RB) * B1s + k0];
-    const double c1 = (sgn > 0) ? col[k1] : sm.W[((j - k1) % RB) * B1s + k1];
-    const double n0 = fma(-c0, x0, z0), n1 = fma(-c1, x1, z1);
-    sm.Z[o0] = n0;
-    sm.Z[o1] = n1;
-  }
-  if (it < nr) {
-    const int i0 = it / bj, k0 = it - i0 * bj + 1;
-    const int o0 = i0 * nmax + j + sgn * k0;
-    const double c0 = (sgn > 0) ? col[k0] : sm.W[((j - k0) % RB) * B1s + k0];
-    sm.Z[o0] = fma(-c0, sm.Z[i0 * nmax + j], sm.Z[o0]);
+__device__ __forceinline__ void fetch_columns(const Smem& sm, const double* fac_e, int c0, int c1,
+                                              int FB, int RB, int B1s, int tid) {
+  for (int it = tid; it < (c1 - c0) * FB; it += NT) {
+    const int c = c0 + it / FB, k = it - (it / FB) * FB;
+    cp_async8(sm.W + (c % RB) * B1s + k, fac_e + (long long)c * FB + k);
   }
 }
 
-// Backward substitution L^T x = y (y in Z, already scaled by 1/d): for j = n-1..0,
-// x_j is final and Z[j-k] -= l_{j,j-k} x_j.  Row j of L lives in the b columns
-// before it, so the factor is streamed column by column into a ring of
-// bmax+1+PD slots with cp.async, PD columns ahead of use; one barrier per step.
+// Backward substitution L^T x = y (y in Z, already scaled by 1/d) in blocks of KS rows
+// from the bottom.  Block [j0, j1]: the KS lanes of one right-hand side hold its rows in
+// registers and resolve the block's triangle with shuffles (x_r is final once the rows
+// below it in the block are applied); then all threads apply the block's x to the b rows
+// above it (row q needs L(r, q), stored at offset r - q of column q).  Factor columns
+// stream through the ring two blocks ahead; a block needs columns [j0 - b, j1).
 template <int NT>
 __device__ void backward_sweep(const Loc& E, const Smem& sm, int nmax, int bmax,
                                const double* fac_e, int tid) {
   const int n = E.n, b = E.b, nvs = E.nvs, FB = b + 1;
   const int RB = ring_slots(bmax), B1s = row_stride(bmax + 1);
-  double* W = sm.W;
-  const int c0 = max(0, n - b - PD);
-  for (int it = tid; it < (n - 1 - c0) * FB; it += NT) {
-    const int c = c0 + it / FB, k = it - (it / FB) * FB;
-    cp_async8(W + (c % RB) * B1s + k, fac_e + (long long)c * FB + k);
+  const double* W = sm.W;
+  const int nblk = (n + KS - 1) / KS;
+  const int lane_tot = ((nvs * KS + 31) / 32) * 32;  // whole warps run the shuffles
+  int flo = max(0, (nblk - 1) * KS - b);              // lowest column requested so far
+  fetch_columns<NT>(sm, fac_e, flo, n - 1, FB, RB, B1s, tid);
+  cp_commit();
+  if (nblk >= 2) {
+    const int c0 = max(0, (nblk - 2) * KS - b);
+    if (c0 < flo) fetch_columns<NT>(sm, fac_e, c0, flo, FB, RB, B1s, tid);
+    flo = min(flo, c0);
   }
   cp_commit();
-  cp_wait<0>();
-  for (int j = n - 1; j >= 0; --j) {
-    const int cl = j - b - PD;
-    if (cl >= 0)
-      for (int k = tid; k < FB; k += NT)
-        cp_async8(W + (cl % RB) * B1s + k, fac_e + (long long)cl * FB + k);
-    cp_commit();
-    cp_wait<PD>();
+  for (int bi = nblk - 1; bi >= 0; --bi) {
+    cp_wait<1>();
     gsync<NT>();
-    const int bj = min(b, j);
-    sweep_update<NT>(sm, nmax, nvs, j, bj, -1, nullptr, RB, B1s, tid);
+    if (bi >= 2) {
+      const int c0 = max(0, (bi - 2) * KS - b);
+      if (c0 < flo) fetch_columns<NT>(sm, fac_e, c0, flo, FB, RB, B1s, tid);
+      flo = min(flo, c0);
+    }
+    cp_commit();
+    const int j0 = bi * KS, j1 = min(n, j0 + KS) - 1;
+    for (int t = tid; t < lane_tot; t += NT) {
+      const int i = t / KS, l = t - (t / KS) * KS;
+      const int rl = j0 + l;
+      const bool ok = (i < nvs) && (rl <= j1);
+      double z = ok ? sm.Z[i * nmax + rl] : 0.0;
+      const double* Wl = W + (rl % RB) * B1s;
+#pragma unroll
+      for (int s = KS - 1; s >= 1; --s) {
+        if (j0 + s <= j1) {
+          const double xr = __shfl_sync(0xffffffffu, z, s, KS);
+          if (ok && l < s && s - l <= b) z = fma(-Wl[s - l], xr, z);
+        }
+      }
+      if (ok) {
+        sm.zb[l * 8 + i] = z;
+        sm.Z[i * nmax + rl] = z;
+      }
+    }
+    gsync<NT>();
+    const int i0 = max(0, j0 - b);
+    const int nrow = j0 - i0;
+    const int nr = nvs * nrow;
+    for (int it = tid; it < nr; it += NT) {
+      const int i = it / nrow, q = i0 + (it - (it / nrow) * nrow);
+      const double* Wq = W + (q % RB) * B1s;
+      double acc = sm.Z[i * nmax + q];
+      const int rmax = min(j1, q + b);
+      for (int r = j0; r <= rmax; ++r) acc = fma(-Wq[r - q], sm.zb[(r - j0) * 8 + i], acc);
+      sm.Z[i * nmax + q] = acc;
+    }
   }
   cp_wait<0>();
   gsync<NT>();
 }
 
-// Forward substitution L z = r with the stored factor, then y = D^{-1} z: column j
-// (1/d_j, l_{j+1..j+b,j}) is streamed PD columns ahead into the ring.
+// Forward substitution L z = r with the stored factor, then y = D^{-1} z, in blocks of KS
+// rows: the block's triangle per right-hand side in registers (shuffles), then one update
+// of the b rows below the block.  A block needs its own KS columns; they stream through
+// the ring two blocks ahead.
 template <int NT>
 __device__ void forward_sweep(const Loc& E, const Smem& sm, int nmax, int bmax,
                               const double* fac_e, int tid) {
   const int n = E.n, b = E.b, nvs = E.nvs, FB = b + 1;
   const int RB = ring_slots(bmax), B1s = row_stride(bmax + 1);
-  double* W = sm.W;
-  const int pre = min(n, PD);
-  for (int it = tid; it < pre * FB; it += NT) {
-    const int c = it / FB, k = it - (it / FB) * FB;
-    cp_async8(W + (c % RB) * B1s + k, fac_e + (long long)c * FB + k);
-  }
+  const double* W = sm.W;
+  const int nblk = (n + KS - 1) / KS;
+  const int lane_tot = ((nvs * KS + 31) / 32) * 32;
+  fetch_columns<NT>(sm, fac_e, 0, min(n, KS), FB, RB, B1s, tid);
   cp_commit();
-  cp_wait<0>();
-  for (int j = 0; j < n; ++j) {
-    const int cn = j + PD;
-    if (cn < n)
-      for (int k = tid; k < FB; k += NT)
-        cp_async8(W + (cn % RB) * B1s + k, fac_e + (long long)cn * FB + k);
-    cp_commit();
-    cp_wait<PD>();
+  fetch_columns<NT>(sm, fac_e, min(n, KS), min(n, 2 * KS), FB, RB, B1s, tid);
+  cp_commit();
+  for (int bi = 0; bi < nblk; ++bi) {
+    cp_wait<1>();
     gsync<NT>();
-    const double* Wj = W + (j % RB) * B1s;
-    if (j > 0) {
-      const double rdp = W[((j - 1) % RB) * B1s];
-      for (int i = tid; i < nvs; i += NT) sm.Z[(long long)i * nmax + j - 1] *= rdp;
+    const int f0 = (bi + 2) * KS, f1 = min(n, f0 + KS);
+    if (f0 < f1) fetch_columns<NT>(sm, fac_e, f0, f1, FB, RB, B1s, tid);
+    cp_commit();
+    const int j0 = bi * KS, j1 = min(n, j0 + KS) - 1;
+    for (int t = tid; t < lane_tot; t += NT) {
+      const int i = t / KS, l = t - (t / KS) * KS;
+      const int rl = j0 + l;
+      const bool ok = (i < nvs) && (rl <= j1);
+      double z = ok ? sm.Z[i * nmax + rl] : 0.0;
+#pragma unroll
+      for (int s = 0; s < KS - 1; ++s) {
+        if (j0 + s < j1) {
+          const double zq = __shfl_sync(0xffffffffu, z, s, KS);
+          if (ok && l > s && l - s <= b) z = fma(-W[((j0 + s) % RB) * B1s + (l - s)], zq, z);
+        }
+      }
+      if (ok) {
+        sm.zb[l * 8 + i] = z;
+        sm.Z[i * nmax + rl] = z * W[(rl % RB) * B1s];
+      }
     }
-    const int bj = min(b, n - 1 - j);
-    sweep_update<NT>(sm, nmax, nvs, j, bj, +1, Wj, RB, B1s, tid);
+    gsync<NT>();
+    const int r1 = min(n - 1, j1 + b);
+    const int nrow = r1 - j1;
+    const int nr = nvs * nrow;
+    for (int it = tid; it < nr; it += NT) {
+      const int i = it / nrow, r = j1 + 1 + (it - (it / nrow) * nrow);
+      double acc = sm.Z[i * nmax + r];
+      for (int q = max(j0, r - b); q <= j1; ++q)
+        acc = fma(-W[(q % RB) * B1s + (r - q)], sm.zb[(q - j0) * 8 + i], acc);
+      sm.Z[i * nmax + r] = acc;
+    }
   }
   cp_wait<0>();
-  gsync<NT>();
-  {
-    const double rdl = W[((n - 1) % RB) * B1s];
-    for (int i = tid; i < nvs; i += NT) sm.Z[(long long)i * nmax + n - 1] *= rdl;
-  }
   gsync<NT>();
 }
 
-// Banded LDL^T of L_E in a sliding window of bmax+1 columns with the forward
-// substitution of the nvs right-hand sides in Z fused into the sweep, then the
-// backward substitution.  On return Z holds the solutions.  The factor is stored
-// to fac_e: column j at j*(b+1) holds 1/d_j then l_{j+1..j+b, j} (zeros past n).
+// Factor one panel (columns j .. j+Kc-1, already updated by all earlier panels) into
+// panel buffer set pb: multipliers, unscaled columns, reciprocal pivots, the stored
+// factor columns and the fused forward substitution of the panel rows.  Threads < PA.
 template <int NT>
-__device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short* __restrict__ tab,
-                             int nmax, int bmax, double* __restrict__ fac_e, int* status, int tid) {
-  const int n = E.n, b = E.b, nvs = E.nvs;
-  const int B1 = bmax + 1;          // window slots (launch-wide, >= b+1)
-  const int B1s = row_stride(B1);
-  const int FB = b + 1;             // stored-factor column stride
+__device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int nmax, int bmax,
+                                             double* __restrict__ fac_e, int* status, int j,
+                                             int pb, int tid) {
+  constexpr int PA = (NT < 64) ? NT : 64;
+  const int n = E.n, b = E.b, nvs = E.nvs, FB = b + 1;
+  const int RS = ring_slots(bmax), B1s = row_stride(bmax + 1), LPS = panel_stride(bmax);
+  const int Kc = min(KP, n - j);
+  double* lp = sm.lp + pb * KP * LPS;
+  double* tp = sm.tp + pb * KP * LPS;
+  double* zj = sm.zj + pb * 8 * KP;
+  double* rdp = sm.misc + pb * KP;
   double* W = sm.W;
-  for (int it = tid; it < B1 * B1; it += NT) {
-    const int col = it / B1, k = it - (it / B1) * B1;
-    W[col * B1s + k] = (col < n && k <= b) ? band_entry(E, sm, nmax, col, k) : 0.0;
+  for (int r = tid; r < KP * LPS; r += PA) {
+    lp[r] = 0.0;
+    tp[r] = 0.0;
   }
-  gsync<NT>();
-  if (tid == 0) sm.misc[0] = 1.0 / W[0];
-  gsync<NT>();
-  int sj = 0;
-  for (int j = 0; j < n; ++j) {
-    const int bj = min(b, n - 1 - j);
-    const double rd = sm.misc[j & 1];
-    double* Wj = W + sj * B1s;
-    // phase A: multipliers l_k = t_k / d_j, stored factor column, scaled RHS entry
-    for (int k = tid; k <= b; k += NT) {
-      const double t = Wj[k];
+  panel_sync<NT>();
+  for (int q = 0; q < Kc; ++q) {
+    const int c = j + q;
+    double* Wc = W + (c % RS) * B1s;
+    const int bq = min(b, n - 1 - c);
+    for (int dl = tid; dl <= bq; dl += PA) {
+      double acc = Wc[dl];
+      for (int p = 0; p < q; ++p) acc = fma(-lp[p * LPS + q + dl], tp[p * LPS + q], acc);
+      Wc[dl] = acc;
+    }
+    panel_sync<NT>();
+    if (tid == 0) {
+      const double dq = Wc[0];
+      if (!(dq > 0.0)) atomicExch(status, 1);
+      rdp[q] = 1.0 / dq;
+    }
+    panel_sync<NT>();
+    const double rd = rdp[q];
+    for (int k = tid; k <= b; k += PA) {
       double outv = 0.0;
       if (k == 0) {
         outv = rd;
-        if (!(t > 0.0)) atomicExch(status, 1);
-      } else if (k <= bj) {
+      } else if (k <= bq) {
+        const double t = Wc[k];
         outv = t * rd;
-        sm.tvec[k] = t;
-        sm.lvec[k] = outv;
+        tp[q * LPS + q + k] = t;
+        lp[q * LPS + q + k] = outv;
       }
-      fac_e[(long long)j * FB + k] = outv;
+      fac_e[(long long)c * FB + k] = outv;
     }
-    for (int i = tid; i < nvs; i += NT) {
-      double* zp = sm.Z + (long long)i * nmax + j;
-      const double z = *zp;
-      sm.zj[i] = z;
-      *zp = z * rd;
+    for (int i = tid; i < nvs; i += PA) {
+      double z = sm.Z[i * nmax + c];
+      for (int p = 0; p < q; ++p) z = fma(-lp[p * LPS + q], zj[p * 8 + i], z);
+      zj[q * 8 + i] = z;
+      sm.Z[i * nmax + c] = z * rd;
+    }
+    panel_sync<NT>();
+  }
+}
+
+// Blocked banded LDL^T of L_E with the forward substitution of the nvs right-hand
+// sides in Z fused into the sweep, then the blocked backward substitution.  Columns are
+// factored in panels of KP.  While all other threads apply panel p's rank-KP update to
+// the trailing window and the right-hand sides, the first 64 threads first update the
+// KP columns of panel p+1 and then factor it (look-ahead), so there is one CTA barrier
+// per panel.  The window is a ring of RS = ring_slots(bmax) columns (column c in slot
+// c % RS), each holding rows c..c+b.  On return Z holds the solutions; the factor is
+// stored to fac_e: column j at j*(b+1) holds 1/d_j then l_{j+1..j+b, j} (zeros past n).
+template <int NT>
+__device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short* __restrict__ tab,
+                             int nmax, int bmax,
+                             double* __restrict__ fac_e, int* status, int tid) {
+  constexpr int PA = (NT < 64) ? NT : 64;
+  const int n = E.n, b = E.b, nvs = E.nvs;
+  const int RS = ring_slots(bmax);
+  const int B1s = row_stride(bmax + 1);
+  const int LPS = panel_stride(bmax);
+  double* W = sm.W;
+  for (int it = tid; it < RS * (b + 1); it += NT) {
+    const int col = it / (b + 1), k = it - (it / (b + 1)) * (b + 1);
+    W[col * B1s + k] = (col < n) ? band_entry(E, sm, nmax, col, k) : 0.0;
+  }
+  gsync<NT>();
+  if (tid < PA) factor_panel<NT>(E, sm, nmax, bmax, fac_e, status, 0, 0, tid);
+  gsync<NT>();
+  int pb = 0;
+  for (int j = 0; j < n; j += KP, pb ^= 1) {
+    const int Kc = min(KP, n - j);
+    const int base = j + Kc - 1;            // last panel column
+    const int bj = min(b, n - 1 - base);     // trailing columns / rows below the panel
+    const int K1 = min(KP, bj);              // trailing columns that form the next panel
+    const int sb = (base + 1) % RS;          // slot of column base+1
+    const double* lp = sm.lp + pb * KP * LPS;
+    const double* tp = sm.tp + pb * KP * LPS;
+    const double* zj = sm.zj + pb * 8 * KP;
+    if (NT == 32 || tid < PA) {
+      // (1) columns base+1 .. base+K1 (the next panel) and their right-hand-side rows
+      for (int k2 = 1; k2 <= K1; ++k2) {
+        int slot = sb + k2 - 1;
+        if (slot >= RS) slot -= RS;
+        double* Wc = W + slot * B1s;
+        const int ci = Kc - 1 + k2;
+        for (int k1 = k2 + tid; k1 <= bj; k1 += PA) {
+          const int ri = Kc - 1 + k1;
+          double acc = Wc[k1 - k2];
+#pragma unroll
+          for (int q = 0; q < KP; ++q)
+            if (q < Kc) acc = fma(-lp[q * LPS + ri], tp[q * LPS + ci], acc);
+          Wc[k1 - k2] = acc;
+        }
+      }
+      for (int it = tid; it < nvs * K1; it += PA) {
+        const int i = it / K1, k = it - (it / K1) * K1 + 1;
+        const int ri = Kc - 1 + k;
+        double* zp = sm.Z + i * nmax + base + k;
+        double acc = *zp;
+#pragma unroll
+        for (int q = 0; q < KP; ++q)
+          if (q < Kc) acc = fma(-lp[q * LPS + ri], zj[q * 8 + i], acc);
+        *zp = acc;
+      }
+      panel_sync<NT>();
+      // (2) factor the next panel into the other buffer set
+      if (j + KP < n) factor_panel<NT>(E, sm, nmax, bmax, fac_e, status, j + KP, pb ^ 1, tid);
+    }
+    if (NT == 32 || tid >= PA) {
+      const int t2 = (NT == 32) ? tid : tid - PA;
+      constexpr int N2 = (NT == 32) ? 32 : NT - 64;
+      // (3) the rest of the trailing triangle: columns base+KP+1 .. base+bj
+      const int m2 = bj - KP;
+      const int np2 = (m2 > 0) ? m2 * (m2 + 1) / 2 : 0;
+      for (int it = t2; it < np2; it += N2) {
+        // the pair table enumerates 1 <= k2 <= k1 <= m; shift it past the next panel
+        const unsigned short pr = tab[it];
+        const int k1 = (pr >> 8) + KP, k2 = (pr & 255) + KP;  // row base+k1, column base+k2
+        int slot = sb + k2 - 1;
+        if (slot >= RS) slot -= RS;
+        const int o = slot * B1s + (k1 - k2);
+        const int ri = Kc - 1 + k1, ci = Kc - 1 + k2;
+        double acc = W[o];
+#pragma unroll
+        for (int q = 0; q < KP; ++q)
+          if (q < Kc) acc = fma(-lp[q * LPS + ri], tp[q * LPS + ci], acc);
+        W[o] = acc;
+      }
+      // (4) right-hand-side rows base+K1+1 .. base+bj
+      const int nrow = bj - K1;
+      const int nr = nvs * nrow;
+      for (int it = t2; it < nr; it += N2) {
+        const int i = it / nrow, k = K1 + 1 + (it - (it / nrow) * nrow);
+        const int ri = Kc - 1 + k;
+        double* zp = sm.Z + i * nmax + base + k;
+        double acc = *zp;
+#pragma unroll
+        for (int q = 0; q < KP; ++q)
+          if (q < Kc) acc = fma(-lp[q * LPS + ri], zj[q * 8 + i], acc);
+        *zp = acc;
+      }
+      // (5) refill the freed slots of panel p with columns j+RS .. j+RS+Kc-1
+      for (int it = t2; it < Kc * (b + 1); it += N2) {
+        const int q = it / (b + 1), k = it - (it / (b + 1)) * (b + 1);
+        const int col = j + RS + q;
+        if (col < n) W[((j + q) % RS) * B1s + k] = band_entry(E, sm, nmax, col, k);
+      }
     }
     gsync<NT>();
-    // phase B: rank-1 window update, fused forward substitution, next column in.
-    // Two updates per trip, both loaded before either is stored; the trip condition
-    // is per lane, so warps whose lanes are all done never issue an FMA.
-    const int np = bj * (bj + 1) / 2;
-    {
-      int it = tid;
-      for (; it + NT < np; it += 2 * NT) {
-        const unsigned short p0 = tab[it], p1 = tab[it + NT];
-        int s0 = sj + (p0 & 255), s1 = sj + (p1 & 255);
-        if (s0 >= B1) s0 -= B1;
-        if (s1 >= B1) s1 -= B1;
-        const int o0 = s0 * B1s + ((p0 >> 8) - (p0 & 255));
-        const int o1 = s1 * B1s + ((p1 >> 8) - (p1 & 255));
-        const double w0 = W[o0], w1 = W[o1];
-        const double l0 = sm.lvec[p0 >> 8], l1 = sm.lvec[p1 >> 8];
-        const double t0 = sm.tvec[p0 & 255], t1 = sm.tvec[p1 & 255];
-        const double n0 = fma(-l0, t0, w0), n1 = fma(-l1, t1, w1);
-        W[o0] = n0;
-        W[o1] = n1;
-        if (it == 0) sm.misc[(j + 1) & 1] = 1.0 / n0;  // pair (1,1): diagonal of column j+1
-      }
-      if (it < np) {
-        const unsigned short p0 = tab[it];
-        int s0 = sj + (p0 & 255);
-        if (s0 >= B1) s0 -= B1;
-        const int o0 = s0 * B1s + ((p0 >> 8) - (p0 & 255));
-        const double n0 = fma(-sm.lvec[p0 >> 8], sm.tvec[p0 & 255], W[o0]);
-        W[o0] = n0;
-        if (it == 0) sm.misc[(j + 1) & 1] = 1.0 / n0;
-      }
-    }
-    {
-      const int nr = nvs * bj;
-      int it = tid;
-      for (; it + NT < nr; it += 2 * NT) {
-        const int i0 = it / bj, k0 = it - i0 * bj + 1;
-        const int i1 = (it + NT) / bj, k1 = it + NT - i1 * bj + 1;
-        const int o0 = i0 * nmax + j + k0, o1 = i1 * nmax + j + k1;
-        const double z0 = sm.Z[o0], z1 = sm.Z[o1];
-        const double n0 = fma(-sm.lvec[k0], sm.zj[i0], z0), n1 = fma(-sm.lvec[k1], sm.zj[i1], z1);
-        sm.Z[o0] = n0;
-        sm.Z[o1] = n1;
-      }
-      if (it < nr) {
-        const int i0 = it / bj, k0 = it - i0 * bj + 1;
-        const int o0 = i0 * nmax + j + k0;
-        sm.Z[o0] = fma(-sm.lvec[k0], sm.zj[i0], sm.Z[o0]);
-      }
-    }
-    if (j + B1 < n)
-      for (int k = tid; k < B1; k += NT) Wj[k] = (k <= b) ? band_entry(E, sm, nmax, j + B1, k) : 0.0;
-    gsync<NT>();
-    sj = (sj + 1 == B1) ? 0 : sj + 1;
   }
   backward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
 }
