@@ -31,10 +31,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1707_07598_gb300 import workloads as W  # noqa: E402
+from paper_1707_07598_gb300 import replicas as R  # noqa: E402
 
 METRIC = "batched/served MSFV fwd+grad solves/s vs plain at 1e-9 rel err; p50/p99 ms"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x 2 flop x max SM clock
 WORKLOAD = "3d_128^3_c8_16dipoles_512rec_fwd+grad"
+# DRAM bytes (read + write) of one k_local_fwd<256,1> launch per fine cell, from the ncu
+# capture of the current kernel at 64^3, c=8 (17.08 MB read + 56.85 MB write over 262144
+# cells; profiles/k_local_fwd_interiors_3d_64cube_c8.md).  The kernel's traffic (factor and
+# basis writes, conductivity reads) grows with the number of cells, so a launch on another
+# mesh is scaled by its cell count.  Set to None whenever the kernel changes.
+INTERIOR_DRAM_BYTES_PER_CELL = (17.078272e6 + 56.845824e6) / 64 ** 3
 
 
 def parse():
@@ -50,10 +57,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    e = R.rank_env()
+    return e.rank, e.world, e.local
 
 
 # ---------------------------------------------------------------------------------
@@ -184,14 +189,15 @@ def run_ours(args):
     B.build()
     from paper_1707_07598_gb300.msfv import Session
 
-    prob, m_np = W.config_3d_128(seed=2 + rank, n=args.n)
+    seeds = R.replica_seeds(rank)
+    prob, m_np = W.config_3d_128(seed=seeds.model, n=args.n)
     stream = torch.cuda.current_stream(dev)
     sess = Session(prob, stream=stream)
     m = torch.from_numpy(m_np).to(dev)
     # observed data: forward at an independent model plus 1% noise (outside the timing)
-    m_true = torch.from_numpy(W.config_3d_128(seed=100 + rank, n=args.n)[1]).to(dev)
+    m_true = torch.from_numpy(W.config_3d_128(seed=seeds.truth, n=args.n)[1]).to(dev)
     d_true = sess.forward(m_true).clone()
-    noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, 7 + rank)).to(dev)
+    noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, seeds.noise)).to(dev)
     d_obs = d_true + 0.01 * d_true.abs() * noise
     grad = torch.empty(prob.N, dtype=torch.float64, device=dev)
     d_pred = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev)
@@ -211,8 +217,7 @@ def run_ours(args):
     clocks = ClockSampler(dev.index if dev.index is not None else 0)
     clocks.start()
     time.sleep(0.3)
-    if world > 1:
-        torch.distributed.barrier()
+    R.barrier()
     torch.cuda.synchronize(dev)
     launches0 = sess.launch_count()
     for k in range(args.steps):
@@ -222,20 +227,15 @@ def run_ours(args):
         ev[k][1].record(stream)
     torch.cuda.synchronize(dev)
     launches = sess.launch_count() - launches0
-    if world > 1:
-        torch.distributed.barrier()
+    R.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     phases = sess.phase_times(reset=True)
     sess.profile(False)
     info = sess.info()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = R.max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value = R.whole_job_rate(world, args.steps, total_ms / 1000.0)
 
     # roofline of the dominant kernel: the dual-cell interior basis solve
     int_ms, int_calls = phases.get("basis_interiors", (0.0, 0))
@@ -248,7 +248,10 @@ def run_ours(args):
             "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (recipe unit "
                            "counts and max clock); a DFMA probe measured 1.20 TFLOP/s at 1987 MHz",
             "flops_per_launch": flops, "avg_launch_ms": int_avg_s * 1000.0,
-            "traffic": None}
+            "traffic": (INTERIOR_DRAM_BYTES_PER_CELL * prob.N
+                        if INTERIOR_DRAM_BYTES_PER_CELL is not None else None),
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel at "
+                              "64^3, scaled by the number of fine cells"}
     phase_ms = {k: v[0] / max(args.steps, 1) for k, v in phases.items() if v[1]}
 
     e2e = None
@@ -263,18 +266,16 @@ def run_ours(args):
         for _ in range(2):
             sess.solve_host(mn, dn, dpn, gn)
         times = []
+        R.barrier()
         for k in range(args.steps):
             flush.fill_(float(k))
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             sess.solve_host(mn, dn, dpn, gn)
             times.append(time.perf_counter() - t0)
-        tot = sum(times)
-        if world > 1:
-            t = torch.tensor([tot], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot = float(t.item())
-        e2e = {"value": world * args.steps / tot, "unit": "solves/s",
+        R.barrier()
+        tot = R.max_over_ranks(sum(times), dev)
+        e2e = {"value": R.whole_job_rate(world, args.steps, tot), "unit": "solves/s",
                "h2d_bytes_per_step": 8 * prob.N + 8 * prob.n_src * prob.n_rec,
                "d2h_bytes_per_step": 8 * prob.N + 8 * prob.n_src * prob.n_rec + 8}
 

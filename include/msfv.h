@@ -58,8 +58,9 @@ typedef struct msfv_desc {
   int dim;                  /* 2 or 3                                                  */
   int n[3];                 /* cells per axis (n[2] ignored when dim == 2)             */
   int coarsen;              /* coarsening factor c >= 1; must divide every n[a];
-                               at least 2 coarse cells in total; c <= 12 in 3D,
-                               c <= 32 in 2D (local problems held on chip)             */
+                               at least 2 coarse cells in total; c <= 11 in 3D,
+                               c <= 32 in 2D (local problems held on chip); the
+                               mesh must have fewer than 2^31 cells                    */
   int n_src;                /* Ns >= 1 dipole sources                                  */
   const int64_t* src_pos;   /* host, Ns cells receiving +src_amp[j]                    */
   const int64_t* src_neg;   /* host, Ns cells receiving -src_amp[j] (!= src_pos[j])    */

@@ -448,10 +448,12 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   s->band.ku = s->band.kl;
   s->band.ldab = 2 * s->band.kl + s->band.ku + 1;
 
-  // coarse solver: banded LU while its factorisation is small, else multigrid GMRES
+  // coarse solver: banded LU while its factorisation is small, else multigrid GMRES.  The
+  // banded LU runs its column loop in one thread block; at Nc = 512 (3D, kl = 73, 5.5e6
+  // band flops) it takes 4.7 ms on a GB300 against 2.0 ms for the multigrid GMRES.
   {
     const double band_work = (double)s->band.n * s->band.kl * (s->band.kl + s->band.ku);
-    s->use_mg = band_work > 1e7;
+    s->use_mg = band_work > 1e6;
     const char* env = getenv("MSFV_COARSE_SOLVER");
     if (env && !strcmp(env, "band")) s->use_mg = false;
     if (env && !strcmp(env, "mg")) s->use_mg = true;
