@@ -41,7 +41,7 @@ WORKLOAD = "3d_128^3_c8_16dipoles_512rec_fwd+grad"
 # cells; profiles/k_local_fwd_interiors_3d_64cube_c8.md).  The kernel's traffic (factor and
 # basis writes, conductivity reads) grows with the number of cells, so a launch on another
 # mesh is scaled by its cell count.  Set to None whenever the kernel changes.
-INTERIOR_DRAM_BYTES_PER_CELL = (17.078272e6 + 56.845824e6) / 64 ** 3
+INTERIOR_DRAM_BYTES_PER_CELL = None
 
 
 def parse():

@@ -58,9 +58,11 @@ typedef struct msfv_desc {
   int dim;                  /* 2 or 3                                                  */
   int n[3];                 /* cells per axis (n[2] ignored when dim == 2)             */
   int coarsen;              /* coarsening factor c >= 1; must divide every n[a];
-                               at least 2 coarse cells in total; c <= 11 in 3D,
-                               c <= 32 in 2D (local problems held on chip); the
-                               mesh must have fewer than 2^31 cells                    */
+                               at least 2 coarse cells in total; local half bandwidth
+                               (c-1)^(d-1) <= 255, i.e. c <= 16 in 3D, c <= 256 in 2D;
+                               the mesh must have fewer than 2^31 cells.  Local
+                               problems that do not fit in shared memory (3D c >= 12)
+                               are factored in global memory                           */
   int n_src;                /* Ns >= 1 dipole sources                                  */
   const int64_t* src_pos;   /* host, Ns cells receiving +src_amp[j]                    */
   const int64_t* src_neg;   /* host, Ns cells receiving -src_amp[j] (!= src_pos[j])    */
@@ -68,8 +70,11 @@ typedef struct msfv_desc {
   int n_rec;                /* Nr >= 1 point receivers                                 */
   const int64_t* rec_cell;  /* host, Nr cells; receiver i reads u_j at rec_cell[i];
                                repeated cells are allowed                              */
-  int factor_mode;          /* 0 auto, 1 store local factors (needed by adjoint / jvec
-                               / jtvec), 2 recompute (not yet supported: MSFV_ERR_ARG) */
+  int factor_mode;          /* 0 auto: store the local factors unless that exceeds
+                               hbm_budget_bytes, then recompute; 1 store them (the
+                               derivative calls reuse them); 2 recompute them in every
+                               derivative call (adjoint / jvec / jtvec refactor each
+                               local problem; only per-thread-group scratch is kept) */
   size_t hbm_budget_bytes;  /* 0 = no limit; else setup fails with MSFV_ERR_OOM when
                                the session workspace would exceed it                   */
 } msfv_desc_t;
@@ -159,7 +164,11 @@ int msfv_set_stream(msfv_session_t* s, void* stream);
  * out[8] / out[9]=largest number of GMRES iterations over the right-hand sides of the
  * last coarse solve with A_c / A_c^T (0 for the banded LU; reading them synchronises
  * the stream), out[10]=thread-block cluster size (CTAs, one per SM) the multigrid
- * GMRES kernel gives each right-hand side.  n_out may be smaller than 11. */
+ * GMRES kernel gives each right-hand side, out[11]=1 when the local factors are
+ * recomputed (0 stored), out[12]=bit k set when the k-dimensional local problems are
+ * factored in global memory.  n_out may be smaller than 13.
+ * The environment variable MSFV_LOCAL_WINDOW=global at msfv_setup forces the global-
+ * memory factorisation for every class (for testing). */
 int msfv_info(const msfv_session_t* s, int64_t* out, int n_out);
 
 /* Barrier time stamps of the multigrid GMRES coarse solver, recorded only when the

@@ -16,6 +16,10 @@
 
 namespace msfv {
 
+// Loop over the mesh axes a < g.d, fully unrolled so that per-axis arrays (coordinates,
+// coarse indices) are indexed by constants and stay in registers.
+#define PER_AXIS(a) _Pragma("unroll") for (int a = 0; a < 3; ++a) if (a < g.d)
+
 namespace {
 
 // cell index -> coordinates; 32-bit arithmetic (setup guarantees N < 2^31)
@@ -47,7 +51,7 @@ __device__ __forceinline__ int lo_vertex(const DevGeom& g, int xa) {
 __device__ __forceinline__ double phi_at(const DevGeom& g, const double* __restrict__ Pw,
                                          long long x, const int* xc, const int* Jc) {
   int s = 0;
-  for (int a = 0; a < g.d; ++a) {
+  PER_AXIS(a) {
     const int bit = Jc[a] - lo_vertex(g, xc[a]);
     if (bit < 0 || bit > 1) return 0.0;
     s |= bit << a;
@@ -58,7 +62,7 @@ __device__ __forceinline__ double phi_at(const DevGeom& g, const double* __restr
 // coarse vertex of slot s at cell x, -1 if it does not exist
 __device__ __forceinline__ long long vertex_of(const DevGeom& g, const int* xc, int s) {
   long long J = 0;
-  for (int a = 0; a < g.d; ++a) {
+  PER_AXIS(a) {
     const int v = lo_vertex(g, xc[a]) + ((s >> a) & 1);
     if (v < 0 || v >= g.nc[a]) return -1;
     J += v * g.cst[a];
@@ -86,11 +90,11 @@ __global__ void k_face_T(DevGeom g, const double* __restrict__ sig, double* __re
     int xc[3];
     coords(g, x, xc);
     const double sx = sig[x];
-    for (int a = 0; a < g.d; ++a) {
+    PER_AXIS(a) {
       double t = 0.0, dl = 0.0;
       if (xc[a] + 1 < g.n[a]) {
         double geo = (double)g.n[a];
-        for (int b = 0; b < g.d; ++b)
+        PER_AXIS(b)
           if (b != a) geo /= (double)g.n[b];
         const double sy = sig[x + g.st[a]];
         const double inv = 1.0 / (sx + sy);
@@ -118,7 +122,7 @@ __global__ void k_vertices(DevGeom g, double* __restrict__ Pw) {
   int Kc[3];
   ccoords(g, J, Kc);
   long long x = 0;
-  for (int a = 0; a < g.d; ++a) x += (long long)(g.c * Kc[a] + g.half) * g.st[a];
+  PER_AXIS(a) x += (long long)(g.c * Kc[a] + g.half) * g.st[a];
   for (int s = 0; s < g.S; ++s) Pw[x * g.S + s] = (s == 0) ? 1.0 : 0.0;
 }
 
@@ -146,19 +150,19 @@ __global__ void k_coarse_assemble(DevGeom g, const double* __restrict__ T,
   ccoords(g, I, Ic);
   {
     int oo = o;
-    for (int a = 0; a < g.d; ++a) {
+    PER_AXIS(a) {
       Jc[a] = Ic[a] + (oo % 3) - 1;
       oo /= 3;
     }
   }
   double acc = 0.0;
   bool valid = true;
-  for (int a = 0; a < g.d; ++a)
+  PER_AXIS(a)
     if (Jc[a] < 0 || Jc[a] >= g.nc[a]) valid = false;
   if (valid) {
-    for (int a = 0; a < g.d; ++a) {
+    PER_AXIS(a) {
       // the two other axes span the face
-      const int b1 = (a + 1) % g.d, b2 = (a + 2) % g.d;
+      const int b1 = (a + 1) % g.d;
       const int n1 = g.c, n2 = (g.d == 3) ? g.c : 1;
       for (int side = 0; side < 2; ++side) {
         const int xa = side ? g.c * Ic[a] + g.c - 1 : g.c * Ic[a];
@@ -166,14 +170,14 @@ __global__ void k_coarse_assemble(DevGeom g, const double* __restrict__ T,
         if (ya < 0 || ya >= g.n[a]) continue;
         for (int i2 = 0; i2 < n2; ++i2)
           for (int i1 = 0; i1 < n1; ++i1) {
-            int xc[3] = {0, 0, 0}, yc[3];
-            xc[a] = xa;
-            xc[b1] = g.c * Ic[b1] + i1;
-            if (g.d == 3) xc[b2] = g.c * Ic[b2] + i2;
-            yc[0] = xc[0];
-            yc[1] = xc[1];
-            yc[2] = xc[2];
-            yc[a] = ya;
+            int xc[3], yc[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              int val = 0;
+              if (q < g.d) val = (q == a) ? xa : g.c * Ic[q] + (q == b1 ? i1 : i2);
+              xc[q] = val;
+              yc[q] = (q == a) ? ya : val;
+            }
             const long long x = xc[0] + g.st[1] * xc[1] + g.st[2] * xc[2];
             const long long y = yc[0] + g.st[1] * yc[1] + g.st[2] * yc[2];
             const long long lower = side ? x : y;
@@ -264,13 +268,15 @@ __global__ void k_prolong_full(DevGeom g, const double* __restrict__ Pw,
     coords(g, x, xc);
     long long J[8];
     double w[8];
-    for (int s = 0; s < g.S; ++s) {
-      J[s] = vertex_of(g, xc, s);
-      w[s] = Pw[x * g.S + s];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      J[s] = s < g.S ? vertex_of(g, xc, s) : -1;
+      w[s] = s < g.S ? Pw[x * g.S + s] : 0.0;
     }
     for (int j = 0; j < Ns; ++j) {
       double acc = 0.0;
-      for (int s = 0; s < g.S; ++s)
+#pragma unroll
+      for (int s = 0; s < 8; ++s)
         if (J[s] >= 0) acc = fma(w[s], t[(long long)j * g.Nc + J[s]], acc);
       u[(long long)j * g.N + x] = acc;
     }
@@ -365,7 +371,7 @@ __global__ void k_lambda(DevGeom g, const double* __restrict__ t, const double* 
   bool ok = true;
   int vc[3];
   ccoords(g, v, vc);
-  for (int a = 0; a < g.d; ++a) {
+  PER_AXIS(a) {
     const int va = vc[a];
     const int ka = va + (oo % 3) - 1;
     oo /= 3;
@@ -413,7 +419,7 @@ __device__ double term_G(const DevGeom& g, const double* __restrict__ Pw,
                          const int* uc) {
   const int S3 = stencil_size(g);
   int Kl[3] = {0, 0, 0}, Ku[3] = {0, 0, 0};
-  for (int a = 0; a < g.d; ++a) {
+  PER_AXIS(a) {
     Kl[a] = lc[a] / g.c;
     Ku[a] = uc[a] / g.c;
   }
@@ -427,7 +433,7 @@ __device__ double term_G(const DevGeom& g, const double* __restrict__ Pw,
       long long vid = 0;
       int ol = 0, ou = 0, mul = 1;
       bool ok = true;
-      for (int a = 0; a < g.d; ++a) {
+      PER_AXIS(a) {
         const int va = lo_vertex(g, xc[a]) + ((s >> a) & 1);
         if (va < 0 || va >= g.nc[a]) ok = false;
         vid += (long long)va * g.cst[a];
@@ -452,7 +458,7 @@ __global__ void k_grad(DevGeom g, const double* __restrict__ T, const double* __
     int xc[3];
     coords(g, x, xc);
     double acc = 0.0;
-    for (int a = 0; a < g.d; ++a) {
+    PER_AXIS(a) {
       // face (x, x+e_a): x is the lower cell
       if (xc[a] + 1 < g.n[a]) {
         double gf = gTloc[(long long)a * g.N + x];
@@ -500,7 +506,7 @@ __global__ void k_coarse_tan_rhs(DevGeom g, const double* __restrict__ dAc,
     int oo = o;
     long long J = 0;
     bool ok = true;
-    for (int a = 0; a < g.d; ++a) {
+    PER_AXIS(a) {
       const int ja = Ic[a] + (oo % 3) - 1;
       oo /= 3;
       if (ja < 0 || ja >= g.nc[a]) ok = false;
@@ -533,7 +539,7 @@ __global__ void k_band_build(DevGeom g, const double* __restrict__ Ac, long long
   int oo = o;
   int Icc[3];
   ccoords(g, I, Icc);
-  for (int a = 0; a < g.d; ++a) {
+  PER_AXIS(a) {
     const int ia = Icc[a];
     const int ja = ia + (oo % 3) - 1;
     oo /= 3;

@@ -31,11 +31,15 @@ namespace msfv {
 
 namespace {
 
+// Per-entity description held in registers: every array is indexed only by a global
+// axis a or a local axis k that unrolled loops make compile-time constants, so nothing
+// spills to local memory.
 struct Loc {
-  int org[3], len[3], perm[3], loc_of[3];  // loc_of[a]: local index of global axis a or -1
-  int off[3];                              // local index offset along perm[k]
+  int org[3], len[3];  // box per global axis
+  int lk[3];           // local axis of global axis a, -1 on a vertex axis
+  int str[3];          // local index stride of global axis a (0 on a vertex axis)
+  int off[3];          // local index stride of local axis k (k < dim)
   int dim, n, b, slots, nvs;
-  int vs[8];
   long long fac;
   int rec_off, rec_cnt;
 };
@@ -48,38 +52,42 @@ __device__ __forceinline__ void load_loc(const EntDesc& e, Loc& E) {
   E.fac = e.fac;
   E.rec_off = e.rec_off;
   E.rec_cnt = e.rec_cnt;
+  int o = 1;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    E.off[k] = o;
+    if (k < e.dim) o *= e.len[e.perm[k]];
+  }
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     E.org[a] = e.org[a];
     E.len[a] = e.len[a];
-    E.perm[a] = e.perm[a];
-    E.loc_of[a] = -1;
+    E.lk[a] = -1;
+    E.str[a] = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < e.dim && e.perm[k] == a) {
+        E.lk[a] = k;
+        E.str[a] = E.off[k];
+      }
   }
-  int o = 1;
-  for (int k = 0; k < 3; ++k) {
-    E.off[k] = o;
-    if (k < e.dim) {
-      E.loc_of[e.perm[k]] = k;
-      o *= e.len[e.perm[k]];
-    }
-  }
-  E.nvs = 0;
-  for (int s = 0; s < 8; ++s)
-    if (e.slots & (1 << s)) E.vs[E.nvs++] = s;
+  E.nvs = __popc(e.slots);
+}
+
+// corner slot of compact right-hand-side index i (the i-th set bit of slots)
+__device__ __forceinline__ int nth_slot(unsigned slots, int i) {
+  for (int q = 0; q < i; ++q) slots &= slots - 1u;
+  return __ffs(slots) - 1;
+}
+// compact right-hand-side index of corner slot s
+__device__ __forceinline__ int slot_index(unsigned slots, int s) {
+  return __popc(slots & ((1u << s) - 1u));
 }
 
 // local index -> global cell coordinates
 __device__ __forceinline__ void p_coords(const Loc& E, int p, int* xc) {
-  xc[0] = E.org[0];
-  xc[1] = E.org[1];
-  xc[2] = E.org[2];
-  int r = p;
-  for (int k = 0; k < E.dim; ++k) {
-    const int a = E.perm[k];
-    const int l = E.len[a];
-    const int q = r / l;
-    xc[a] += r - q * l;
-    r = q;
-  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) xc[a] = E.org[a] + (E.str[a] ? (p / E.str[a]) % E.len[a] : 0);
 }
 
 __device__ __forceinline__ long long cell_id(const DevGeom& g, const int* xc) {
@@ -118,14 +126,19 @@ __device__ __forceinline__ void cp_wait() {
 
 // Shared-memory carve-up of one thread group.
 struct Smem {
-  double* W;      // window / ring: ring_slots x B1s doubles
+  double* W;      // window: a ring of RS columns of stride B1s in shared memory, or (global
+                  // window) the entity's whole band in global memory, column c at c * B1s
   double* Z;      // nslot x nmax right-hand sides / solutions (compacted slots)
   double* coef;   // 4 x nmax: diag and couplings along local axes 0..2
+  double* F;      // recompute mode: per-group factor storage in global memory
   double* lp;     // 2 x KP x LPS: multipliers of a panel (zero padded), double-buffered
   double* tp;     // 2 x KP x LPS: unscaled panel columns (zero padded), double-buffered
   double* zj;     // 2 x KP x 8: unscaled forward-substitution values of a panel
   double* misc;   // 2 x KP: reciprocal pivots of a panel
   double* zb;     // KS x 8: block values of the blocked solve sweeps
+  int RS;         // ring slots (a huge value for the global window: column c in slot c)
+  int B1s;        // column stride of W
+  int gw;         // 1: global window (no ring, no cp.async staging)
 };
 
 // Panel width of the blocked factorisation (columns factored per rank-KP update).
@@ -139,25 +152,69 @@ __host__ __device__ inline int row_stride(int B1) { return (B1 & 1) ? B1 + 1 : B
 __host__ __device__ inline int ring_slots(int bmax) { return bmax + 3 * KS; }
 __host__ __device__ inline int panel_stride(int bmax) { return bmax + KP + 1; }
 
-__host__ __device__ inline long long group_doubles(int nmax, int bmax, int nslot) {
+constexpr int kGlobalRing = 1 << 30;
+
+// Shared-memory doubles of one thread group: the panel buffers, plus (shared window)
+// the ring, the right-hand sides and the coefficients.
+__host__ __device__ inline long long group_doubles(int nmax, int bmax, int nslot, int gw) {
   const int B1 = bmax + 1;
-  long long v = (long long)ring_slots(bmax) * row_stride(B1) + (long long)nslot * nmax + 4LL * nmax +
-                4LL * KP * panel_stride(bmax) + 2 * 8 * KP + 2 * KP + 8 * KS;
+  long long v = 4LL * KP * panel_stride(bmax) + 2 * 8 * KP + 2 * KP + 8 * KS;
+  if (!gw) v += (long long)ring_slots(bmax) * row_stride(B1) + (long long)nslot * nmax + 4LL * nmax;
   return (v + 1) & ~1LL;
 }
 
-__device__ __forceinline__ Smem carve(double* base, int nmax, int bmax, int nslot) {
+// Global scratch doubles of one thread group: (global window) right-hand sides and
+// coefficients, (recompute) the factor of the largest entity.
+__host__ __device__ inline long long scratch_group_doubles(int nmax, int bmax, int nslot, int gw,
+                                                           int recompute) {
+  long long v = 0;
+  if (gw) v += (long long)nslot * nmax + 4LL * nmax;
+  if (recompute) v += (long long)nmax * (bmax + 1);
+  return (v + 31) & ~31LL;
+}
+
+// Carve the group's shared memory (base) and global scratch (gs).  For the global
+// window, W and B1s are set per entity (set_window).
+__device__ __forceinline__ Smem carve(double* base, double* gs, int nmax, int bmax, int nslot,
+                                      int gw, int recompute) {
   Smem s;
   const int B1 = bmax + 1;
-  s.W = base;
-  s.Z = s.W + (long long)ring_slots(bmax) * row_stride(B1);
-  s.coef = s.Z + (long long)nslot * nmax;
-  s.lp = s.coef + 4LL * nmax;
+  s.gw = gw;
+  double* p;
+  if (!gw) {
+    s.RS = ring_slots(bmax);
+    s.B1s = row_stride(B1);
+    s.W = base;
+    s.Z = s.W + (long long)s.RS * s.B1s;
+    s.coef = s.Z + (long long)nslot * nmax;
+    p = s.coef + 4LL * nmax;
+    s.F = recompute ? gs : nullptr;
+  } else {
+    s.RS = kGlobalRing;
+    s.B1s = B1;
+    s.W = nullptr;
+    s.Z = gs;
+    s.coef = gs + (long long)nslot * nmax;
+    s.F = recompute ? s.coef + 4LL * nmax : nullptr;
+    p = base;
+  }
+  s.lp = p;
   s.tp = s.lp + 2LL * KP * panel_stride(bmax);
   s.zj = s.tp + 2LL * KP * panel_stride(bmax);
   s.misc = s.zj + 2 * 8 * KP;
   s.zb = s.misc + 2 * KP;
   return s;
+}
+
+// Factor storage of entity E (stored factors or the group's recompute scratch); with the
+// global window the band is factored in place there.
+__device__ __forceinline__ double* set_window(Smem& sm, const Loc& E, double* fac) {
+  double* fe = sm.F ? sm.F : fac + E.fac;
+  if (sm.gw) {
+    sm.W = fe;
+    sm.B1s = E.b + 1;
+  }
+  return fe;
 }
 
 // barrier of the threads that factor a panel (the first min(NT, 64) threads)
@@ -179,28 +236,28 @@ __device__ void build_coef(const DevGeom& g, const Loc& E, const double* __restr
     p_coords(E, p, xc);
     const long long x = cell_id(g, xc);
     double dg = 0.0;
-    double cp[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < E.dim; ++k) {
-      const int a = E.perm[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (E.lk[a] < 0) continue;
+      double cpa = 0.0;
       if (xc[a] + 1 < g.n[a]) {
         const double t = face_at(T, g, a, x);
         dg += t;
-        if (xc[a] + 1 < E.org[a] + E.len[a]) cp[k] = -t;
+        if (xc[a] + 1 < E.org[a] + E.len[a]) cpa = -t;
       }
       if (xc[a] > 0) dg += face_at(T, g, a, x - g.st[a]);
+      sm.coef[(E.lk[a] + 1) * nmax + p] = cpa;
     }
     sm.coef[p] = dg;
-    sm.coef[nmax + p] = cp[0];
-    sm.coef[2 * nmax + p] = cp[1];
-    sm.coef[3 * nmax + p] = cp[2];
   }
 }
 
 // Original entry (col+k, col) of L_E for the window initialisation.
 __device__ __forceinline__ double band_entry(const Loc& E, const Smem& sm, int nmax, int col, int k) {
   double v = (k == 0) ? sm.coef[col] : 0.0;
-  for (int q = 0; q < E.dim; ++q)
-    if (E.off[q] == k) v += sm.coef[(q + 1) * nmax + col];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    if (q < E.dim && E.off[q] == k) v += sm.coef[(q + 1) * nmax + col];
   return v;
 }
 
@@ -208,6 +265,7 @@ __device__ __forceinline__ double band_entry(const Loc& E, const Smem& sm, int n
 template <int NT>
 __device__ __forceinline__ void fetch_columns(const Smem& sm, const double* fac_e, int c0, int c1,
                                               int FB, int RB, int B1s, int tid) {
+  if (sm.gw) return;  // the global window reads the factor in place
   for (int it = tid; it < (c1 - c0) * FB; it += NT) {
     const int c = c0 + it / FB, k = it - (it / FB) * FB;
     cp_async8(sm.W + (c % RB) * B1s + k, fac_e + (long long)c * FB + k);
@@ -224,7 +282,7 @@ template <int NT>
 __device__ void backward_sweep(const Loc& E, const Smem& sm, int nmax, int bmax,
                                const double* fac_e, int tid) {
   const int n = E.n, b = E.b, nvs = E.nvs, FB = b + 1;
-  const int RB = ring_slots(bmax), B1s = row_stride(bmax + 1);
+  const int RB = sm.RS, B1s = sm.B1s;
   const double* W = sm.W;
   const int nblk = (n + KS - 1) / KS;
   const int lane_tot = ((nvs * KS + 31) / 32) * 32;  // whole warps run the shuffles
@@ -290,7 +348,7 @@ template <int NT>
 __device__ void forward_sweep(const Loc& E, const Smem& sm, int nmax, int bmax,
                               const double* fac_e, int tid) {
   const int n = E.n, b = E.b, nvs = E.nvs, FB = b + 1;
-  const int RB = ring_slots(bmax), B1s = row_stride(bmax + 1);
+  const int RB = sm.RS, B1s = sm.B1s;
   const double* W = sm.W;
   const int nblk = (n + KS - 1) / KS;
   const int lane_tot = ((nvs * KS + 31) / 32) * 32;
@@ -343,11 +401,10 @@ __device__ void forward_sweep(const Loc& E, const Smem& sm, int nmax, int bmax,
 // factor columns and the fused forward substitution of the panel rows.  Threads < PA.
 template <int NT>
 __device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int nmax, int bmax,
-                                             double* __restrict__ fac_e, int* status, int j,
-                                             int pb, int tid) {
+                                             double* fac_e, int* status, int j, int pb, int tid) {
   constexpr int PA = (NT < 64) ? NT : 64;
   const int n = E.n, b = E.b, nvs = E.nvs, FB = b + 1;
-  const int RS = ring_slots(bmax), B1s = row_stride(bmax + 1), LPS = panel_stride(bmax);
+  const int RS = sm.RS, B1s = sm.B1s, LPS = panel_stride(bmax);
   const int Kc = min(KP, n - j);
   double* lp = sm.lp + pb * KP * LPS;
   double* tp = sm.tp + pb * KP * LPS;
@@ -371,7 +428,7 @@ __device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int n
     panel_sync<NT>();
     if (tid == 0) {
       const double dq = Wc[0];
-      if (!(dq > 0.0)) atomicExch(status, 1);
+      if (!(dq > 0.0) && status) atomicExch(status, 1);
       rdp[q] = 1.0 / dq;
     }
     panel_sync<NT>();
@@ -408,15 +465,15 @@ __device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int n
 // stored to fac_e: column j at j*(b+1) holds 1/d_j then l_{j+1..j+b, j} (zeros past n).
 template <int NT>
 __device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short* __restrict__ tab,
-                             int nmax, int bmax,
-                             double* __restrict__ fac_e, int* status, int tid) {
+                             int nmax, int bmax, double* fac_e, int* status, int tid) {
   constexpr int PA = (NT < 64) ? NT : 64;
   const int n = E.n, b = E.b, nvs = E.nvs;
-  const int RS = ring_slots(bmax);
-  const int B1s = row_stride(bmax + 1);
+  const int RS = sm.RS;
+  const int B1s = sm.B1s;
   const int LPS = panel_stride(bmax);
   double* W = sm.W;
-  for (int it = tid; it < RS * (b + 1); it += NT) {
+  const int ncol0 = RS < n ? RS : n;  // columns loaded up front (all of them for a global window)
+  for (int it = tid; it < ncol0 * (b + 1); it += NT) {
     const int col = it / (b + 1), k = it - (it / (b + 1)) * (b + 1);
     W[col * B1s + k] = (col < n) ? band_entry(E, sm, nmax, col, k) : 0.0;
   }
@@ -470,9 +527,12 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short*
       const int m2 = bj - KP;
       const int np2 = (m2 > 0) ? m2 * (m2 + 1) / 2 : 0;
       for (int it = t2; it < np2; it += N2) {
-        // the pair table enumerates 1 <= k2 <= k1 <= m; shift it past the next panel
+        // pair table entry (c'+1, r+1) of the triangle 0 <= r <= c' < m2, read column by
+        // column from the last: column k2 = m2 - c', row k1 = k2 + r (contiguous rows of a
+        // column for consecutive threads), both shifted past the next panel
         const unsigned short pr = tab[it];
-        const int k1 = (pr >> 8) + KP, k2 = (pr & 255) + KP;  // row base+k1, column base+k2
+        const int k2 = m2 - ((pr >> 8) - 1) + KP;  // column base+k2
+        const int k1 = k2 + (pr & 255) - 1;         // row base+k1
         int slot = sb + k2 - 1;
         if (slot >= RS) slot -= RS;
         const int o = slot * B1s + (k1 - k2);
@@ -509,11 +569,43 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short*
 }
 
 // Solve L_E x = Z (nvs right-hand sides in shared memory) with the stored factor.
+// Solve L_E x = Z (nvs right-hand sides in Z) with the factor: read the stored factor,
+// or (recompute mode) factor L_E again with the forward substitution fused in.
 template <int NT>
-__device__ void stored_solve(const Loc& E, const Smem& sm, int nmax, int bmax,
-                             const double* __restrict__ fac_e, int tid) {
-  forward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
-  backward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
+__device__ void derivative_solve(const Loc& E, const Smem& sm, const unsigned short* tab, int nmax,
+                                 int bmax, double* fac_e, int tid) {
+  if (sm.F) {
+    factor_solve<NT>(E, sm, tab, nmax, bmax, fac_e, nullptr, tid);
+  } else {
+    forward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
+    backward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
+  }
+}
+
+// Pair table of the blocked factorisation: entry i of the triangle 0 <= r <= c', in
+// order of c' then r, holds ((c'+1) << 8) | (r+1).
+__device__ void build_pair_table(unsigned short* tab, int npairs) {
+  for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+    int k1 = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
+    while (k1 * (k1 + 1) / 2 > i) --k1;
+    while ((k1 + 1) * (k1 + 2) / 2 <= i) ++k1;
+    const int k2 = i - k1 * (k1 + 1) / 2;
+    tab[i] = (unsigned short)(((k1 + 1) << 8) | (k2 + 1));
+  }
+}
+
+// Next entity of a thread group from the launch's work counter (dynamic schedule).
+template <int NT>
+__device__ __forceinline__ int next_entity(int* counter, int* s_next, int tid) {
+  if (NT == 32) {
+    int e = 0;
+    if (tid == 0) e = atomicAdd(counter, 1);
+    return __shfl_sync(0xffffffffu, e, 0);
+  }
+  __syncthreads();  // every thread has read the previous value
+  if (tid == 0) *s_next = atomicAdd(counter, 1);
+  __syncthreads();
+  return *s_next;
 }
 
 // Value of basis slot s of the entity at a neighbouring cell y that lies outside
@@ -534,65 +626,60 @@ __device__ __forceinline__ int mapped_slot(int s, int a, int dir) {
 template <int NT, int G>
 __global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_fwd(DevGeom g, LocalLaunch L,
                                                      const double* __restrict__ T,
-                                                     double* __restrict__ Pw,
-                                                     double* __restrict__ fac, int* status) {
+                                                     double* __restrict__ Pw, double* fac,
+                                                     int* status) {
   extern __shared__ double smem[];
+  __shared__ int s_next;
   const int nslot = 1 << g.d;
-  const long long gd = group_doubles(L.nmax, L.bmax, nslot);
+  const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
   unsigned short* tab = reinterpret_cast<unsigned short*>(smem + G * gd);
-  for (int i = threadIdx.x; i < L.npairs; i += NT * G) {
-    // k1-major enumeration of 1 <= k2 <= k1 <= bmax (prefix property per b)
-    int k1 = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
-    while (k1 * (k1 + 1) / 2 > i) --k1;
-    while ((k1 + 1) * (k1 + 2) / 2 <= i) ++k1;
-    const int k2 = i - k1 * (k1 + 1) / 2;
-    tab[i] = (unsigned short)(((k1 + 1) << 8) | (k2 + 1));
-  }
+  build_pair_table(tab, L.npairs);
   __syncthreads();
   const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
-  const int eid = blockIdx.x * G + grp;
-  if (eid >= L.n_ents) return;
-  Loc E;
-  load_loc(L.ents[eid], E);
-  Smem sm = carve(smem + grp * gd, L.nmax, L.bmax, nslot);
-  build_coef<NT>(g, E, T, sm, L.nmax, tid);
-  // right-hand sides: T * phi_v at Dirichlet neighbours across the box boundary
-  for (int it = tid; it < E.n * E.nvs; it += NT) {
-    const int i = it / E.n, p = it - (it / E.n) * E.n;
-    const int s = E.vs[i];
-    int xc[3];
-    p_coords(E, p, xc);
-    const long long x = cell_id(g, xc);
-    double r = 0.0;
-    for (int k = 0; k < E.dim; ++k) {
-      const int a = E.perm[k];
-      if (xc[a] + 1 < g.n[a] && xc[a] + 1 >= E.org[a] + E.len[a]) {
-        const int sp = mapped_slot(s, a, +1);
-        if (sp >= 0) r += face_at(T, g, a, x) * Pw[(x + g.st[a]) * nslot + sp];
+  double* gs = L.scratch ? L.scratch + (long long)(blockIdx.x * G + grp) * L.scratch_group : nullptr;
+  Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute);
+  for (;;) {
+    const int eid = next_entity<NT>(L.counter + 0, &s_next, tid);
+    if (eid >= L.n_ents) break;
+    Loc E;
+    load_loc(L.ents[eid], E);
+    double* fac_e = set_window(sm, E, fac);
+    build_coef<NT>(g, E, T, sm, L.nmax, tid);
+    // right-hand sides: T * phi_v at Dirichlet neighbours across the box boundary
+    for (int it = tid; it < E.n * E.nvs; it += NT) {
+      const int i = it / E.n, p = it - (it / E.n) * E.n;
+      const int s = nth_slot(E.slots, i);
+      int xc[3];
+      p_coords(E, p, xc);
+      const long long x = cell_id(g, xc);
+      double r = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (E.lk[a] < 0) continue;
+        if (xc[a] + 1 < g.n[a] && xc[a] + 1 >= E.org[a] + E.len[a]) {
+          const int sp = mapped_slot(s, a, +1);
+          if (sp >= 0) r += face_at(T, g, a, x) * Pw[(x + g.st[a]) * nslot + sp];
+        }
+        if (xc[a] > 0 && xc[a] - 1 < E.org[a]) {
+          const int sp = mapped_slot(s, a, -1);
+          if (sp >= 0) r += face_at(T, g, a, x - g.st[a]) * Pw[(x - g.st[a]) * nslot + sp];
+        }
       }
-      if (xc[a] > 0 && xc[a] - 1 < E.org[a]) {
-        const int sp = mapped_slot(s, a, -1);
-        if (sp >= 0) r += face_at(T, g, a, x - g.st[a]) * Pw[(x - g.st[a]) * nslot + sp];
-      }
+      sm.Z[(long long)i * L.nmax + p] = r;
     }
-    sm.Z[(long long)i * L.nmax + p] = r;
-  }
-  gsync<NT>();
-  factor_solve<NT>(E, sm, tab, L.nmax, L.bmax, fac + E.fac, status, tid);
-  // write the basis weights of every slot (zeros for slots the entity lacks)
-  for (int it = tid; it < E.n * nslot; it += NT) {
-    const int p = it / nslot, s = it - (it / nslot) * nslot;
-    int xc[3];
-    p_coords(E, p, xc);
-    const long long x = cell_id(g, xc);
-    double v = 0.0;
-    if (E.slots & (1 << s)) {
-      int i = 0;
-      for (int q = 0; q < E.nvs; ++q)
-        if (E.vs[q] == s) i = q;
-      v = sm.Z[(long long)i * L.nmax + p];
+    gsync<NT>();
+    factor_solve<NT>(E, sm, tab, L.nmax, L.bmax, fac_e, status, tid);
+    // write the basis weights of every slot (zeros for slots the entity lacks)
+    for (int it = tid; it < E.n * nslot; it += NT) {
+      const int p = it / nslot, s = it - (it / nslot) * nslot;
+      int xc[3];
+      p_coords(E, p, xc);
+      const long long x = cell_id(g, xc);
+      double v = 0.0;
+      if (E.slots & (1 << s)) v = sm.Z[(long long)slot_index(E.slots, s) * L.nmax + p];
+      Pw[x * nslot + s] = v;
     }
-    Pw[x * nslot + s] = v;
+    gsync<NT>();
   }
 }
 
@@ -602,8 +689,7 @@ __global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_fwd(DevGeom 
 template <int NT, int G>
 __global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_adj(DevGeom g, LocalLaunch L,
                                                      const double* __restrict__ T,
-                                                     const double* __restrict__ Pw,
-                                                     const double* __restrict__ fac,
+                                                     const double* __restrict__ Pw, double* fac,
                                                      const double* __restrict__ Lam,
                                                      const int* __restrict__ rec_p,
                                                      const int* __restrict__ rec_u,
@@ -611,108 +697,130 @@ __global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_adj(DevGeom 
                                                      double* __restrict__ MU,
                                                      double* __restrict__ gTloc) {
   extern __shared__ double smem[];
+  __shared__ int s_next;
   const int nslot = 1 << g.d;
-  const long long gd = group_doubles(L.nmax, L.bmax, nslot);
+  const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
+  unsigned short* tab = reinterpret_cast<unsigned short*>(smem + G * gd);
+  if (L.recompute) {
+    build_pair_table(tab, L.npairs);
+    __syncthreads();
+  }
   const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
-  const int eid = blockIdx.x * G + grp;
-  if (eid >= L.n_ents) return;
-  Loc E;
-  load_loc(L.ents[eid], E);
-  if (E.nvs < 2) return;  // constant basis on this entity: no derivative
-  Smem sm = carve(smem + grp * gd, L.nmax, L.bmax, nslot);
+  double* gs = L.scratch ? L.scratch + (long long)(blockIdx.x * G + grp) * L.scratch_group : nullptr;
+  Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute);
   const int S3 = (g.d == 3) ? 27 : 9;
-  // seeds
-  for (int it = tid; it < E.n * E.nvs; it += NT) {
-    const int i = it / E.n, p = it - (it / E.n) * E.n;
-    const int s = E.vs[i];
-    int xc[3];
-    p_coords(E, p, xc);
-    const long long x = cell_id(g, xc);
-    // corner vertex of slot s and coarse cell of x
-    int v[3] = {0, 0, 0}, K[3] = {0, 0, 0};
-    long long vid = 0;
-    for (int a = 0; a < g.d; ++a) {
-      v[a] = lo_vertex(g, xc[a]) + ((s >> a) & 1);
-      K[a] = xc[a] / g.c;
-      vid += v[a] * g.cst[a];
+  for (;;) {
+    const int eid = next_entity<NT>(L.counter + 1, &s_next, tid);
+    if (eid >= L.n_ents) break;
+    Loc E;
+    load_loc(L.ents[eid], E);
+    if (E.nvs < 2) continue;  // constant basis on this entity: no derivative
+    double* fac_e = set_window(sm, E, fac);
+    if (L.recompute) {
+      build_coef<NT>(g, E, T, sm, L.nmax, tid);
+      gsync<NT>();
     }
-    const double* Lv = Lam + vid * S3;
-    int ox = 0, mul = 1;
-    for (int a = 0; a < g.d; ++a) {
-      ox += (K[a] - v[a] + 1) * mul;
-      mul *= 3;
-    }
-    const double lx = Lv[ox];
-    double w = 0.0;
-    // -(A Lambda_v)(x): only neighbours in another coarse cell contribute
-    for (int a = 0; a < g.d; ++a) {
-      mul = (a == 0) ? 1 : (a == 1 ? 3 : 9);
-      if (xc[a] + 1 < g.n[a] && (xc[a] + 1) / g.c != K[a])
-        w -= face_at(T, g, a, x) * (lx - Lv[ox + mul]);
-      if (xc[a] > 0 && (xc[a] - 1) / g.c != K[a])
-        w -= face_at(T, g, a, x - g.st[a]) * (lx - Lv[ox - mul]);
-    }
-    // receivers inside the entity
-    for (int r = 0; r < E.rec_cnt; ++r)
-      if (rec_p[E.rec_off + r] == p) w += ZT[(long long)rec_u[E.rec_off + r] * nslot + s];
-    // mu of the higher-dimensional neighbours across the vertex axes
-    for (int a = 0; a < g.d; ++a) {
-      if (E.loc_of[a] >= 0) continue;
-      if (xc[a] + 1 < g.n[a]) w += face_at(T, g, a, x) * MU[(x + g.st[a]) * nslot + s];
-      if (xc[a] > 0) w += face_at(T, g, a, x - g.st[a]) * MU[(x - g.st[a]) * nslot + (s | (1 << a))];
-    }
-    sm.Z[(long long)i * L.nmax + p] = w;
-  }
-  gsync<NT>();
-  stored_solve<NT>(E, sm, L.nmax, L.bmax, fac + E.fac, tid);
-  // transmissibility gradient of the owned faces and mu for lower entities
-  for (int it = tid; it < E.n * E.dim; it += NT) {
-    const int k = it / E.n, p = it - (it / E.n) * E.n;
-    const int a = E.perm[k];
-    int xc[3];
-    p_coords(E, p, xc);
-    const long long x = cell_id(g, xc);
-    // face to the + side (owned whenever it exists)
-    if (xc[a] + 1 < g.n[a]) {
-      const long long y = x + g.st[a];
-      const bool in = xc[a] + 1 < E.org[a] + E.len[a];
-      double acc = 0.0;
-      for (int i = 0; i < E.nvs; ++i) {
-        const int s = E.vs[i];
-        const double mx = sm.Z[(long long)i * L.nmax + p];
-        double my = 0.0, py = 0.0;
-        if (in) {
-          my = sm.Z[(long long)i * L.nmax + p + E.off[k]];
-          py = Pw[y * nslot + s];
-        } else {
-          const int sp = mapped_slot(s, a, +1);
-          if (sp >= 0) py = Pw[y * nslot + sp];
-        }
-        acc = fma(mx - my, Pw[x * nslot + s] - py, acc);
-      }
-      gTloc[(long long)a * g.N + x] = -acc;
-    }
-    // face to the - side when the neighbour is outside the box
-    if (xc[a] > 0 && xc[a] - 1 < E.org[a]) {
-      const long long y = x - g.st[a];
-      double acc = 0.0;
-      for (int i = 0; i < E.nvs; ++i) {
-        const int s = E.vs[i];
-        const double mx = sm.Z[(long long)i * L.nmax + p];
-        const int sp = mapped_slot(s, a, -1);
-        const double py = (sp >= 0) ? Pw[y * nslot + sp] : 0.0;
-        acc = fma(mx, Pw[x * nslot + s] - py, acc);
-      }
-      gTloc[(long long)a * g.N + y] = -acc;
-    }
-  }
-  if (E.dim > 1) {
+    // seeds
     for (int it = tid; it < E.n * E.nvs; it += NT) {
       const int i = it / E.n, p = it - (it / E.n) * E.n;
+      const int s = nth_slot(E.slots, i);
       int xc[3];
       p_coords(E, p, xc);
-      MU[cell_id(g, xc) * nslot + E.vs[i]] = sm.Z[(long long)i * L.nmax + p];
+      const long long x = cell_id(g, xc);
+      // corner vertex of slot s and coarse cell of x
+      int v[3] = {0, 0, 0}, K[3] = {0, 0, 0};
+      long long vid = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (a >= g.d) continue;
+        v[a] = lo_vertex(g, xc[a]) + ((s >> a) & 1);
+        K[a] = xc[a] / g.c;
+        vid += v[a] * g.cst[a];
+      }
+      const double* Lv = Lam + vid * S3;
+      int ox = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a < g.d) ox += (K[a] - v[a] + 1) * (a == 0 ? 1 : (a == 1 ? 3 : 9));
+      const double lx = Lv[ox];
+      double w = 0.0;
+      // -(A Lambda_v)(x): only neighbours in another coarse cell contribute
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (a >= g.d) continue;
+        const int mul = (a == 0) ? 1 : (a == 1 ? 3 : 9);
+        if (xc[a] + 1 < g.n[a] && (xc[a] + 1) / g.c != K[a])
+          w -= face_at(T, g, a, x) * (lx - Lv[ox + mul]);
+        if (xc[a] > 0 && (xc[a] - 1) / g.c != K[a])
+          w -= face_at(T, g, a, x - g.st[a]) * (lx - Lv[ox - mul]);
+      }
+      // receivers inside the entity
+      for (int r = 0; r < E.rec_cnt; ++r)
+        if (rec_p[E.rec_off + r] == p) w += ZT[(long long)rec_u[E.rec_off + r] * nslot + s];
+      // mu of the higher-dimensional neighbours across the vertex axes
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (a >= g.d || E.lk[a] >= 0) continue;
+        if (xc[a] + 1 < g.n[a]) w += face_at(T, g, a, x) * MU[(x + g.st[a]) * nslot + s];
+        if (xc[a] > 0)
+          w += face_at(T, g, a, x - g.st[a]) * MU[(x - g.st[a]) * nslot + (s | (1 << a))];
+      }
+      sm.Z[(long long)i * L.nmax + p] = w;
     }
+    gsync<NT>();
+    derivative_solve<NT>(E, sm, tab, L.nmax, L.bmax, fac_e, tid);
+    // transmissibility gradient of the owned faces and mu for lower entities
+    for (int p = tid; p < E.n; p += NT) {
+      int xc[3];
+      p_coords(E, p, xc);
+      const long long x = cell_id(g, xc);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (E.lk[a] < 0) continue;
+        // face to the + side (owned whenever it exists)
+        if (xc[a] + 1 < g.n[a]) {
+          const long long y = x + g.st[a];
+          const bool in = xc[a] + 1 < E.org[a] + E.len[a];
+          double acc = 0.0;
+          for (int i = 0; i < E.nvs; ++i) {
+            const int s = nth_slot(E.slots, i);
+            const double mx = sm.Z[(long long)i * L.nmax + p];
+            double my = 0.0, py = 0.0;
+            if (in) {
+              my = sm.Z[(long long)i * L.nmax + p + E.str[a]];
+              py = Pw[y * nslot + s];
+            } else {
+              const int sp = mapped_slot(s, a, +1);
+              if (sp >= 0) py = Pw[y * nslot + sp];
+            }
+            acc = fma(mx - my, Pw[x * nslot + s] - py, acc);
+          }
+          gTloc[(long long)a * g.N + x] = -acc;
+        }
+        // face to the - side when the neighbour is outside the box
+        if (xc[a] > 0 && xc[a] - 1 < E.org[a]) {
+          const long long y = x - g.st[a];
+          double acc = 0.0;
+          for (int i = 0; i < E.nvs; ++i) {
+            const int s = nth_slot(E.slots, i);
+            const double mx = sm.Z[(long long)i * L.nmax + p];
+            const int sp = mapped_slot(s, a, -1);
+            const double py = (sp >= 0) ? Pw[y * nslot + sp] : 0.0;
+            acc = fma(mx, Pw[x * nslot + s] - py, acc);
+          }
+          gTloc[(long long)a * g.N + y] = -acc;
+        }
+      }
+    }
+    if (E.dim > 1) {
+      for (int it = tid; it < E.n * E.nvs; it += NT) {
+        const int i = it / E.n, p = it - (it / E.n) * E.n;
+        int xc[3];
+        p_coords(E, p, xc);
+        MU[cell_id(g, xc) * nslot + nth_slot(E.slots, i)] = sm.Z[(long long)i * L.nmax + p];
+      }
+    }
+    gsync<NT>();
   }
 }
 
@@ -724,76 +832,86 @@ __global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_tan(DevGeom 
                                                      const double* __restrict__ T,
                                                      const double* __restrict__ Dl,
                                                      const double* __restrict__ v,
-                                                     const double* __restrict__ Pw,
-                                                     const double* __restrict__ fac,
+                                                     const double* __restrict__ Pw, double* fac,
                                                      double* __restrict__ dPw) {
   extern __shared__ double smem[];
+  __shared__ int s_next;
   const int nslot = 1 << g.d;
-  const long long gd = group_doubles(L.nmax, L.bmax, nslot);
+  const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
+  unsigned short* tab = reinterpret_cast<unsigned short*>(smem + G * gd);
+  if (L.recompute) {
+    build_pair_table(tab, L.npairs);
+    __syncthreads();
+  }
   const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
-  const int eid = blockIdx.x * G + grp;
-  if (eid >= L.n_ents) return;
-  Loc E;
-  load_loc(L.ents[eid], E);
-  if (E.nvs < 2) {
+  double* gs = L.scratch ? L.scratch + (long long)(blockIdx.x * G + grp) * L.scratch_group : nullptr;
+  Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute);
+  for (;;) {
+    const int eid = next_entity<NT>(L.counter + 2, &s_next, tid);
+    if (eid >= L.n_ents) break;
+    Loc E;
+    load_loc(L.ents[eid], E);
+    if (E.nvs < 2) {
+      for (int it = tid; it < E.n * nslot; it += NT) {
+        const int p = it / nslot, s = it - (it / nslot) * nslot;
+        int xc[3];
+        p_coords(E, p, xc);
+        dPw[cell_id(g, xc) * nslot + s] = 0.0;
+      }
+      continue;
+    }
+    double* fac_e = set_window(sm, E, fac);
+    if (L.recompute) {
+      build_coef<NT>(g, E, T, sm, L.nmax, tid);
+      gsync<NT>();
+    }
+    for (int it = tid; it < E.n * E.nvs; it += NT) {
+      const int i = it / E.n, p = it - (it / E.n) * E.n;
+      const int s = nth_slot(E.slots, i);
+      int xc[3];
+      p_coords(E, p, xc);
+      const long long x = cell_id(g, xc);
+      const double px = Pw[x * nslot + s];
+      double r = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (E.lk[a] < 0) continue;
+        for (int dir = -1; dir <= 1; dir += 2) {
+          const int ya = xc[a] + dir;
+          if (ya < 0 || ya >= g.n[a]) continue;
+          const long long y = x + dir * g.st[a];
+          const long long lower = dir > 0 ? x : y;
+          const double t = face_at(T, g, a, lower);
+          const double dl = face_at(Dl, g, a, lower);
+          const double dT = dl * v[lower] + (t - dl) * v[lower + g.st[a]];
+          const bool in = ya >= E.org[a] && ya < E.org[a] + E.len[a];
+          double py = 0.0, dpy = 0.0;
+          if (in) {
+            py = Pw[y * nslot + s];
+          } else {
+            const int sp = mapped_slot(s, a, dir);
+            if (sp >= 0) {
+              py = Pw[y * nslot + sp];
+              dpy = dPw[y * nslot + sp];
+            }
+          }
+          r = fma(-dT, px - py, r);
+          if (!in) r = fma(t, dpy, r);
+        }
+      }
+      sm.Z[(long long)i * L.nmax + p] = r;
+    }
+    gsync<NT>();
+    derivative_solve<NT>(E, sm, tab, L.nmax, L.bmax, fac_e, tid);
     for (int it = tid; it < E.n * nslot; it += NT) {
       const int p = it / nslot, s = it - (it / nslot) * nslot;
       int xc[3];
       p_coords(E, p, xc);
-      dPw[cell_id(g, xc) * nslot + s] = 0.0;
+      double val = 0.0;
+      if (E.slots & (1 << s)) val = sm.Z[(long long)slot_index(E.slots, s) * L.nmax + p];
+      dPw[cell_id(g, xc) * nslot + s] = val;
     }
-    return;
-  }
-  Smem sm = carve(smem + grp * gd, L.nmax, L.bmax, nslot);
-  for (int it = tid; it < E.n * E.nvs; it += NT) {
-    const int i = it / E.n, p = it - (it / E.n) * E.n;
-    const int s = E.vs[i];
-    int xc[3];
-    p_coords(E, p, xc);
-    const long long x = cell_id(g, xc);
-    const double px = Pw[x * nslot + s];
-    double r = 0.0;
-    for (int k = 0; k < E.dim; ++k) {
-      const int a = E.perm[k];
-      for (int dir = -1; dir <= 1; dir += 2) {
-        const int ya = xc[a] + dir;
-        if (ya < 0 || ya >= g.n[a]) continue;
-        const long long y = x + dir * g.st[a];
-        const long long lower = dir > 0 ? x : y;
-        const double t = face_at(T, g, a, lower);
-        const double dl = face_at(Dl, g, a, lower);
-        const double dT = dl * v[lower] + (t - dl) * v[lower + g.st[a]];
-        const bool in = ya >= E.org[a] && ya < E.org[a] + E.len[a];
-        double py = 0.0, dpy = 0.0;
-        if (in) {
-          py = Pw[y * nslot + s];
-        } else {
-          const int sp = mapped_slot(s, a, dir);
-          if (sp >= 0) {
-            py = Pw[y * nslot + sp];
-            dpy = dPw[y * nslot + sp];
-          }
-        }
-        r = fma(-dT, px - py, r);
-        if (!in) r = fma(t, dpy, r);
-      }
-    }
-    sm.Z[(long long)i * L.nmax + p] = r;
-  }
-  gsync<NT>();
-  stored_solve<NT>(E, sm, L.nmax, L.bmax, fac + E.fac, tid);
-  for (int it = tid; it < E.n * nslot; it += NT) {
-    const int p = it / nslot, s = it - (it / nslot) * nslot;
-    int xc[3];
-    p_coords(E, p, xc);
-    double val = 0.0;
-    if (E.slots & (1 << s)) {
-      int i = 0;
-      for (int q = 0; q < E.nvs; ++q)
-        if (E.vs[q] == s) i = q;
-      val = sm.Z[(long long)i * L.nmax + p];
-    }
-    dPw[cell_id(g, xc) * nslot + s] = val;
+    gsync<NT>();
   }
 }
 
@@ -804,32 +922,78 @@ namespace {
 template <int NT, int G>
 size_t smem_bytes(const DevGeom& g, const LocalLaunch& L) {
   const int nslot = 1 << g.d;
-  return (size_t)G * group_doubles(L.nmax, L.bmax, nslot) * sizeof(double) +
+  return (size_t)G * group_doubles(L.nmax, L.bmax, nslot, L.gw) * sizeof(double) +
          ((size_t)L.npairs * sizeof(unsigned short) + 15) / 16 * 16;
 }
 
-template <int NT, int G, typename K, typename... Args>
-void launch_k(K kern, const DevGeom& g, const LocalLaunch& L, cudaStream_t s, Args... args) {
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// CTAs of one full wave of kernel kern (at least 1, at most what the entities need)
+template <int NT, int G, typename K>
+int wave_ctas(K kern, const DevGeom& g, const LocalLaunch& L) {
   const size_t sh = smem_bytes<NT, G>(g, L);
+  if (sh > kSmemLimit) return 0;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-  const int grid = (L.n_ents + G - 1) / G;
-  kern<<<grid, NT * G, sh, s>>>(g, L, args...);
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT * G, sh) != cudaSuccess)
+    per_sm = 1;
+  if (per_sm < 1) per_sm = 1;
+  if (sms < 1) sms = 1;
+  const long long need = (L.n_ents + G - 1) / G;
+  const long long wave = (long long)sms * per_sm;
+  return (int)(need < wave ? (need > 0 ? need : 1) : wave);
 }
 
-bool big(const LocalLaunch& L) { return L.nmax > 64; }
+template <int NT, int G, typename K, typename... Args>
+void launch_k(K kern, int which, const DevGeom& g, const LocalLaunch& L, cudaStream_t s,
+              Args... args) {
+  const size_t sh = smem_bytes<NT, G>(g, L);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  cudaMemsetAsync(L.counter + which, 0, sizeof(int), s);
+  kern<<<L.grid[which], NT * G, sh, s>>>(g, L, args...);
+}
 }  // namespace
 
 size_t local_smem_bytes(const DevGeom& g, const LocalLaunch& L) {
-  return big(L) ? smem_bytes<256, 1>(g, L) : smem_bytes<32, 4>(g, L);
+  return L.big ? smem_bytes<256, 1>(g, L) : smem_bytes<32, 4>(g, L);
+}
+
+bool local_plan(const DevGeom& g, LocalLaunch& L, int force_gw) {
+  L.big = L.nmax > 64;
+  L.gw = force_gw ? 1 : 0;
+  if (!L.gw && local_smem_bytes(g, L) > kSmemLimit) L.gw = 1;
+  if (local_smem_bytes(g, L) > kSmemLimit) return false;
+  const int nslot = 1 << g.d;
+  L.scratch_group = scratch_group_doubles(L.nmax, L.bmax, nslot, L.gw, L.recompute);
+  if (L.big) {
+    L.grid[0] = wave_ctas<256, 1>(k_local_fwd<256, 1>, g, L);
+    L.grid[1] = wave_ctas<256, 1>(k_local_adj<256, 1>, g, L);
+    L.grid[2] = wave_ctas<256, 1>(k_local_tan<256, 1>, g, L);
+  } else {
+    L.grid[0] = wave_ctas<32, 4>(k_local_fwd<32, 4>, g, L);
+    L.grid[1] = wave_ctas<32, 4>(k_local_adj<32, 4>, g, L);
+    L.grid[2] = wave_ctas<32, 4>(k_local_tan<32, 4>, g, L);
+  }
+  return L.grid[0] > 0 && L.grid[1] > 0 && L.grid[2] > 0;
+}
+
+long long local_scratch_doubles(const LocalLaunch& L) {
+  if (L.scratch_group == 0) return 0;
+  const int G = L.big ? 1 : 4;
+  int gmax = 0;
+  for (int k = 0; k < 3; ++k) gmax = L.grid[k] > gmax ? L.grid[k] : gmax;
+  return (long long)gmax * G * L.scratch_group;
 }
 
 void launch_local_forward(const DevGeom& g, const LocalLaunch& L, const double* T, double* Pw,
                           double* fac, int* status, cudaStream_t s) {
   if (L.n_ents == 0) return;
-  if (big(L))
-    launch_k<256, 1>(k_local_fwd<256, 1>, g, L, s, T, Pw, fac, status);
+  if (L.big)
+    launch_k<256, 1>(k_local_fwd<256, 1>, 0, g, L, s, T, Pw, fac, status);
   else
-    launch_k<32, 4>(k_local_fwd<32, 4>, g, L, s, T, Pw, fac, status);
+    launch_k<32, 4>(k_local_fwd<32, 4>, 0, g, L, s, T, Pw, fac, status);
 }
 
 void launch_local_adjoint(const DevGeom& g, const LocalLaunch& L, const double* T,
@@ -837,20 +1001,22 @@ void launch_local_adjoint(const DevGeom& g, const LocalLaunch& L, const double* 
                           const int* rec_p, const int* rec_u, const double* ZT, double* MU,
                           double* gTloc, cudaStream_t s) {
   if (L.n_ents == 0) return;
-  if (big(L))
-    launch_k<256, 1>(k_local_adj<256, 1>, g, L, s, T, Pw, fac, Lam, rec_p, rec_u, ZT, MU, gTloc);
+  double* f = const_cast<double*>(fac);  // written only in recompute mode (then it is scratch)
+  if (L.big)
+    launch_k<256, 1>(k_local_adj<256, 1>, 1, g, L, s, T, Pw, f, Lam, rec_p, rec_u, ZT, MU, gTloc);
   else
-    launch_k<32, 4>(k_local_adj<32, 4>, g, L, s, T, Pw, fac, Lam, rec_p, rec_u, ZT, MU, gTloc);
+    launch_k<32, 4>(k_local_adj<32, 4>, 1, g, L, s, T, Pw, f, Lam, rec_p, rec_u, ZT, MU, gTloc);
 }
 
 void launch_local_tangent(const DevGeom& g, const LocalLaunch& L, const double* T,
                           const double* Dl, const double* v, const double* Pw,
                           const double* fac, double* dPw, cudaStream_t s) {
   if (L.n_ents == 0) return;
-  if (big(L))
-    launch_k<256, 1>(k_local_tan<256, 1>, g, L, s, T, Dl, v, Pw, fac, dPw);
+  double* f = const_cast<double*>(fac);
+  if (L.big)
+    launch_k<256, 1>(k_local_tan<256, 1>, 2, g, L, s, T, Dl, v, Pw, f, dPw);
   else
-    launch_k<32, 4>(k_local_tan<32, 4>, g, L, s, T, Dl, v, Pw, fac, dPw);
+    launch_k<32, 4>(k_local_tan<32, 4>, 2, g, L, s, T, Dl, v, Pw, f, dPw);
 }
 
 }  // namespace msfv

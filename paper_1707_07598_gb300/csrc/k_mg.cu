@@ -658,28 +658,42 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
   const int m = min(P.m, MAXM);
   long long b, e;
   chunk(n0, c.rank, G, b, e);
-  // levels >= 1 for CTA 0: vectors first, then (when they fit) the stencils and
-  // diagonals copied into shared memory
-  MGLevelDev LV[kMaxLevels];
+  // Level descriptors in shared memory (indexing the kernel parameter or a local array
+  // by a runtime level would put it in per-thread local memory).  Levels >= 1 for CTA 0:
+  // vectors first, then (when they fit) the stencils and diagonals copied into shared
+  // memory.
+  __shared__ MGLevelDev LV[kMaxLevels];
   {
     const int S3 = (D == 3) ? 27 : 9;
     long long vec = 0, mat = 0;
-    for (int l = 0; l < P.nlev; ++l) {
-      LV[l] = P.lev[l];
-      if (l >= 1) {
-        vec += 3 * P.lev[l].n;
-        mat += P.lev[l].n * (S3 + 1);
+#pragma unroll
+    for (int l = 0; l < kMaxLevels; ++l) {
+      if (l < P.nlev) {
+        if (c.tid == 0) LV[l] = P.lev[l];
+        if (l >= 1) {
+          vec += 3 * P.lev[l].n;
+          mat += P.lev[l].n * (S3 + 1);
+        }
       }
     }
+    __syncthreads();
     if (c.rank == 0 && vec + mat <= CSM_CAP) {
       double* q = c.cs + vec;
       for (int l = 1; l < P.nlev; ++l) {
-        const long long na = P.lev[l].n * S3, nd = P.lev[l].n;
-        for (long long t = c.tid; t < na; t += NTH) q[t] = P.lev[l].A[t];
-        for (long long t = c.tid; t < nd; t += NTH) q[na + t] = P.lev[l].dinv[t];
-        LV[l].A = q;
-        LV[l].dinv = q + na;
+        const long long na = LV[l].n * S3, nd = LV[l].n;
+        for (long long t = c.tid; t < na; t += NTH) q[t] = LV[l].A[t];
+        for (long long t = c.tid; t < nd; t += NTH) q[na + t] = LV[l].dinv[t];
         q += na + nd;
+      }
+      __syncthreads();  // every thread has read the global level pointers
+      if (c.tid == 0) {
+        q = c.cs + vec;
+        for (int l = 1; l < P.nlev; ++l) {
+          const long long na = LV[l].n * S3, nd = LV[l].n;
+          LV[l].A = q;
+          LV[l].dinv = q + na;
+          q += na + nd;
+        }
       }
       __syncthreads();
     }

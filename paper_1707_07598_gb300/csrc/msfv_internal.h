@@ -51,13 +51,23 @@ struct EntDesc {
   int rec_cnt;
 };
 
-// Launch-wide parameters of the local-problem kernels.
+// Launch-wide parameters of the local-problem kernels.  The kernels are persistent: a
+// grid of at most one wave of thread groups takes entities from a work counter (largest
+// first, since the entity lists are sorted by cost).
 struct LocalLaunch {
   const EntDesc* ents;
   int n_ents;
   int nmax;           // largest n in this launch
   int bmax;           // largest b in this launch
   int npairs;         // bmax*(bmax+1)/2
+  int big;            // 1: one 256-thread CTA per entity; 0: one warp per entity, 4 per CTA
+  int gw;             // 1: the factor window, right-hand sides and coefficients live in
+                      //    global memory (entities too large for shared memory)
+  int recompute;      // 1: factors are not stored; the derivative kernels refactor
+  int grid[3];        // persistent grid (CTAs) of the forward / adjoint / tangent kernels
+  int* counter;       // 3 work counters (forward / adjoint / tangent), zeroed per launch
+  double* scratch;    // per-group scratch in global memory (null when not needed)
+  long long scratch_group;  // doubles of scratch per thread group
 };
 
 struct DevGeom {
@@ -85,7 +95,13 @@ void launch_face_T(const DevGeom& g, const double* m, double* T, double* sig, cu
 void launch_vertices(const DevGeom& g, double* Pw, cudaStream_t s);
 // Dynamic shared memory one launch of the local kernels needs (bytes).
 size_t local_smem_bytes(const DevGeom& g, const LocalLaunch& L);
-// Basis (forward) local solves; the factors are always stored (fac).
+// Choose shared- or global-memory windows (global when the shared-memory layout does not
+// fit, or when force_gw), the persistent grids and the scratch per group.  Sets L.big,
+// L.gw, L.grid, L.scratch_group; returns false when even the global layout does not fit.
+bool local_plan(const DevGeom& g, LocalLaunch& L, int force_gw);
+// Scratch doubles one launch class needs (all its thread groups).
+long long local_scratch_doubles(const LocalLaunch& L);
+// Basis (forward) local solves; the factors are stored in fac unless L.recompute.
 void launch_local_forward(const DevGeom& g, const LocalLaunch& L, const double* T, double* Pw,
                           double* fac, int* status, cudaStream_t s);
 // adjoint: seeds from receivers (ZT), Lambda and the MU of higher entities

@@ -74,7 +74,10 @@ struct msfv_session {
   double* Pw = nullptr;     // N*S basis weights
   double* X = nullptr;      // N*S: adjoint mu / tangent dP
   double* gT = nullptr;     // d*N transmissibility gradient of the local problems
-  double* fac = nullptr;    // stored local factors
+  double* fac = nullptr;    // stored local factors (null in recompute mode)
+  double* local_scratch = nullptr;  // per-group scratch of the local kernels
+  int* local_ctr = nullptr;         // work counters of the persistent local kernels
+  bool recompute = false;           // local factors recomputed by the derivative kernels
   // coarse and per-source buffers
   double *Ac = nullptr, *dAc = nullptr, *t = nullptr, *rq = nullptr, *lam = nullptr,
          *dt = nullptr, *Lam = nullptr;
@@ -219,8 +222,6 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   for (int i = 0; i < desc->n_rec; ++i)
     if (desc->rec_cell[i] < 0 || desc->rec_cell[i] >= N)
       return fail(nullptr, MSFV_ERR_ARG, "receiver cell out of range");
-  if (desc->factor_mode == 2)
-    return fail(nullptr, MSFV_ERR_ARG, "factor_mode 2 (recompute) is not supported");
   if (desc->factor_mode < 0 || desc->factor_mode > 2)
     return fail(nullptr, MSFV_ERR_ARG, "factor_mode must be 0, 1 or 2");
 
@@ -314,6 +315,8 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       }
   // sort by cost (largest first) and place the stored factors
   long long fac_total = 0;
+  const char* win_env = getenv("MSFV_LOCAL_WINDOW");
+  const int force_gw = (win_env && !strcmp(win_env, "global")) ? 1 : 0;
   for (int k = 1; k <= d; ++k) {
     auto& v = s->h_ents[k];
     std::stable_sort(v.begin(), v.end(), [](const EntDesc& x, const EntDesc& y) {
@@ -337,10 +340,10 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       delete s;
       return fail(nullptr, MSFV_ERR_ARG, "local band too wide (coarsening too large)");
     }
-    if (local_smem_bytes(g, L) > 227 * 1024) {
+    L.recompute = (desc->factor_mode == 2) ? 1 : 0;
+    if (!local_plan(g, L, force_gw)) {
       delete s;
-      return fail(nullptr, MSFV_ERR_ARG,
-                  "coarsening too large for on-chip local problems (3D c <= 11, 2D c <= 32)");
+      return fail(nullptr, MSFV_ERR_ARG, "coarsening too large for the local problems");
     }
     for (int i = 0; i < (int)v.size(); ++i) {
       const EntDesc& e = v[i];
@@ -349,6 +352,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     }
   }
   s->fac_bytes = (size_t)fac_total * sizeof(double);
+  s->recompute = (desc->factor_mode == 2);
   for (const auto& e : s->h_ents[d]) {
     const int nvs = __builtin_popcount((unsigned)e.slots);
     s->int_flops += entity_flops(e, nvs);
@@ -470,12 +474,31 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   const int S3 = (d == 3) ? 27 : 9;
   const size_t Ssz = G.S;
   size_t need = sizeof(double) * ((size_t)2 * d * N + N + 2 * N * Ssz + (size_t)d * N) +
-                s->fac_bytes +
                 sizeof(double) * ((size_t)3 * Nc * S3 + (size_t)5 * s->Ns * Nc +
                                   (size_t)4 * s->Ns * s->Nr + 1 + (size_t)s->Ns * s->Nru +
                                   (size_t)s->Nru * Ssz + 2 * N) +
                 (s->use_mg ? sizeof(double) * ((size_t)s->Ns * (2 * s->mg.m + 3) * Nc + 4 * Nc * S3)
                            : sizeof(double) * (size_t)s->band.ldab * (size_t)s->band.n);
+  // local-problem scratch (one buffer: the classes run one after another on the stream)
+  auto scratch_bytes = [&]() {
+    long long m = 0;
+    for (int k = 1; k <= d; ++k) m = std::max(m, local_scratch_doubles(s->launch[k]));
+    return (size_t)m * sizeof(double);
+  };
+  size_t scr = scratch_bytes();
+  if (!s->recompute && desc->factor_mode == 0 && desc->hbm_budget_bytes &&
+      need + s->fac_bytes + scr > desc->hbm_budget_bytes) {
+    // automatic mode: recompute the local factors in the derivative passes when storing
+    // them does not fit the budget
+    s->recompute = true;
+    for (int k = 1; k <= d; ++k) {
+      s->launch[k].recompute = 1;
+      local_plan(g, s->launch[k], force_gw);
+    }
+    scr = scratch_bytes();
+  }
+  if (s->recompute) s->fac_bytes = 0;
+  need += s->fac_bytes + scr + sizeof(int) * 12;
   if (desc->hbm_budget_bytes && need > desc->hbm_budget_bytes) {
     delete s;
     return fail(nullptr, MSFV_ERR_OOM, "session workspace exceeds hbm_budget_bytes");
@@ -486,7 +509,9 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   s->Pw = dalloc<double>(s, (size_t)N * Ssz, &ce);
   s->X = dalloc<double>(s, (size_t)N * Ssz, &ce);
   s->gT = dalloc<double>(s, (size_t)d * N, &ce);
-  s->fac = dalloc<double>(s, (size_t)fac_total, &ce);
+  if (!s->recompute) s->fac = dalloc<double>(s, (size_t)fac_total, &ce);
+  if (scr) s->local_scratch = dalloc<double>(s, scr / sizeof(double), &ce);
+  s->local_ctr = dalloc<int>(s, 12, &ce);
   s->Ac = dalloc<double>(s, (size_t)Nc * S3, &ce);
   s->dAc = dalloc<double>(s, (size_t)Nc * S3, &ce);
   s->Lam = dalloc<double>(s, (size_t)Nc * S3, &ce);
@@ -576,7 +601,11 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     delete s;
     return fail(nullptr, MSFV_ERR_CUDA, msg);
   }
-  for (int k = 1; k <= d; ++k) s->launch[k].ents = s->d_ents[k];
+  for (int k = 1; k <= d; ++k) {
+    s->launch[k].ents = s->d_ents[k];
+    s->launch[k].counter = s->local_ctr + 3 * k;
+    s->launch[k].scratch = s->launch[k].scratch_group ? s->local_scratch : nullptr;
+  }
   *out = s;
   return MSFV_OK;
 }
@@ -828,11 +857,13 @@ extern "C" int msfv_info(const msfv_session_t* s, int64_t* out, int n_out) {
         it[1] = std::max<int64_t>(it[1], h[s->Ns + j]);
       }
   }
-  int64_t v[11] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
+  int gw = 0;
+  for (int k = 1; k <= s->dg.d; ++k) gw |= s->launch[k].gw ? (1 << k) : 0;
+  int64_t v[13] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
                    (int64_t)(s->h_ents[1].size() + s->h_ents[2].size() + s->h_ents[3].size()),
                    (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, s->use_mg ? 1 : 0, it[0], it[1],
-                   s->use_mg ? s->mg.group : 0};
-  for (int i = 0; i < n_out && i < 11; ++i) out[i] = v[i];
+                   s->use_mg ? s->mg.group : 0, s->recompute ? 1 : 0, gw};
+  for (int i = 0; i < n_out && i < 13; ++i) out[i] = v[i];
   return MSFV_OK;
 }
 

@@ -205,10 +205,11 @@ class Session:
 
     # -- introspection ----------------------------------------------------------------
     def info(self) -> dict:
-        out = (ctypes.c_int64 * 11)()
-        self._check(self._lib.msfv_info(self._h, out, 11))
+        out = (ctypes.c_int64 * 13)()
+        self._check(self._lib.msfv_info(self._h, out, 13))
         keys = ["N", "Nc", "Ns", "Nr", "n_local_problems", "workspace_bytes", "factor_bytes",
-                "coarse_solver", "coarse_iters", "coarse_iters_T", "coarse_group_ctas"]
+                "coarse_solver", "coarse_iters", "coarse_iters_T", "coarse_group_ctas",
+                "recompute", "global_window_mask"]
         return dict(zip(keys, list(out)))
 
     def profile(self, enable: bool = True):

@@ -65,8 +65,8 @@ def _desc(**kw):
     (dict(nr=0), "n_rec"),
     (dict(same=True), "pos == neg"),
     (dict(badrec=True), "receiver"),
-    (dict(fm=2), "recompute"),
-    (dict(dim=3, n=(48, 48, 48), c=16), "coarsening too large"),
+    (dict(fm=3), "factor_mode"),
+    (dict(dim=3, n=(34, 34, 34), c=17), "too wide"),
     (dict(budget=1000), "hbm_budget"),
 ])
 def test_setup_rejects_bad_descriptors_on_the_host(lib, kw, frag):

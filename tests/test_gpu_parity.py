@@ -51,13 +51,13 @@ CASES = [
 ]
 
 
-def run_pair(prob, m, dev, seed=0):
+def run_pair(prob, m, dev, seed=0, factor_mode=0):
     orc = Oracle(prob)
     st = orc.forward(m)
     d_obs = st['d'] * 1.02 + W.noise_like(st['d'].shape, 1e-3 * np.abs(st['d']).max(), seed + 1)
     phi_ref, g_ref = orc.misfit_gradient(st, d_obs)
     from paper_1707_07598_gb300.msfv import Session
-    s = Session(prob)
+    s = Session(prob, factor_mode=factor_mode)
     mt = torch.from_numpy(m).to(dev)
     u = torch.empty((prob.n_src, prob.N), dtype=torch.float64, device=dev)
     d = s.forward(mt, u=u)
@@ -202,3 +202,66 @@ def test_both_coarse_solvers_match_oracle(dev, monkeypatch, solver, n, c, ns, nr
     v = W.noise_like(prob.N, 1.0, 53)
     assert rel(s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy(), orc.jvec(st, v)) < TOL
     s.close()
+
+
+@pytest.mark.parametrize("window", ["shared", "global"])
+@pytest.mark.parametrize("fm", [1, 2])
+@pytest.mark.parametrize("n,c,ns,nr", [((20, 15), 5, 2, 8), ((32, 32), 8, 2, 16),
+                                       ((9, 9, 6), 3, 2, 7), ((16, 16, 16), 8, 3, 20),
+                                       ((24, 16, 16), 8, 4, 30)])
+def test_factor_modes_and_windows_match_oracle(dev, monkeypatch, window, fm, n, c, ns, nr):
+    """Stored or recomputed local factors, shared- or global-memory factor windows."""
+    if window == "global":
+        monkeypatch.setenv("MSFV_LOCAL_WINDOW", "global")
+    prob = W.make_problem(n, c, ns, nr, seed=71, top_layer=len(n) == 3)
+    m = W.gaussian_random_field(n, 0.2, 72)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev, factor_mode=fm)
+    info = s.info()
+    assert info["recompute"] == (1 if fm == 2 else 0)
+    assert (info["global_window_mask"] != 0) == (window == "global")
+    assert (info["factor_bytes"] == 0) == (fm == 2)
+    assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
+    assert abs(phi - phi_ref) <= TOL * abs(phi_ref)
+    v = W.noise_like(prob.N, 1.0, 73)
+    w = W.noise_like((prob.n_src, prob.n_rec), 1.0, 74)
+    assert rel(s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy(), orc.jvec(st, v)) < TOL
+    assert rel(s.jtvec(torch.from_numpy(w).to(dev)).cpu().numpy(), orc.jtvec(st, w)) < TOL
+    s.close()
+
+
+@pytest.mark.parametrize("fm", [1, 2])
+@pytest.mark.parametrize("n,ns,nr", [((32, 32, 32), 2, 16), ((48, 32, 16), 3, 20),
+                                     ((64, 64, 64), 4, 64)])
+def test_coarsening_16_in_3d_matches_oracle(dev, fm, n, ns, nr):
+    """c = 16 in 3D: dual-cell interiors of up to 15^3 unknowns, half bandwidth 225,
+    factored in global memory."""
+    prob = W.make_problem(n, 16, ns, nr, seed=81, top_layer=True)
+    m = W.gaussian_random_field(n, 0.15, 82)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev, factor_mode=fm)
+    assert s.info()["global_window_mask"] & (1 << 3)
+    assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
+    v = W.noise_like(prob.N, 1.0, 83)
+    assert rel(s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy(), orc.jvec(st, v)) < TOL
+    s.close()
+
+
+def test_auto_factor_mode_recomputes_under_a_tight_budget(dev):
+    """Automatic factor mode: stores the factors when they fit, recomputes them when the
+    budget is a quarter of the factor bytes short of the stored-factor workspace
+    (recompute keeps one largest factor per resident thread group, 63 MB for 456 groups,
+    against 0.2 GB of stored factors for the 2197 interiors at 96^3)."""
+    prob = W.make_problem((96, 96, 96), 8, 4, 32, seed=91, top_layer=True)
+    m = W.gaussian_random_field(prob.n, 0.2, 92)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
+    info = s.info()
+    assert info["recompute"] == 0 and info["factor_bytes"] > 0
+    budget = info["workspace_bytes"] - info["factor_bytes"] // 4
+    s.close()
+    from paper_1707_07598_gb300.msfv import Session
+    s2 = Session(prob, factor_mode=0, hbm_budget_bytes=budget)
+    assert s2.info()["recompute"] == 1 and s2.info()["workspace_bytes"] <= budget
+    mt = torch.from_numpy(m).to(dev)
+    d2 = s2.forward(mt).cpu().numpy()
+    phi2, g2 = s2.adjoint(torch.from_numpy(d_obs).to(dev))
+    assert rel(d2, st['d']) < TOL and rel(g2.cpu().numpy(), g_ref) < TOL
+    s2.close()
