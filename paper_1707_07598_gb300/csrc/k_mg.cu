@@ -487,16 +487,11 @@ __device__ __noinline__ void gram_schmidt(Ctx& c, double* V, long long n0, long 
 // Levels >= 1 of the V-cycle inside one CTA, vectors in shared memory.
 // in: rs (level-1 right-hand side); out: xs (level-1 correction).
 template <int D>
-__device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV, double* mem) {
+__device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV,
+                              const long long* off, double* mem) {
   const int tr = P.transpose;
   const double om = P.omega;
   // per level l >= 1: r, x, s at offsets off[l] (3 n_l doubles each)
-  long long off[kMaxLevels];
-  long long o = 0;
-  for (int l = 1; l < P.nlev; ++l) {
-    off[l] = o;
-    o += 3 * LV[l].n;
-  }
   for (int l = 1; l < P.nlev - 1; ++l) {
     const MGLevelDev& L = LV[l];
     double* r = mem + off[l];
@@ -549,7 +544,7 @@ __device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV
 // run inside CTA 0 of the group (shared memory) when they fit, else on the group.
 template <int D>
 __device__ __forceinline__ void vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV,
-                                       const double* r0, double* x0, double* s0, double* x1g) {
+                                       const long long* LOFF, const double* r0, double* x0, double* s0, double* x1g) {
   const int tr = P.transpose;
   const double om = P.omega;
   const MGLevelDev& L = P.lev[0];
@@ -591,7 +586,7 @@ __device__ __forceinline__ void vcycle(Ctx& c, const MGParamsDev& P, const MGLev
     double* r1 = c.cs;
     for (long long K = c.tid; K < C.n; K += NTH) r1[K] = restrict_row<D>(L, C, K, Vec{nullptr, s0, 0});
     __syncthreads();
-    coarse_vcycle<D>(c, P, LV, c.cs);
+    coarse_vcycle<D>(c, P, LV, LOFF, c.cs);
     const double* x1 = c.cs + C.n;
     for (long long K = c.tid; K < C.n; K += NTH) x1g[K] = x1[K];
   }
@@ -663,13 +658,20 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
   // vectors first, then (when they fit) the stencils and diagonals copied into shared
   // memory.
   __shared__ MGLevelDev LV[kMaxLevels];
+  __shared__ long long LOFF[kMaxLevels];  // offsets of the level-l vectors in the coarse memory
+  // coarse-level vectors of this group: shared memory, or global memory when they do not
+  // fit there (then the stencils stay in global memory too)
+  if (P.cws) c.cs = P.cws + (long long)grp * P.cws_stride;
   {
     const int S3 = (D == 3) ? 27 : 9;
     long long vec = 0, mat = 0;
 #pragma unroll
     for (int l = 0; l < kMaxLevels; ++l) {
       if (l < P.nlev) {
-        if (c.tid == 0) LV[l] = P.lev[l];
+        if (c.tid == 0) {
+          LV[l] = P.lev[l];
+          LOFF[l] = vec;
+        }
         if (l >= 1) {
           vec += 3 * P.lev[l].n;
           mat += P.lev[l].n * (S3 + 1);
@@ -677,7 +679,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
       }
     }
     __syncthreads();
-    if (c.rank == 0 && vec + mat <= CSM_CAP) {
+    if (c.rank == 0 && !P.cws && vec + mat <= CSM_CAP) {
       double* q = c.cs + vec;
       for (int l = 1; l < P.nlev; ++l) {
         const long long na = LV[l].n * S3, nd = LV[l].n;
@@ -757,7 +759,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
           double* vk = V + (long long)k * n0;
           double* zk = Z + (long long)k * n0;
           double* w = V + (long long)(k + 1) * n0;
-          vcycle<D>(c, P, LV, vk, zk, s0, x1g);
+          vcycle<D>(c, P, LV, LOFF, vk, zk, s0, x1g);
           ++iters;
           c.tag = 90;
           {
@@ -852,11 +854,13 @@ void mg_setup_levels(MGHost& H, const DevGeom& g) {
   }
 }
 
-bool mg_coarse_fits(const MGHost& H) {
+long long mg_coarse_doubles(const MGHost& H) {
   long long need = 0;
   for (int l = 1; l < H.nlev; ++l) need += 3 * H.lev[l].n;
-  return need <= CSM_CAP;
+  return need;
 }
+
+bool mg_coarse_fits(const MGHost& H) { return mg_coarse_doubles(H) <= CSM_CAP; }
 
 void launch_mg_setup(const MGHost& H, int* status, cudaStream_t s) {
   const int S3 = H.d == 3 ? 27 : 9;
@@ -928,6 +932,8 @@ cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose,
   P.iters = H.iters;
   P.trace = H.trace;
   P.trace_cap = H.trace_cap;
+  P.cws = H.cws;
+  P.cws_stride = H.cws_stride;
   const size_t dyn = mg_dyn_smem();
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

@@ -178,6 +178,8 @@ struct MGHost {
   int trace_cap = 0;
   int group = 1, ngroups = 1; // cluster size (CTAs per right-hand side), clusters launched
   int max_clusters = 0;       // co-resident clusters (occupancy API)
+  double* cws = nullptr;      // coarse-level vectors in global memory, one block per cluster
+  long long cws_stride = 0;   //   group, when they do not fit in shared memory
 };
 struct MGParamsDev {
   int d, nlev;
@@ -195,9 +197,14 @@ struct MGParamsDev {
   int* iters;
   long long* trace;
   int trace_cap;
+  double* cws;          // global coarse-level vectors per cluster group (null: on chip)
+  long long cws_stride;
 };
 void mg_setup_levels(MGHost& H, const DevGeom& g);
+// true when the vectors of levels >= 1 fit in one CTA's shared memory
 bool mg_coarse_fits(const MGHost& H);
+// doubles of the vectors of levels >= 1 (per cluster group)
+long long mg_coarse_doubles(const MGHost& H);
 int mg_pick_cluster(int d, int Ns, int* max_clusters);
 void launch_mg_setup(const MGHost& H, int* status, cudaStream_t s);
 // rhs: Ns x Nc, solved in place (pinned: entry 0 of each solution is zero);

@@ -461,14 +461,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     const char* env = getenv("MSFV_COARSE_SOLVER");
     if (env && !strcmp(env, "band")) s->use_mg = false;
     if (env && !strcmp(env, "mg")) s->use_mg = true;
-    if (s->use_mg) {
-      mg_setup_levels(s->mg, g);
-      if (!mg_coarse_fits(s->mg)) {
-        delete s;
-        return fail(nullptr, MSFV_ERR_ARG,
-                    "coarse mesh too large for the on-chip multigrid levels (Nc <= ~38000)");
-      }
-    }
+    if (s->use_mg) mg_setup_levels(s->mg, g);
   }
   // ---- HBM budget and allocations --------------------------------------------------
   const int S3 = (d == 3) ? 27 : 9;
@@ -568,6 +561,12 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       return fail(nullptr, MSFV_ERR_CUDA, "thread-block clusters unavailable for the coarse solver");
     }
     H.ngroups = std::max(1, std::min(s->Ns, std::max(1, H.max_clusters)));
+    const char* cg_env = getenv("MSFV_MG_COARSE_GLOBAL");
+    if (!mg_coarse_fits(H) || (cg_env && atoi(cg_env) > 0)) {
+      // coarse-level vectors in global memory, one block per cluster group
+      H.cws_stride = (mg_coarse_doubles(H) + 31) & ~31LL;
+      H.cws = dalloc<double>(s, (size_t)H.ngroups * H.cws_stride, &ce);
+    }
   }
   for (int k = 1; k <= d; ++k) s->d_ents[k] = dalloc<EntDesc>(s, s->h_ents[k].size(), &ce);
   if (ce != cudaSuccess) {

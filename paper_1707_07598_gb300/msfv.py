@@ -71,6 +71,8 @@ def load(path: Optional[str] = None):
     L.msfv_coarse_trace.argtypes = [vp, i64p, ctypes.c_int]
     L.msfv_launch_count.argtypes = [vp]
     L.msfv_launch_count.restype = ctypes.c_int64
+    L.msfv_misfit_static.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
+    L.msfv_misfit_static.restype = ctypes.c_int
     for f in ("msfv_setup", "msfv_forward", "msfv_adjoint", "msfv_jvec", "msfv_jtvec",
               "msfv_solve_host", "msfv_destroy", "msfv_set_stream", "msfv_info", "msfv_profile",
               "msfv_phase_times", "msfv_phase_name", "msfv_coarse_trace"):
@@ -136,6 +138,7 @@ class Session:
         if rc != MSFV_OK:
             raise MSFVError(rc, L.msfv_last_error(None).decode())
         self._h = h
+        self.version = 0   # bumped by every forward: derivative calls refer to the last one
 
     # -- helpers ------------------------------------------------------------------
     def _check(self, rc):
@@ -163,6 +166,7 @@ class Session:
             d_pred = torch.empty((self.Ns, self.Nr), dtype=torch.float64, device=m.device)
         self._check(self._lib.msfv_forward(self._h, _ptr(m), _ptr(d_pred),
                                            _ptr(u) if u is not None else None))
+        self.version += 1
         return d_pred
 
     def adjoint(self, d_obs, grad=None, want_phi: bool = True):
@@ -234,3 +238,20 @@ class Session:
 
     def launch_count(self) -> int:
         return int(self._lib.msfv_launch_count(self._h))
+
+
+def misfit_static(d_pred, d_obs, r=None, phi=None, stream=None):
+    """phi = 1/2 ||d_pred - d_obs||^2 (device scalar) and optionally r = d_pred - d_obs,
+    through msfv_misfit_static: no device allocation inside the call."""
+    import torch
+    L = load()
+    if phi is None:
+        phi = torch.empty((), dtype=torch.float64, device=d_pred.device)
+    if d_pred.shape != d_obs.shape:
+        raise ValueError("d_pred and d_obs must have the same shape")
+    rc = L.msfv_misfit_static(_ptr(d_pred), _ptr(d_obs), d_pred.numel(),
+                              _ptr(r) if r is not None else None, _ptr(phi),
+                              ctypes.c_void_p(_stream_handle(stream)))
+    if rc != MSFV_OK:
+        raise MSFVError(rc, L.msfv_last_error(None).decode())
+    return phi

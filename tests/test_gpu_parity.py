@@ -265,3 +265,43 @@ def test_auto_factor_mode_recomputes_under_a_tight_budget(dev):
     phi2, g2 = s2.adjoint(torch.from_numpy(d_obs).to(dev))
     assert rel(d2, st['d']) < TOL and rel(g2.cpu().numpy(), g_ref) < TOL
     s2.close()
+
+
+@pytest.mark.parametrize("n,c,ns,nr", [((16, 16, 16), 4, 3, 20), ((24, 16, 16), 8, 4, 30),
+                                       ((32, 32), 4, 2, 16)])
+def test_multigrid_with_coarse_levels_in_global_memory(dev, monkeypatch, n, c, ns, nr):
+    """The multigrid levels >= 1 kept in global memory (as for coarse meshes whose level
+    vectors do not fit in one CTA's shared memory) reproduce the oracle."""
+    monkeypatch.setenv("MSFV_COARSE_SOLVER", "mg")
+    monkeypatch.setenv("MSFV_MG_COARSE_GLOBAL", "1")
+    prob = W.make_problem(n, c, ns, nr, seed=131, top_layer=len(n) == 3)
+    m = W.gaussian_random_field(n, 0.2, 132)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
+    assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
+    s.close()
+
+
+def test_large_coarse_mesh_192_c4(dev):
+    """192^3, c = 4: 110592 coarse unknowns, multigrid levels in global memory.  Too large
+    for the oracle; checked by the adjoint identity <w, J v> = <J^T w, v> and by the
+    gradient matching J^T r."""
+    from paper_1707_07598_gb300.msfv import Session
+    prob = W.make_problem((192, 192, 192), 4, 8, 64, seed=141, top_layer=True)
+    m = torch.from_numpy(W.gaussian_random_field(prob.n, 0.1, 142)).to(dev)
+    s = Session(prob)
+    info = s.info()
+    assert info["Nc"] == 48 ** 3 and info["coarse_solver"] == 1
+    d = s.forward(m)
+    assert torch.isfinite(d).all()
+    d_obs = d * 1.02
+    phi, g = s.adjoint(d_obs)
+    assert s.info()["coarse_iters"] > 0
+    v = torch.from_numpy(W.noise_like(prob.N, 1.0, 143)).to(dev)
+    w = torch.from_numpy(W.noise_like((prob.n_src, prob.n_rec), 1.0, 144)).to(dev)
+    jv = s.jvec(v)
+    jtw = s.jtvec(w)
+    lhs, rhs = float((w * jv).sum()), float(jtw @ v)
+    assert abs(lhs - rhs) <= 1e-10 * float(w.norm() * jv.norm())
+    jtr = s.jtvec((d - d_obs).contiguous())
+    assert float((jtr - g).norm()) <= 1e-12 * float(g.norm())
+    s.close()
