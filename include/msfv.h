@@ -146,6 +146,34 @@ int msfv_solve_host(msfv_session_t* s, const double* m_host, const double* d_obs
 int msfv_misfit_static(const double* d_pred_dev, const double* d_obs_dev, int64_t count,
                        double* r_dev, double* phi_dev, void* stream);
 
+/* ---- batches (several instances, one CUDA graph) -----------------------------------
+ * Captures one forward + gradient step (msfv_forward then msfv_adjoint without phi) of K
+ * independent sessions as one CUDA graph: the K instances run as parallel branches, so
+ * the device overlaps one instance's latency-bound phases (the coarse solve) with
+ * another's local solves, and the whole step is one graph launch.  The pointers are
+ * captured: msfv_batch_run replays the step on the same buffers, so callers refresh
+ * m_dev[k] / d_obs_dev[k] in place between runs.
+ *   sessions   K distinct sessions (any meshes, coarsening factors and sources)
+ *   m_dev[k], d_obs_dev[k]         inputs of instance k (device, read at every run)
+ *   d_pred_dev[k], grad_dev[k]     outputs of instance k (device, written at every run)
+ *   stream     cudaStream_t (NULL = legacy default) the runs are ordered on: a run starts
+ *              after the work enqueued on stream before it, and work enqueued on stream
+ *              after msfv_batch_run waits for the run; the graph itself is launched on
+ *              a stream the batch owns, and the instances run on streams it owns
+ * Creation synchronises the sessions' streams and captures (no work runs).  Sessions must
+ * outlive the batch and must not be used on their own while a run is in flight.
+ * msfv_batch_run enqueues one step; msfv_batch_check synchronises the stream and reports
+ * the first instance whose local pivots or coarse solve failed (MSFV_ERR_NUMERIC). */
+typedef struct msfv_batch msfv_batch_t;
+int msfv_batch_create(msfv_session_t* const* sessions, int K, const double* const* m_dev,
+                      const double* const* d_obs_dev, double* const* d_pred_dev,
+                      double* const* grad_dev, void* stream, msfv_batch_t** out);
+int msfv_batch_run(msfv_batch_t* b);
+int msfv_batch_check(msfv_batch_t* b);
+int msfv_batch_destroy(msfv_batch_t* b);
+/* Last error of the batch (or of the last failed msfv_batch_create when b is NULL). */
+const char* msfv_batch_last_error(const msfv_batch_t* b);
+
 /* Free the session and its device workspace (synchronises its stream). NULL is ok. */
 int msfv_destroy(msfv_session_t* s);
 

@@ -141,12 +141,14 @@ struct PhaseScope {
   }
 };
 
+// Stream-ordered allocations on the session stream: creating or destroying a session does
+// not wait for work other sessions have in flight on the device.
 template <class T>
 T* dalloc(msfv_session* s, size_t count, cudaError_t* err) {
   void* p = nullptr;
   if (*err != cudaSuccess) return nullptr;
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-  *err = cudaMalloc(&p, bytes);
+  *err = cudaMallocAsync(&p, bytes, s->stream);
   if (*err != cudaSuccess) return nullptr;
   s->allocs.push_back(p);
   s->ws_bytes += bytes;
@@ -160,7 +162,8 @@ cudaError_t upload(T* dst, const std::vector<T>& v, cudaStream_t st) {
 }
 
 void free_all(msfv_session* s) {
-  for (void* p : s->allocs) cudaFree(p);
+  for (void* p : s->allocs) cudaFreeAsync(p, s->stream);
+  cudaStreamSynchronize(s->stream);
   s->allocs.clear();
   for (auto& e : s->pending) {
     cudaEventDestroy(e.a);
@@ -918,3 +921,160 @@ extern "C" const char* msfv_phase_name(int k) {
 extern "C" double msfv_interior_flops(const msfv_session_t* s) { return s ? s->int_flops : 0.0; }
 
 extern "C" int64_t msfv_launch_count(const msfv_session_t* s) { return s ? s->launches : 0; }
+
+// =============================================================================
+// batches: one forward + gradient step of several sessions captured as one CUDA graph
+// =============================================================================
+struct msfv_batch {
+  std::vector<msfv_session*> ss;
+  std::vector<cudaStream_t> branch;  // one stream per instance, owned by the batch
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // order the graph after / before the caller's stream
+  cudaStream_t stream = nullptr;     // the caller's stream
+  cudaStream_t origin = nullptr;     // the batch's own stream: capture and graph launches
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string err;
+};
+
+namespace {
+std::string g_batch_error;
+
+void batch_release(msfv_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  for (auto st : b->branch) cudaStreamDestroy(st);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  b->origin = nullptr;
+  b->join.clear();
+  b->branch.clear();
+}
+
+int batch_fail(msfv_batch* b, int code, const std::string& msg) {
+  if (b) {
+    b->err = msg;
+    batch_release(b);
+    delete b;
+  }
+  g_batch_error = msg;
+  return code;
+}
+}  // namespace
+
+extern "C" int msfv_batch_create(msfv_session_t* const* sessions, int K,
+                                 const double* const* m_dev, const double* const* d_obs_dev,
+                                 double* const* d_pred_dev, double* const* grad_dev, void* stream,
+                                 msfv_batch_t** out) {
+  if (!out) return batch_fail(nullptr, MSFV_ERR_ARG, "msfv_batch_create: out is NULL");
+  *out = nullptr;
+  if (K < 1 || !sessions || !m_dev || !d_obs_dev || !d_pred_dev || !grad_dev)
+    return batch_fail(nullptr, MSFV_ERR_ARG, "msfv_batch_create: empty batch or NULL array");
+  for (int k = 0; k < K; ++k) {
+    if (!sessions[k] || !m_dev[k] || !d_obs_dev[k] || !d_pred_dev[k] || !grad_dev[k])
+      return batch_fail(nullptr, MSFV_ERR_ARG, "msfv_batch_create: NULL entry");
+    for (int q = 0; q < k; ++q)
+      if (sessions[q] == sessions[k])
+        return batch_fail(nullptr, MSFV_ERR_ARG, "msfv_batch_create: a session appears twice");
+  }
+  msfv_batch* b = new msfv_batch();
+  b->stream = static_cast<cudaStream_t>(stream);
+  b->ss.assign(sessions, sessions + K);
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->branch.push_back(st);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->join.push_back(ev);
+  }
+  if (e != cudaSuccess)
+    return batch_fail(b, MSFV_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e));
+  // every session's previous work is complete before the capture starts
+  for (auto s : b->ss) cudaStreamSynchronize(s->stream);
+  e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess)
+    return batch_fail(b, MSFV_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  int rc = MSFV_OK;
+  std::string msg;
+  e = cudaEventRecord(b->fork, b->origin);
+  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
+    msfv_session* s = b->ss[k];
+    const cudaStream_t old = s->stream;
+    const bool prof = s->prof;
+    s->prof = false;
+    s->stream = b->branch[k];
+    e = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+    if (e == cudaSuccess) rc = msfv_forward(s, m_dev[k], d_pred_dev[k], nullptr);
+    if (e == cudaSuccess && rc == MSFV_OK) rc = msfv_adjoint(s, d_obs_dev[k], grad_dev[k], nullptr);
+    if (rc != MSFV_OK) msg = s->err;
+    if (e == cudaSuccess) e = cudaEventRecord(b->join[k], b->branch[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+    s->stream = old;
+    s->prof = prof;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
+  b->graph = g;
+  if (rc != MSFV_OK) return batch_fail(b, rc, "batch capture: " + msg);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return batch_fail(b, MSFV_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return MSFV_OK;
+}
+
+extern "C" int msfv_batch_run(msfv_batch_t* b) {
+  if (!b) return MSFV_ERR_ARG;
+  cudaError_t e = cudaEventRecord(b->ev_in, b->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev_in, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->origin);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->origin);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_out, 0);
+  if (e != cudaSuccess) {
+    b->err = std::string("graph launch: ") + cudaGetErrorString(e);
+    return MSFV_ERR_CUDA;
+  }
+  return MSFV_OK;
+}
+
+extern "C" int msfv_batch_check(msfv_batch_t* b) {
+  if (!b) return MSFV_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    b->err = std::string("batch sync: ") + cudaGetErrorString(e);
+    return MSFV_ERR_CUDA;
+  }
+  for (size_t k = 0; k < b->ss.size(); ++k) {
+    const int rc = read_status(b->ss[k]);
+    if (rc != MSFV_OK) {
+      b->err = "instance " + std::to_string(k) + ": " + b->ss[k]->err;
+      return rc;
+    }
+  }
+  return MSFV_OK;
+}
+
+extern "C" int msfv_batch_destroy(msfv_batch_t* b) {
+  if (!b) return MSFV_OK;
+  cudaStreamSynchronize(b->origin);
+  cudaStreamSynchronize(b->stream);
+  batch_release(b);
+  delete b;
+  return MSFV_OK;
+}
+
+extern "C" const char* msfv_batch_last_error(const msfv_batch_t* b) {
+  return b ? b->err.c_str() : g_batch_error.c_str();
+}

@@ -73,6 +73,15 @@ def load(path: Optional[str] = None):
     L.msfv_launch_count.restype = ctypes.c_int64
     L.msfv_misfit_static.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
     L.msfv_misfit_static.restype = ctypes.c_int
+    L.msfv_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    vp, ctypes.POINTER(vp)]
+    L.msfv_batch_create.restype = ctypes.c_int
+    for f in ("msfv_batch_run", "msfv_batch_check", "msfv_batch_destroy"):
+        getattr(L, f).argtypes = [vp]
+        getattr(L, f).restype = ctypes.c_int
+    L.msfv_batch_last_error.argtypes = [vp]
+    L.msfv_batch_last_error.restype = ctypes.c_char_p
     for f in ("msfv_setup", "msfv_forward", "msfv_adjoint", "msfv_jvec", "msfv_jtvec",
               "msfv_solve_host", "msfv_destroy", "msfv_set_stream", "msfv_info", "msfv_profile",
               "msfv_phase_times", "msfv_phase_name", "msfv_coarse_trace"):
@@ -255,3 +264,62 @@ def misfit_static(d_pred, d_obs, r=None, phi=None, stream=None):
     if rc != MSFV_OK:
         raise MSFVError(rc, L.msfv_last_error(None).decode())
     return phi
+
+
+class Batch:
+    """One forward + gradient step of several sessions captured as one CUDA graph
+    (msfv_batch_*).  The graph reads m[k] / d_obs[k] and writes d_pred[k] / grad[k] in
+    place at every run, so refresh the inputs in place between runs."""
+
+    def __init__(self, sessions, m, d_obs, d_pred=None, grad=None, stream=None):
+        import torch
+        L = load()
+        self._lib = L
+        K = len(sessions)
+        if not (len(m) == len(d_obs) == K):
+            raise ValueError("one m and one d_obs per session")
+        self.sessions = list(sessions)
+        self.m = list(m)
+        self.d_obs = list(d_obs)
+        self.d_pred = list(d_pred) if d_pred is not None else [
+            torch.empty((s.Ns, s.Nr), dtype=torch.float64, device=mm.device)
+            for s, mm in zip(sessions, m)]
+        self.grad = list(grad) if grad is not None else [
+            torch.empty(s.N, dtype=torch.float64, device=mm.device) for s, mm in zip(sessions, m)]
+        arr = lambda xs: (ctypes.c_void_p * K)(*[ctypes.c_void_p(v) for v in xs])  # noqa: E731
+        h = ctypes.c_void_p()
+        self._h = None
+        self._stream = stream
+        rc = L.msfv_batch_create(arr([s._h.value for s in sessions]), K,
+                                 arr([_ptr(t) for t in self.m]), arr([_ptr(t) for t in self.d_obs]),
+                                 arr([_ptr(t) for t in self.d_pred]),
+                                 arr([_ptr(t) for t in self.grad]),
+                                 ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h))
+        if rc != MSFV_OK:
+            raise MSFVError(rc, L.msfv_batch_last_error(None).decode())
+        self._h = h
+        for s in sessions:
+            s.version += 1
+
+    def run(self):
+        rc = self._lib.msfv_batch_run(self._h)
+        if rc != MSFV_OK:
+            raise MSFVError(rc, self._lib.msfv_batch_last_error(self._h).decode())
+        for s in self.sessions:
+            s.version += 1
+
+    def check(self):
+        rc = self._lib.msfv_batch_check(self._h)
+        if rc != MSFV_OK:
+            raise MSFVError(rc, self._lib.msfv_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.msfv_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,289 @@
+"""Request loop for served MSFV forward + gradient solves (continuous batching).
+
+Requests (``workloads.RequestSpec``) arrive over time; each is one forward + gradient
+solve of a client's instance.  A client's requests are successive Gauss-Newton
+iterations on one mesh and survey, so they reuse one device-resident session (its stored
+local factors, coarse hierarchy and buffers) and run in order.  The loop
+
+* admits a request as soon as its client's session is idle and an in-flight slot is
+  free, or, for a new client, as soon as its session fits the HBM budget (idle sessions
+  are evicted least recently used first to make room; a session that cannot fit even in
+  an empty budget is rejected);
+* runs every admitted request on its session's own CUDA stream, so requests that arrive
+  while others are on the GPU overlap with them on the device;
+* records arrival, start and finish times, so it reports p50 / p99 latency and the
+  throughput beside those of the plain one-at-a-time path.
+
+The scheduling logic is independent of the GPU: ``Server`` drives a backend object
+(``GpuBackend`` here, a simulated one in the CPU tests).
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+
+class DoesNotFit(Exception):
+    """The backend cannot open a session within the given byte budget."""
+
+
+@dataclass
+class Slot:
+    client: int
+    handle: object
+    nbytes: int
+    busy: bool = False
+    last_used: float = 0.0
+
+
+@dataclass
+class Record:
+    rid: int
+    client: int
+    arrival: float
+    start: float = float("nan")
+    finish: float = float("nan")
+    status: str = "queued"      # queued / running / done / rejected
+    result: object = None
+
+    @property
+    def latency(self) -> float:
+        return self.finish - self.arrival
+
+
+@dataclass
+class Stats:
+    records: List[Record]
+    makespan: float
+    evictions: int
+    opened: int
+    peak_bytes: int
+
+    def done(self) -> List[Record]:
+        return [r for r in self.records if r.status == "done"]
+
+    @property
+    def throughput(self) -> float:
+        d = self.done()
+        return len(d) / self.makespan if self.makespan > 0 else 0.0
+
+    def percentile(self, q: float) -> float:
+        lat = [r.latency for r in self.done()]
+        return float(np.percentile(lat, q)) if lat else float("nan")
+
+
+class Server:
+    """Continuous-batching request loop over a backend with open / launch / done / close.
+
+    max_inflight = 1 gives the plain one-at-a-time path (no overlap), with the same
+    admission and eviction rules."""
+
+    def __init__(self, backend, budget_bytes: int, max_inflight: int = 8,
+                 clock: Callable[[], float] = time.perf_counter, idle_sleep: float = 2e-4,
+                 keep_results: bool = False, sleep: Callable[[float], None] = time.sleep):
+        self.backend = backend
+        self.budget = int(budget_bytes)
+        self.max_inflight = max(1, int(max_inflight))
+        self.clock = clock
+        self.sleep = sleep
+        self.idle_sleep = idle_sleep
+        self.keep_results = keep_results
+
+    # -- memory ---------------------------------------------------------------------
+    def _used(self, slots: Dict[int, Slot]) -> int:
+        return sum(s.nbytes for s in slots.values())
+
+    def _open(self, slots: Dict[int, Slot], req, now: float):
+        """Open a session for req's client, evicting idle sessions (LRU) as needed.
+        Returns the slot, None when it must wait, or 'reject' when it can never fit."""
+        while True:
+            try:
+                h, nb = self.backend.open(req.instance, self.budget - self._used(slots))
+                s = Slot(client=req.client, handle=h, nbytes=nb, last_used=now)
+                slots[req.client] = s
+                self.opened += 1
+                return s
+            except DoesNotFit:
+                idle = [s for s in slots.values() if not s.busy]
+                if idle:
+                    victim = min(idle, key=lambda s: s.last_used)
+                    self.backend.close(victim.handle)
+                    del slots[victim.client]
+                    self.evictions += 1
+                    continue
+                if not slots:
+                    return "reject"       # does not fit even in an empty budget
+                return None               # wait for running sessions to finish
+
+    # -- loop -----------------------------------------------------------------------
+    def run(self, requests, horizon: Optional[float] = None) -> Stats:
+        reqs = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        recs = {r.rid: Record(r.rid, r.client, r.arrival) for r in reqs}
+        slots: Dict[int, Slot] = {}
+        inflight = []            # (req, slot, token)
+        queue = []               # arrived, not started (arrival order)
+        nxt = 0
+        self.evictions = 0
+        self.opened = 0
+        peak = 0
+        t0 = self.clock()
+        last_finish = 0.0
+        while nxt < len(reqs) or queue or inflight:
+            now = self.clock() - t0
+            if horizon is not None and now > horizon and not inflight:
+                break
+            while nxt < len(reqs) and reqs[nxt].arrival <= now:
+                queue.append(reqs[nxt])
+                nxt += 1
+            progressed = False
+            # completions
+            still = []
+            for req, s, tok in inflight:
+                if self.backend.done(tok):
+                    r = recs[req.rid]
+                    r.finish = self.clock() - t0
+                    r.status = "done"
+                    if self.keep_results:
+                        r.result = self.backend.result(tok)
+                    last_finish = max(last_finish, r.finish)
+                    s.busy = False
+                    s.last_used = r.finish
+                    progressed = True
+                else:
+                    still.append((req, s, tok))
+            inflight = still
+            # admissions, in arrival order; a client's requests stay in order
+            blocked = set()
+            rest = []
+            for req in queue:
+                if req.client in blocked or len(inflight) >= self.max_inflight:
+                    rest.append(req)
+                    blocked.add(req.client)
+                    continue
+                s = slots.get(req.client)
+                if s is not None and s.busy:
+                    rest.append(req)
+                    blocked.add(req.client)
+                    continue
+                if s is None:
+                    s = self._open(slots, req, now)
+                    if s == "reject":
+                        recs[req.rid].status = "rejected"
+                        progressed = True
+                        continue
+                    if s is None:
+                        rest.append(req)
+                        blocked.add(req.client)
+                        continue
+                peak = max(peak, self._used(slots))
+                s.busy = True
+                r = recs[req.rid]
+                r.start = self.clock() - t0
+                r.status = "running"
+                inflight.append((req, s, self.backend.launch(s.handle, req)))
+                progressed = True
+            queue = rest
+            if not progressed:
+                if nxt < len(reqs) and not inflight and not queue:
+                    wait = reqs[nxt].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        self.sleep(min(wait, 0.05))
+                        continue
+                self.sleep(self.idle_sleep)
+        for s in list(slots.values()):
+            self.backend.close(s.handle)
+        return Stats(records=[recs[r.rid] for r in reqs], makespan=last_finish,
+                     evictions=self.evictions, opened=self.opened, peak_bytes=peak)
+
+
+class GpuBackend:
+    """Sessions of the MSFV library on one GPU, one CUDA stream each.  A client's model
+    at Gauss-Newton iteration k is m_0 + 0.01 k dm (m_0 a seeded lognormal field's log,
+    dm seeded noise); its observed data are seeded noise.  Each request copies nothing
+    from the host: the inputs are generated on the device, the step runs as a captured
+    CUDA graph of msfv_forward + msfv_adjoint, and d_pred / grad are copied back to
+    pinned host buffers."""
+
+    def __init__(self, device=None, factor_mode: int = 0, use_graph: bool = True,
+                 copy_back: bool = True):
+        import torch
+        self.torch = torch
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.factor_mode = factor_mode
+        self.use_graph = use_graph
+        self.copy_back = copy_back
+
+    def open(self, spec, budget_bytes: int):
+        from . import workloads as W
+        from .msfv import MSFV_OK, Batch, MSFVError, Session  # noqa: F401
+        torch = self.torch
+        if budget_bytes <= 0:
+            raise DoesNotFit()
+        stream = torch.cuda.Stream(device=self.device)
+        prob = spec.problem()
+        try:
+            sess = Session(prob, stream=stream, factor_mode=self.factor_mode,
+                           hbm_budget_bytes=int(budget_bytes))
+        except MSFVError as e:
+            if e.code == 2:
+                raise DoesNotFit() from e
+            raise
+        with torch.cuda.stream(stream):
+            m0 = W.gaussian_random_field_device(prob.n, spec.corr_len, spec.seed, self.device)
+            g = torch.Generator(device=self.device)
+            g.manual_seed(spec.seed + 1)
+            dm = torch.randn(prob.N, generator=g, device=self.device, dtype=torch.float64)
+            d_obs = 1e-3 * torch.randn((prob.n_src, prob.n_rec), generator=g,
+                                       device=self.device, dtype=torch.float64)
+            m = m0.clone()
+        h = {"sess": sess, "stream": stream, "prob": prob, "m0": m0, "dm": dm, "m": m,
+             "d_obs": d_obs, "batch": None}
+        if self.use_graph:
+            stream.synchronize()
+            h["batch"] = Batch([sess], [m], [d_obs], stream=stream)
+        else:
+            h["d_pred"] = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64,
+                                      device=self.device)
+            h["grad"] = torch.empty(prob.N, dtype=torch.float64, device=self.device)
+        nbytes = int(sess.info()["workspace_bytes"]) + 8 * (3 * prob.N + 2 * prob.n_src * prob.n_rec)
+        return h, nbytes
+
+    def launch(self, h, req):
+        torch = self.torch
+        st = h["stream"]
+        with torch.cuda.stream(st):
+            torch.add(h["m0"], h["dm"], alpha=0.01 * req.iteration, out=h["m"])
+            if h["batch"] is not None:
+                h["batch"].run()
+                d_pred, grad = h["batch"].d_pred[0], h["batch"].grad[0]
+            else:
+                h["sess"].forward(h["m"], h["d_pred"])
+                h["sess"].adjoint(h["d_obs"], h["grad"], want_phi=False)
+                d_pred, grad = h["d_pred"], h["grad"]
+            out = None
+            if self.copy_back:
+                out = (torch.empty(d_pred.shape, dtype=torch.float64, pin_memory=True),
+                       torch.empty(grad.shape, dtype=torch.float64, pin_memory=True))
+                out[0].copy_(d_pred, non_blocking=True)
+                out[1].copy_(grad, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return (ev, out, h)
+
+    def done(self, tok) -> bool:
+        return tok[0].query()
+
+    def result(self, tok):
+        if tok[1] is None:
+            return None
+        return tok[1][0].numpy().copy(), tok[1][1].numpy().copy()
+
+    def close(self, h):
+        h["stream"].synchronize()
+        if h["batch"] is not None:
+            h["batch"].check()
+            h["batch"].close()
+        h["sess"].close()

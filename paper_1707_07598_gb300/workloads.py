@@ -176,3 +176,110 @@ def config_3d_128(seed: int = 2, n: int = 128):
 def noise_like(shape, scale: float, seed: int) -> np.ndarray:
     """Seeded Gaussian noise (used for 1% data noise and random directions)."""
     return scale * _rng(seed).standard_normal(shape)
+
+
+def gaussian_random_field_device(n: Sequence[int], corr_len: float, seed: int, device):
+    """The same recipe as ``gaussian_random_field`` (2x padded periodic spectral synthesis,
+    squared-exponential spectrum, crop, standardise) drawn with torch on a device, for
+    meshes whose host-side FFT would dominate a benchmark's set-up (up to 256^3).  Its
+    random numbers differ from the host generator's; it feeds only GPU runs."""
+    import torch
+    n = tuple(int(v) for v in n)
+    shape = tuple(2 * v for v in n[::-1])
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    spec = torch.fft.fftn(torch.randn(shape, generator=g, device=device, dtype=torch.float64))
+    k2 = torch.zeros(shape, dtype=torch.float64, device=device)
+    for ax_np, npad in enumerate(shape):
+        a = len(shape) - 1 - ax_np
+        kk = 2.0 * np.pi * torch.fft.fftfreq(npad, d=1.0 / n[a], dtype=torch.float64,
+                                            device=device)
+        sh = [1] * len(shape)
+        sh[ax_np] = npad
+        k2 = k2 + kk.reshape(sh) ** 2
+    field_ = torch.fft.ifftn(spec * torch.exp(-0.25 * k2 * corr_len ** 2)).real
+    crop = field_[tuple(slice(0, v) for v in n[::-1])]
+    crop = crop - crop.mean()
+    sd = crop.std(unbiased=False)
+    if float(sd) > 0:
+        crop = crop / sd
+    return crop.contiguous().reshape(-1)
+
+
+@dataclass
+class InstanceSpec:
+    """One independent instance of a batched or served workload (drawn, not built)."""
+    n: tuple
+    coarsen: int
+    corr_len: float
+    n_src: int
+    n_rec: int
+    seed: int
+
+    def problem(self) -> Problem:
+        return make_problem(self.n, self.coarsen, self.n_src, self.n_rec, self.seed,
+                            top_layer=True,
+                            name=f"3d_{self.n[0]}^3_c{self.coarsen}_s{self.n_src}")
+
+
+def batch_instances(count: int = 64, seed: int = 3,
+                    sizes=(64, 96, 128, 192), coarsenings=(4, 8, 16)) -> list:
+    """Independent 3D instances of uneven dual-cell sizes: fine size drawn uniformly from
+    ``sizes`` (per axis, cubic), coarsening from ``coarsenings``, correlation length from
+    U[0.05, 0.2], 8-32 dipoles, 256 top-layer receivers."""
+    rng = _rng(seed)
+    out = []
+    for k in range(count):
+        n = int(rng.choice(sizes))
+        c = int(rng.choice(coarsenings))
+        out.append(InstanceSpec(n=(n, n, n), coarsen=c, corr_len=float(rng.uniform(0.05, 0.2)),
+                                n_src=int(rng.integers(8, 33)), n_rec=256,
+                                seed=int(seed * 100003 + k)))
+    return out
+
+
+@dataclass
+class RequestSpec:
+    """One served forward + gradient request: arrival time (s), the client session it
+    belongs to (requests of one client are successive Gauss-Newton iterations on one
+    mesh and survey), and the seed of its model perturbation."""
+    rid: int
+    arrival: float
+    client: int
+    iteration: int
+    instance: InstanceSpec
+
+
+def served_requests(rate: float = 50.0, duration: float = 60.0, seed: int = 5,
+                    sizes=(32, 64, 128, 256), coarsenings=(4, 8, 16), max_src: int = 64,
+                    p_new_client: float = 0.2) -> list:
+    """Poisson arrivals at ``rate`` per second over ``duration`` seconds.  A request opens
+    a new client with probability ``p_new_client`` (fine size, coarsening and 1..max_src
+    dipoles drawn uniformly, its own seeded lognormal field), else it is the next
+    Gauss-Newton iteration of a client drawn uniformly from the open ones."""
+    rng = _rng(seed)
+    t, rid = 0.0, 0
+    clients: list = []
+    iters: list = []
+    out = []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        if not clients or rng.random() < p_new_client:
+            n = int(rng.choice(sizes))
+            c = int(rng.choice(coarsenings))
+            ns = int(rng.integers(1, max_src + 1))
+            nr = min(256, n * n // 2)
+            clients.append(InstanceSpec(n=(n, n, n), coarsen=c,
+                                        corr_len=float(rng.uniform(0.05, 0.2)), n_src=ns,
+                                        n_rec=nr, seed=int(seed * 1000003 + len(clients))))
+            iters.append(0)
+            k = len(clients) - 1
+        else:
+            k = int(rng.integers(0, len(clients)))
+        out.append(RequestSpec(rid=rid, arrival=t, client=k, iteration=iters[k],
+                               instance=clients[k]))
+        iters[k] += 1
+        rid += 1
+    return out
