@@ -53,6 +53,15 @@ def parse():
     p.add_argument("--n", type=int, default=128, help="mesh size per axis (default 128)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", default="plain", choices=["plain", "batched", "served", "diff"],
+                   help="plain: the one-instance 128^3 step (default); batched: independent "
+                        "instances in one CUDA graph vs one at a time; served: the Poisson "
+                        "request stream; diff: 256^3, c=16 gradient, J v, J^T w")
+    p.add_argument("--instances", type=int, default=64, help="batched: number of instances")
+    p.add_argument("--rate", type=float, default=50.0, help="served: requests per second")
+    p.add_argument("--duration", type=float, default=10.0,
+                   help="served: seconds of the arrival stream that are replayed")
+    p.add_argument("--fd-dirs", type=int, default=20, help="diff: finite-difference directions")
     return p.parse_args()
 
 
@@ -310,10 +319,234 @@ def run_ours(args):
     return 0
 
 
+
+# ---------------------------------------------------------------------------------
+# Extra workloads (not the default line): batched instances, served requests, and the
+# 256^3 differentiation case.  Each prints its own JSON line.
+# ---------------------------------------------------------------------------------
+def _gpu_setup():
+    import torch
+    from paper_1707_07598_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    return torch, dev
+
+
+def run_batched(args):
+    """Independent 3D instances (sizes 64..192^3, c in {4, 8, 16}, 8-32 dipoles) as one
+    CUDA graph per step, against the same instances run one at a time."""
+    torch, dev = _gpu_setup()
+    from paper_1707_07598_gb300.msfv import Batch, Session
+    specs = W.batch_instances(args.instances)
+    sessions, ms, dobs = [], [], []
+    per_instance_budget = 6 << 30     # larger stored factors switch to recompute
+    for sp in specs:
+        prob = sp.problem()
+        st = torch.cuda.Stream(dev)
+        sessions.append(Session(prob, stream=st, factor_mode=0,
+                                hbm_budget_bytes=per_instance_budget))
+        ms.append(W.gaussian_random_field_device(prob.n, sp.corr_len, sp.seed, dev))
+        dobs.append(torch.zeros((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev))
+    torch.cuda.synchronize()
+    batch = Batch(sessions, ms, dobs)
+    batch.run()
+    batch.check()
+    for k in range(len(specs)):                       # observed data: 97% of the prediction
+        dobs[k].copy_(0.97 * batch.d_pred[k])
+    for _ in range(max(args.warmup - 1, 0)):
+        batch.run()
+    batch.check()
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        batch.run()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    batch.check()
+    bt = [a.elapsed_time(b) for a, b in ev]
+    clk = clocks.stop()
+    # the plain one-instance path: the same instances one after another, no graph
+    plain_ms = []
+    d_plain, g_plain = [], []
+    for rep in range(max(1, min(args.steps, 2))):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k, s in enumerate(sessions):
+            s.set_stream(stream)
+            d = s.forward(ms[k])
+            _, g = s.adjoint(dobs[k], want_phi=False)
+            if rep == 0:
+                d_plain.append(d)
+                g_plain.append(g)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(t0.elapsed_time(t1))
+    same = all(torch.equal(d_plain[k], batch.d_pred[k]) and torch.equal(g_plain[k], batch.grad[k])
+               for k in range(len(specs)))
+    K = len(specs)
+    ms_step = float(np.mean(bt))
+    value = K / (ms_step / 1000.0)
+    plain_val = K / (float(np.mean(plain_ms)) / 1000.0)
+    recompute = sum(int(s.info()["recompute"]) for s in sessions)
+    mix = {}
+    for sp in specs:
+        key = f"{sp.n[0]}^3_c{sp.coarsen}"
+        mix[key] = mix.get(key, 0) + 1
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+           "p50_ms": float(np.percentile(bt, 50)), "p99_ms": float(np.percentile(bt, 99)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"batched_{K}_instances_3d", "instances": K, "mix": mix,
+                      "graph": "one CUDA graph per step, one branch per instance",
+                      "recompute_instances": recompute,
+                      "l2": "working set of every step far larger than L2"},
+           "plain": {"value": plain_val, "unit": "solves/s",
+                     "ms_per_step": float(np.mean(plain_ms)),
+                     "path": "same sessions, forward + adjoint one instance at a time"},
+           "speedup_vs_plain": value / plain_val,
+           "parity": "batched == plain bit for bit on every instance" if same else "MISMATCH",
+           "clocks": clk}
+    print(json.dumps(out))
+    batch.close()
+    for s in sessions:
+        s.close()
+    return 0 if same else 1
+
+
+def run_served(args):
+    """The Poisson request stream (rate x duration), fine sizes 32..256^3, c in {4, 8, 16},
+    1-64 dipoles, 150 GB budget: continuous batching against one request at a time."""
+    torch, dev = _gpu_setup()
+    from paper_1707_07598_gb300.serve import GpuBackend, Server
+    reqs = W.served_requests(rate=args.rate, duration=args.duration)
+    budget = 150 * 10 ** 9
+    # warm the kernels and the allocator pool on a small request
+    warm = W.served_requests(rate=100.0, duration=0.05, seed=99, sizes=(32,))
+    Server(GpuBackend(dev), budget, max_inflight=4).run(warm)
+    res = {}
+    clk = None
+    for mode, inflight in (("served", 8), ("plain", 1)):
+        clocks = ClockSampler(0)
+        clocks.start()
+        st = Server(GpuBackend(dev, use_graph=(inflight > 1)), budget,
+                    max_inflight=inflight).run(reqs)
+        c = clocks.stop()
+        if mode == "served":
+            clk = c
+        done = st.done()
+        res[mode] = {"value": st.throughput, "unit": "solves/s", "completed": len(done),
+                     "rejected": sum(r.status == "rejected" for r in st.records),
+                     "p50_ms": 1000.0 * st.percentile(50), "p99_ms": 1000.0 * st.percentile(99),
+                     "makespan_s": st.makespan, "sessions_opened": st.opened,
+                     "evictions": st.evictions, "peak_session_bytes": st.peak_bytes}
+    sv = res["served"]
+    out = {"metric": METRIC, "value": sv["value"], "unit": "solves/s", "n_gpus": 1,
+           "steps": len(reqs), "warmup": len(warm), "ms_per_step": 1000.0 / max(sv["value"], 1e-12),
+           "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"served_poisson_{args.rate:g}_per_s_{args.duration:g}_s",
+                      "requests": len(reqs), "sizes": [32, 64, 128, 256],
+                      "coarsenings": [4, 8, 16], "sources": "1-64", "hbm_budget_bytes": budget,
+                      "max_inflight": 8},
+           "served": sv, "plain": res["plain"],
+           "speedup_vs_plain": sv["value"] / max(res["plain"]["value"], 1e-12), "clocks": clk}
+    print(json.dumps(out))
+    return 0
+
+
+def run_diff(args):
+    """256^3, c = 16, 64 dipoles, 4096 receivers: gradient, J v and J^T w through the
+    torch.autograd bindings, with stored and with recomputed local factors; central
+    differences (step 1e-6) along --fd-dirs random directions."""
+    torch, dev = _gpu_setup()
+    from paper_1707_07598_gb300.autograd import misfit, predict
+    from paper_1707_07598_gb300.msfv import Session
+    import torch.autograd.forward_ad as fwAD
+    n = args.n if args.n != 128 else 256
+    prob = W.make_problem((n, n, n), 16, 64, 4096, seed=4, top_layer=True)
+    m0 = W.gaussian_random_field_device(prob.n, 0.15, 4, dev)
+    stream = torch.cuda.current_stream(dev)
+    out_modes = {}
+    for fm, name in ((1, "store"), (2, "recompute")):
+        s = Session(prob, stream=stream, factor_mode=fm)
+        d_obs = (s.forward(m0) * 1.02).contiguous()
+        v = torch.randn(prob.N, dtype=torch.float64, device=dev,
+                        generator=torch.Generator(device=dev).manual_seed(5))
+        w = torch.randn((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev,
+                        generator=torch.Generator(device=dev).manual_seed(6))
+
+        def step():
+            m = m0.clone().requires_grad_(True)
+            phi = misfit(m, d_obs, s)
+            phi.backward()
+            with fwAD.dual_level():
+                jv = fwAD.unpack_dual(predict(fwAD.make_dual(m0, v), s)).tangent
+            m2 = m0.clone().requires_grad_(True)
+            predict(m2, s).backward(w)
+            return m.grad, jv, m2.grad
+        for _ in range(max(args.warmup, 1)):
+            g, jv, jtw = step()
+        ts = []
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g, jv, jtw = step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        # adjoint identity and central differences of the misfit
+        dot = abs(float((w * jv).sum()) - float(jtw @ v)) / float(w.norm() * jv.norm())
+        fd_err = 0.0
+        gen = torch.Generator(device=dev).manual_seed(7)
+        for k in range(args.fd_dirs):
+            dirn = torch.randn(prob.N, dtype=torch.float64, device=dev, generator=gen)
+            with torch.no_grad():
+                fp = misfit(m0 + 1e-6 * dirn, d_obs, s).item()
+                fm_ = misfit(m0 - 1e-6 * dirn, d_obs, s).item()
+            an = float(g @ dirn)
+            fd_err = max(fd_err, abs((fp - fm_) / 2e-6 - an) /
+                         max(abs(an), 1e-3 * float(g.norm() * dirn.norm())))
+        info = s.info()
+        out_modes[name] = {"ms_per_step": float(np.mean(ts)), "p50_ms": float(np.percentile(ts, 50)),
+                           "p99_ms": float(np.percentile(ts, 99)),
+                           "factor_bytes": info["factor_bytes"],
+                           "workspace_bytes": info["workspace_bytes"],
+                           "fd_max_rel_err": fd_err, "fd_dirs": args.fd_dirs,
+                           "adjoint_identity_rel_err": dot}
+        s.close()
+        torch.cuda.synchronize()
+    st = out_modes["store"]
+    out = {"metric": METRIC, "value": 1000.0 / st["ms_per_step"], "unit": "grad+Jv+JTw per s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": st["ms_per_step"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"diff_{n}^3_c16_64dipoles_4096rec", "n": [n] * 3,
+                      "coarsen": 16, "n_src": 64, "n_rec": 4096,
+                      "step": "misfit gradient + J v (forward-mode) + J^T w (reverse-mode)"},
+           "modes": out_modes}
+    print(json.dumps(out))
+    return 0
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
+    if args.workload == "diff":
+        return run_diff(args)
     return run_ours(args)
 
 
