@@ -41,6 +41,19 @@ constexpr int NTH = 512;      // threads per CTA (one CTA per SM)
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
+// 1D interpolation weight of coarse node K at fine node i as a code: -1 for 0, 0 for 1,
+// 1 for 1/2 (the product over axes is 2^-(sum of codes), exact, with no FP64 multiply).
+__device__ __forceinline__ int pw1_code(int i, int K, int gc, int coarsened) {
+  if (!coarsened) return i == K ? 0 : -1;
+  if ((i & 1) == 0) return (K == (i >> 1)) ? 0 : -1;
+  const int lo = (i - 1) >> 1, hi = (i + 1) >> 1;
+  if (hi < gc) return (K == lo || K == hi) ? 1 : -1;
+  return K == lo ? 0 : -1;
+}
+__device__ __forceinline__ double halvings(int k) {
+  return k == 0 ? 1.0 : (k == 1 ? 0.5 : (k == 2 ? 0.25 : 0.125));
+}
+
 // 1D interpolation weight of coarse node K at fine node i.
 __device__ __forceinline__ double pw1(int i, int K, int gc, int coarsened) {
   if (!coarsened) return i == K ? 1.0 : 0.0;
@@ -208,8 +221,9 @@ __global__ void k_mg_coarsest(MGLevelDev L, int d, double* inv, double* invT, in
 namespace {
 
 constexpr int MAXM = 24;          // GMRES restart length bound
-constexpr int STAGE_CAP = 6144;   // doubles of shared memory for a staged level-0 range
-constexpr int CSM_CAP = 21500;    // doubles of shared memory for levels >= 1 (one CTA)
+constexpr int STAGE_CAP = 9600;   // doubles of shared memory for a staged range of a distributed level
+constexpr int CSM_CAP = 18500;    // doubles of shared memory for the local levels (one CTA)
+constexpr long long kLocalLevelMax = 640;  // largest level run inside one CTA
 
 struct Ctx {
   int rank;          // CTA rank in its cluster
@@ -258,8 +272,12 @@ struct Vec {
   const double* sm;
   const double* g;
   long long lo;
+  const double* scale = nullptr;  // unstaged scaled view: om * scale[j] * g[j]
+  double om = 0.0;
   __device__ __forceinline__ double operator[](long long j) const {
-    return sm ? sm[j - lo] : ldcg(g + j);
+    if (sm) return sm[j - lo];
+    const double v = ldcg(g + j);
+    return scale ? om * scale[j] * v : v;
   }
 };
 
@@ -268,7 +286,7 @@ __device__ __forceinline__ Vec stage_range(Ctx& c, const double* src, long long 
                                            double om = 0.0) {
   lo = max(0LL, lo);
   hi = min(n, hi);
-  Vec v{nullptr, src, lo};
+  Vec v{nullptr, src, lo, scale, om};
   __syncthreads();
   if (hi - lo <= STAGE_CAP && hi > lo) {
     for (long long j = lo + c.tid; j < hi; j += NTH) {
@@ -292,17 +310,27 @@ __device__ __forceinline__ double apply_row(const MGLevelDev& L, int tr, long lo
   int ic[3];
   dec(i, L.g, ic);
   const long long sy = L.g[0], sz = (long long)L.g[0] * L.g[1];
-  double acc[3] = {0.0, 0.0, 0.0};
+  // issue every stencil load before the first FMA (all in flight together), then
+  // accumulate in three chains
+  unsigned inmask = 0;
+  double av[S3];
 #pragma unroll
   for (int s = 0; s < S3; ++s) {
     const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = (D == 3) ? s / 9 - 1 : 0;
     const bool in = (unsigned)(ic[0] + ox) < (unsigned)L.g[0] &&
                     (unsigned)(ic[1] + oy) < (unsigned)L.g[1] &&
                     (D == 2 || (unsigned)(ic[2] + oz) < (unsigned)L.g[2]);
-    if (in) {
+    const long long j = i + ox + oy * sy + oz * sz;
+    av[s] = in ? (tr ? L.A[(long long)(S3 - 1 - s) * L.n + j] : L.A[(long long)s * L.n + i]) : 0.0;
+    inmask |= in ? (1u << s) : 0u;
+  }
+  double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int s = 0; s < S3; ++s) {
+    if (inmask & (1u << s)) {
+      const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = (D == 3) ? s / 9 - 1 : 0;
       const long long j = i + ox + oy * sy + oz * sz;
-      const double a = tr ? L.A[(long long)(S3 - 1 - s) * L.n + j] : L.A[(long long)s * L.n + i];
-      acc[s % 3] = fma(a, x[j], acc[s % 3]);
+      acc[s % 3] = fma(av[s], x[j], acc[s % 3]);
     }
   }
   return (acc[0] + acc[1]) + acc[2];
@@ -331,10 +359,13 @@ __device__ __forceinline__ double restrict_row(const MGLevelDev& L, const MGLeve
       if ((unsigned)ic[a] >= (unsigned)L.g[a]) in = false;
     }
     if (in) {
-      double wt = 1.0;
+      int k = 0;
 #pragma unroll
-      for (int a = 0; a < D; ++a) wt *= pw1(ic[a], Kc[a], C.g[a], L.coarsened[a]);
-      acc = fma(wt, s[ic[0] + ic[1] * sy + ic[2] * sz], acc);
+      for (int a = 0; a < D; ++a) {
+        const int w = pw1_code(ic[a], Kc[a], C.g[a], L.coarsened[a]);
+        k = (w < 0 || k < 0) ? -1 : k + w;
+      }
+      if (k >= 0) acc = fma(halvings(k), s[ic[0] + ic[1] * sy + ic[2] * sz], acc);
     }
   }
   return acc;
@@ -367,10 +398,15 @@ __device__ __forceinline__ double prolong_row(const MGLevelDev& L, const MGLevel
       if (K[a] >= C.g[a]) in = false;
     }
     if (in) {
-      double wt = 1.0;
+      int k = 0;
 #pragma unroll
-      for (int a = 0; a < D; ++a) wt *= pw1(ic[a], K[a], C.g[a], L.coarsened[a]);
-      acc = fma(wt, xc[K[0] + (long long)C.g[0] * (K[1] + (long long)C.g[1] * K[2])], acc);
+      for (int a = 0; a < D; ++a) {
+        const int w = pw1_code(ic[a], K[a], C.g[a], L.coarsened[a]);
+        k = (w < 0 || k < 0) ? -1 : k + w;
+      }
+      if (k >= 0)
+        acc = fma(halvings(k), xc[K[0] + (long long)C.g[0] * (K[1] + (long long)C.g[1] * K[2])],
+                  acc);
     }
   }
   return acc;
@@ -491,8 +527,8 @@ __device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV
                               const long long* off, double* mem) {
   const int tr = P.transpose;
   const double om = P.omega;
-  // per level l >= 1: r, x, s at offsets off[l] (3 n_l doubles each)
-  for (int l = 1; l < P.nlev - 1; ++l) {
+  // per local level l >= P.ld: r, x, s at offsets off[l] (3 n_l doubles each)
+  for (int l = P.ld; l < P.nlev - 1; ++l) {
     const MGLevelDev& L = LV[l];
     double* r = mem + off[l];
     double* x = r + L.n;
@@ -522,7 +558,7 @@ __device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV
     }
     __syncthreads();
   }
-  for (int l = P.nlev - 2; l >= 1; --l) {
+  for (int l = P.nlev - 2; l >= P.ld; --l) {
     const MGLevelDev& L = LV[l];
     const MGLevelDev& C = LV[l + 1];
     double* r = mem + off[l];
@@ -540,19 +576,96 @@ __device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV
   }
 }
 
-// Full V(2,2) cycle, x_0 ~= M^{-1} r_0.  Level 0 is spread over the group; levels >= 1
-// run inside CTA 0 of the group (shared memory) when they fit, else on the group.
+// Range of level C nodes whose prolongation reaches the fine rows [b, e) of level L.
+__device__ __forceinline__ void coarse_range(const MGLevelDev& L, const MGLevelDev& C, long long b,
+                                             long long e, long long& clo, long long& chi) {
+  clo = 0;
+  chi = 0;
+  if (e <= b) return;
+  int i0[3], i1[3], c0[3], c1[3];
+  dec(b, L.g, i0);
+  dec(e - 1, L.g, i1);
+  for (int a = 0; a < 3; ++a) {
+    const int lo_f = (a == 2) ? i0[2] : 0, hi_f = (a == 2) ? i1[2] : L.g[a] - 1;
+    c0[a] = L.coarsened[a] ? (lo_f >> 1) : lo_f;
+    c1[a] = L.coarsened[a] ? min(C.g[a] - 1, (hi_f + 1) >> 1) : hi_f;
+  }
+  clo = enc(c0, C.g);
+  chi = enc(c1, C.g) + 1;
+}
+
+// Pre-smoothing of a level spread over the cluster: two damped Jacobi sweeps from zero
+// (the first one, x = om D^-1 r, is folded into the second) and the residual s = r - A x.
 template <int D>
-__device__ __forceinline__ void vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV,
-                                       const long long* LOFF, const double* r0, double* x0, double* s0, double* x1g) {
-  const int tr = P.transpose;
-  const double om = P.omega;
-  const MGLevelDev& L = P.lev[0];
+__device__ __forceinline__ void smooth_down(Ctx& c, const MGLevelDev& L, int tr, double om,
+                                            const double* r, double* x, double* s) {
   long long b, e;
   chunk(L.n, c.rank, c.G, b, e);
   const long long H = halo(L);
+  c.tag = 2;
+  {
+    const Vec y = stage_range(c, r, b - H, e + H, L.n, L.dinv, om);
+    for (long long i = b + c.tid; i < e; i += NTH) {
+      const double ri = ldcg(r + i);
+      x[i] = fma(om * L.dinv[i], ri - apply_row<D>(L, tr, i, y), y[i]);
+    }
+  }
+  gsync(c);
+  c.tag = 3;
+  {
+    const Vec xv = stage_range(c, x, b - H, e + H, L.n);
+    for (long long i = b + c.tid; i < e; i += NTH) s[i] = ldcg(r + i) - apply_row<D>(L, tr, i, xv);
+  }
+  gsync(c);
+}
+
+// Coarse-grid correction x += P x_C and two post-smoothing sweeps, spread over the cluster.
+template <int D>
+__device__ __forceinline__ void smooth_up(Ctx& c, const MGLevelDev& L, const MGLevelDev& C, int tr,
+                                          double om, const double* r, double* x, double* s,
+                                          const double* xc) {
+  long long b, e;
+  chunk(L.n, c.rank, c.G, b, e);
+  const long long H = halo(L);
+  c.tag = 5;
+  {
+    long long clo, chi;
+    coarse_range(L, C, b, e, clo, chi);
+    const Vec cv = stage_range(c, xc, clo, chi, C.n);
+    for (long long i = b + c.tid; i < e; i += NTH) x[i] = ldcg(x + i) + prolong_row<D>(L, C, i, cv);
+  }
+  gsync(c);
+  c.tag = 6;
+  {
+    const Vec xv = stage_range(c, x, b - H, e + H, L.n);
+    for (long long i = b + c.tid; i < e; i += NTH)
+      s[i] = fma(om * L.dinv[i], ldcg(r + i) - apply_row<D>(L, tr, i, xv), xv[i]);
+  }
+  gsync(c);
+  c.tag = 7;
+  {
+    const Vec sv = stage_range(c, s, b - H, e + H, L.n);
+    for (long long i = b + c.tid; i < e; i += NTH)
+      x[i] = fma(om * L.dinv[i], ldcg(r + i) - apply_row<D>(L, tr, i, sv), sv[i]);
+  }
+  gsync(c);
+}
+
+// Full V(2,2) cycle, x_0 ~= M^{-1} r_0.  Levels 0 .. P.ld-1 are spread over the cluster
+// (their vectors in global memory: level 0 uses r0 / x0 / s0, level l >= 1 uses
+// r, x, s at dist + DOFF[l]); levels >= P.ld run inside CTA 0 from shared memory, and
+// their correction x_{ld} is handed back through dist + DOFF[P.ld].
+template <int D>
+__device__ __forceinline__ void vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV,
+                                       const long long* LOFF, const long long* DOFF, double* dist,
+                                       const double* r0, double* x0, double* s0) {
+  const int tr = P.transpose;
+  const double om = P.omega;
   if (P.nlev == 1) {
     // coarsest only: dense pinned solve by every CTA of its own rows
+    const MGLevelDev& L = LV[0];
+    long long b, e;
+    chunk(L.n, c.rank, c.G, b, e);
     const double* inv = tr ? P.invT : P.inv;
     for (long long i = b + c.tid; i < e; i += NTH) {
       double acc = 0.0;
@@ -563,67 +676,46 @@ __device__ __forceinline__ void vcycle(Ctx& c, const MGParamsDev& P, const MGLev
     gsync(c);
     return;
   }
-  const MGLevelDev& C = P.lev[1];
-  c.tag = 2;
-  {
-    const Vec y = stage_range(c, r0, b - H, e + H, L.n, L.dinv, om);
-    for (long long i = b + c.tid; i < e; i += NTH) {
-      const double ri = ldcg(r0 + i);
-      x0[i] = fma(om * L.dinv[i], ri - apply_row<D>(L, tr, i, y), y[i]);
+  const int ld = P.ld;
+  // down the distributed levels
+  for (int l = 0; l < ld; ++l) {
+    const MGLevelDev& L = LV[l];
+    const MGLevelDev& C = LV[l + 1];
+    const double* r = (l == 0) ? r0 : dist + DOFF[l];
+    double* x = (l == 0) ? x0 : dist + DOFF[l] + L.n;
+    double* s = (l == 0) ? s0 : dist + DOFF[l] + 2 * L.n;
+    smooth_down<D>(c, L, tr, om, r, x, s);
+    c.tag = 4;
+    if (l + 1 < ld) {
+      // restriction into the next distributed level
+      double* rc = dist + DOFF[l + 1];
+      long long bc, ec;
+      chunk(C.n, c.rank, c.G, bc, ec);
+      for (long long K = bc + c.tid; K < ec; K += NTH)
+        rc[K] = restrict_row<D>(L, C, K, Vec{nullptr, s, 0});
+    } else if (c.rank == 0) {
+      // CTA 0 gathers the first local level's right-hand side into its coarse memory
+      // and runs the local levels there
+      double* rl = c.cs + LOFF[ld];
+      for (long long K = c.tid; K < C.n; K += NTH) rl[K] = restrict_row<D>(L, C, K, Vec{nullptr, s, 0});
+      __syncthreads();
+      coarse_vcycle<D>(c, P, LV, LOFF, c.cs);
+      const double* xl = c.cs + LOFF[ld] + C.n;
+      double* xg = dist + DOFF[ld];
+      for (long long K = c.tid; K < C.n; K += NTH) xg[K] = xl[K];
     }
+    gsync(c);
   }
-  gsync(c);
-  c.tag = 3;
-  {
-    const Vec xv = stage_range(c, x0, b - H, e + H, L.n);
-    for (long long i = b + c.tid; i < e; i += NTH) s0[i] = ldcg(r0 + i) - apply_row<D>(L, tr, i, xv);
+  // up the distributed levels
+  for (int l = ld - 1; l >= 0; --l) {
+    const MGLevelDev& L = LV[l];
+    const MGLevelDev& C = LV[l + 1];
+    const double* r = (l == 0) ? r0 : dist + DOFF[l];
+    double* x = (l == 0) ? x0 : dist + DOFF[l] + L.n;
+    double* s = (l == 0) ? s0 : dist + DOFF[l] + 2 * L.n;
+    const double* xc = (l + 1 == ld) ? dist + DOFF[ld] : dist + DOFF[l + 1] + C.n;
+    smooth_up<D>(c, L, C, tr, om, r, x, s, xc);
   }
-  gsync(c);
-  // restriction: CTA 0 gathers the whole level-1 right-hand side into shared memory
-  // and runs the coarse levels there
-  c.tag = 4;
-  if (c.rank == 0) {
-    double* r1 = c.cs;
-    for (long long K = c.tid; K < C.n; K += NTH) r1[K] = restrict_row<D>(L, C, K, Vec{nullptr, s0, 0});
-    __syncthreads();
-    coarse_vcycle<D>(c, P, LV, LOFF, c.cs);
-    const double* x1 = c.cs + C.n;
-    for (long long K = c.tid; K < C.n; K += NTH) x1g[K] = x1[K];
-  }
-  gsync(c);
-  c.tag = 5;
-  {
-    long long clo = 0, chi = 0;
-    if (e > b) {
-      int i0[3], i1[3], c0[3], c1[3];
-      dec(b, L.g, i0);
-      dec(e - 1, L.g, i1);
-      for (int a = 0; a < 3; ++a) {
-        const int lo_f = (a == 2) ? i0[2] : 0, hi_f = (a == 2) ? i1[2] : L.g[a] - 1;
-        c0[a] = L.coarsened[a] ? (lo_f >> 1) : lo_f;
-        c1[a] = L.coarsened[a] ? min(C.g[a] - 1, (hi_f + 1) >> 1) : hi_f;
-      }
-      clo = enc(c0, C.g);
-      chi = enc(c1, C.g) + 1;
-    }
-    const Vec cv = stage_range(c, x1g, clo, chi, C.n);
-    for (long long i = b + c.tid; i < e; i += NTH) x0[i] = ldcg(x0 + i) + prolong_row<D>(L, C, i, cv);
-  }
-  gsync(c);
-  c.tag = 6;
-  {
-    const Vec xv = stage_range(c, x0, b - H, e + H, L.n);
-    for (long long i = b + c.tid; i < e; i += NTH)
-      s0[i] = fma(om * L.dinv[i], ldcg(r0 + i) - apply_row<D>(L, tr, i, xv), xv[i]);
-  }
-  gsync(c);
-  c.tag = 7;
-  {
-    const Vec sv = stage_range(c, s0, b - H, e + H, L.n);
-    for (long long i = b + c.tid; i < e; i += NTH)
-      x0[i] = fma(om * L.dinv[i], ldcg(r0 + i) - apply_row<D>(L, tr, i, sv), sv[i]);
-  }
-  gsync(c);
 }
 
 }  // namespace
@@ -658,30 +750,34 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
   // vectors first, then (when they fit) the stencils and diagonals copied into shared
   // memory.
   __shared__ MGLevelDev LV[kMaxLevels];
-  __shared__ long long LOFF[kMaxLevels];  // offsets of the level-l vectors in the coarse memory
+  __shared__ long long LOFF[kMaxLevels];  // local levels: offsets of their vectors in the coarse memory
+  __shared__ long long DOFF[kMaxLevels];  // distributed levels >= 1: offsets in the per-RHS block
   // coarse-level vectors of this group: shared memory, or global memory when they do not
   // fit there (then the stencils stay in global memory too)
   if (P.cws) c.cs = P.cws + (long long)grp * P.cws_stride;
   {
     const int S3 = (D == 3) ? 27 : 9;
-    long long vec = 0, mat = 0;
+    long long vec = 0, mat = 0, dsum = 0;
 #pragma unroll
     for (int l = 0; l < kMaxLevels; ++l) {
       if (l < P.nlev) {
         if (c.tid == 0) {
           LV[l] = P.lev[l];
           LOFF[l] = vec;
+          DOFF[l] = dsum;
         }
-        if (l >= 1) {
+        if (l >= P.ld) {
           vec += 3 * P.lev[l].n;
           mat += P.lev[l].n * (S3 + 1);
+        } else if (l >= 1) {
+          dsum += 3 * P.lev[l].n;
         }
       }
     }
     __syncthreads();
     if (c.rank == 0 && !P.cws && vec + mat <= CSM_CAP) {
       double* q = c.cs + vec;
-      for (int l = 1; l < P.nlev; ++l) {
+      for (int l = P.ld; l < P.nlev; ++l) {
         const long long na = LV[l].n * S3, nd = LV[l].n;
         for (long long t = c.tid; t < na; t += NTH) q[t] = LV[l].A[t];
         for (long long t = c.tid; t < nd; t += NTH) q[na + t] = LV[l].dinv[t];
@@ -690,7 +786,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
       __syncthreads();  // every thread has read the global level pointers
       if (c.tid == 0) {
         q = c.cs + vec;
-        for (int l = 1; l < P.nlev; ++l) {
+        for (int l = P.ld; l < P.nlev; ++l) {
           const long long na = LV[l].n * S3, nd = LV[l].n;
           LV[l].A = q;
           LV[l].dinv = q + na;
@@ -706,7 +802,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
     double* Z = V + (long long)(P.m + 1) * n0; // m x n0
     double* bh = Z + (long long)P.m * n0;      // n0
     double* s0 = bh + n0;                      // n0
-    double* x1g = s0 + n0;                     // level-1 correction (n_1)
+    double* dist = s0 + n0;                    // distributed levels >= 1, then x_ld
     double* x = P.rhs + (long long)j * n0;     // solution, in place of b
     {
       double hp[2] = {0.0, 0.0};
@@ -759,7 +855,7 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
           double* vk = V + (long long)k * n0;
           double* zk = Z + (long long)k * n0;
           double* w = V + (long long)(k + 1) * n0;
-          vcycle<D>(c, P, LV, LOFF, vk, zk, s0, x1g);
+          vcycle<D>(c, P, LV, LOFF, DOFF, dist, vk, zk, s0);
           ++iters;
           c.tag = 90;
           {
@@ -852,12 +948,23 @@ void mg_setup_levels(MGHost& H, const DevGeom& g) {
     }
     for (int a = 0; a < 3; ++a) gd[a] = L.coarsened[a] ? (gd[a] + 1) / 2 : gd[a];
   }
+  // the first level small enough for one CTA, and every level below it, run locally
+  H.ld = 1;
+  while (H.ld < H.nlev - 1 && H.lev[H.ld].n > kLocalLevelMax) ++H.ld;
 }
 
 long long mg_coarse_doubles(const MGHost& H) {
   long long need = 0;
-  for (int l = 1; l < H.nlev; ++l) need += 3 * H.lev[l].n;
+  for (int l = H.ld; l < H.nlev; ++l) need += 3 * H.lev[l].n;
   return need;
+}
+
+long long mg_rhs_doubles(const MGHost& H) {
+  const long long n0 = H.lev[0].n;
+  long long v = (long long)(2 * H.m + 3) * n0;
+  for (int l = 1; l < H.ld && l < H.nlev; ++l) v += 3 * H.lev[l].n;
+  if (H.nlev > 1) v += H.lev[H.ld].n;
+  return v;
 }
 
 bool mg_coarse_fits(const MGHost& H) { return mg_coarse_doubles(H) <= CSM_CAP; }
@@ -915,6 +1022,7 @@ cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose,
   MGParamsDev P;
   P.d = H.d;
   P.nlev = H.nlev;
+  P.ld = H.ld;
   for (int l = 0; l < H.nlev; ++l) P.lev[l] = H.lev[l];
   P.inv = H.inv;
   P.invT = H.invT;

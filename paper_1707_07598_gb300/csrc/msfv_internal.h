@@ -166,6 +166,7 @@ struct MGLevelDev {
 };
 struct MGHost {
   int d = 0, nlev = 0;
+  int ld = 1;                 // levels 0 .. ld-1 spread over the cluster, ld .. on CTA 0
   MGLevelDev lev[kMaxLevels];
   double* inv = nullptr;      // 8 x 8 pinned coarsest inverse
   double* invT = nullptr;     // same for the transposed operator
@@ -182,7 +183,7 @@ struct MGHost {
   long long cws_stride = 0;   //   group, when they do not fit in shared memory
 };
 struct MGParamsDev {
-  int d, nlev;
+  int d, nlev, ld;
   MGLevelDev lev[kMaxLevels];
   const double* inv;
   const double* invT;
@@ -203,8 +204,10 @@ struct MGParamsDev {
 void mg_setup_levels(MGHost& H, const DevGeom& g);
 // true when the vectors of levels >= 1 fit in one CTA's shared memory
 bool mg_coarse_fits(const MGHost& H);
-// doubles of the vectors of levels >= 1 (per cluster group)
+// doubles of the vectors of the local levels (per cluster group)
 long long mg_coarse_doubles(const MGHost& H);
+// doubles of one right-hand side's GMRES and distributed-level workspace
+long long mg_rhs_doubles(const MGHost& H);
 int mg_pick_cluster(int d, int Ns, int* max_clusters);
 void launch_mg_setup(const MGHost& H, int* status, cudaStream_t s);
 // rhs: Ns x Nc, solved in place (pinned: entry 0 of each solution is zero);

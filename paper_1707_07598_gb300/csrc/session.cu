@@ -547,8 +547,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     }
     H.inv = dalloc<double>(s, 64, &ce);
     H.invT = dalloc<double>(s, 64, &ce);
-    const long long n1 = H.nlev > 1 ? H.lev[1].n : 0;
-    H.rhs_stride = (long long)(2 * H.m + 3) * Nc + n1;
+    H.rhs_stride = (mg_rhs_doubles(H) + 31) & ~31LL;
     H.ws = dalloc<double>(s, (size_t)s->Ns * H.rhs_stride, &ce);
     H.iters = dalloc<int>(s, 2 * (size_t)s->Ns, &ce);
     const char* tr = getenv("MSFV_TRACE_COARSE");

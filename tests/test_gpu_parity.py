@@ -190,7 +190,8 @@ def test_config_3d_128_full(dev):
 @pytest.mark.parametrize("solver", ["band", "mg"])
 @pytest.mark.parametrize("n,c,ns,nr", [((32, 32), 4, 2, 16), ((20, 15), 5, 2, 8),
                                        ((16, 16, 16), 4, 3, 20), ((24, 16, 16), 8, 4, 30),
-                                       ((12, 10, 6), 2, 2, 9)])
+                                       ((12, 10, 6), 2, 2, 9), ((128, 128), 4, 3, 24),
+                                       ((320, 256), 4, 2, 20), ((48, 48, 48), 4, 3, 30)])
 def test_both_coarse_solvers_match_oracle(dev, monkeypatch, solver, n, c, ns, nr):
     """Banded LU and multigrid GMRES both reproduce the oracle's pinned coarse solve."""
     monkeypatch.setenv("MSFV_COARSE_SOLVER", solver)
