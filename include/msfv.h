@@ -146,6 +146,38 @@ int msfv_solve_host(msfv_session_t* s, const double* m_host, const double* d_obs
 int msfv_misfit_static(const double* d_pred_dev, const double* d_obs_dev, int64_t count,
                        double* r_dev, double* phi_dev, void* stream);
 
+/* ---- Gauss-Newton-CG inversion step (Sec. 5) -----------------------------------------
+ * One Gauss-Newton iteration on the regularised misfit
+ *   Phi(m) = 1/2 ||d(m) - d_obs||^2 + alpha/2 sum_f w_f ((m - m_ref)_y - (m - m_ref)_x)^2,
+ * the second term a diffusion regulariser over the interior faces f between cells x and
+ * y with the finite-volume weight w_f = area_f / distance_f.  The step dm solves
+ *   (J^T J + alpha K) dm = -(J^T r + alpha K (m - m_ref)),   r = d(m) - d_obs,
+ * by conjugate gradients (J v and J^T w through the same kernels as msfv_jvec /
+ * msfv_jtvec, K the Hessian of the regulariser / alpha), then m is replaced by
+ * clip(m + s dm, m_min, m_max) with s = 1, 1/2, ... (Armijo condition, 1e-4).
+ * m_dev is updated in place (unchanged when no step is accepted, reported as step 0).
+ * The session is left linearised at the last model it evaluated; the call synchronises
+ * the stream (it reads scalars on the host).  Dot products are deterministic. */
+typedef struct msfv_gn_opts {
+  double alpha;             /* regularisation weight (>= 0)                          */
+  const double* m_ref_dev;  /* reference model (N doubles, device) or NULL for 0     */
+  int cg_iters;             /* maximum CG iterations (>= 1)                          */
+  double cg_tol;            /* stop when ||residual|| <= cg_tol ||gradient||          */
+  int max_backtracks;       /* line-search halvings (>= 0)                           */
+  double m_min, m_max;      /* bounds on m                                           */
+} msfv_gn_opts_t;
+typedef struct msfv_gn_stats {
+  double phi_d0, phi_r0;    /* data misfit and regulariser at the incoming m         */
+  double phi_d1, phi_r1;    /* the same at the returned m                             */
+  double grad_norm;         /* ||J^T r + alpha K (m - m_ref)||                        */
+  int cg_iters;             /* CG iterations taken                                    */
+  double cg_rel_res;        /* final relative CG residual                             */
+  double step;              /* accepted step length (0: none)                         */
+  int backtracks;           /* halvings before acceptance                             */
+} msfv_gn_stats_t;
+int msfv_gn_step(msfv_session_t* s, double* m_dev, const double* d_obs_dev,
+                 const msfv_gn_opts_t* opts, msfv_gn_stats_t* stats);
+
 /* ---- batches (several instances, one CUDA graph) -----------------------------------
  * Captures one forward + gradient step (msfv_forward then msfv_adjoint without phi) of K
  * independent sessions as one CUDA graph: the K instances run as parallel branches, so
@@ -173,6 +205,18 @@ int msfv_batch_check(msfv_batch_t* b);
 int msfv_batch_destroy(msfv_batch_t* b);
 /* Last error of the batch (or of the last failed msfv_batch_create when b is NULL). */
 const char* msfv_batch_last_error(const msfv_batch_t* b);
+
+/* ---- autotuning ------------------------------------------------------------------
+ * Times the local basis kernel of every entity class (edges, faces, dual-cell interiors)
+ * in each of its shapes -- a warp per entity with 4 or 8 entities per block, or a block
+ * of 128 or 256 threads per entity -- on this session's problem at the model m_dev
+ * (device, N doubles; NULL = m = 0) and keeps the fastest for the session and for later
+ * sessions of the same entity shapes in this process.  variants_out (host, 4 ints, may
+ * be NULL) receives the chosen shape per class index 1..dim; ms_out (host, 16 doubles,
+ * may be NULL) the best time of shape v for class k at 4*(k-1)+v (-1: not run).
+ * Synchronises the stream; the session must run msfv_forward again before derivative
+ * calls.  MSFV_LOCAL_VARIANT=0..3 at msfv_setup forces a shape for every class. */
+int msfv_autotune(msfv_session_t* s, const double* m_dev, int* variants_out, double* ms_out);
 
 /* Free the session and its device workspace (synchronises its stream). NULL is ok. */
 int msfv_destroy(msfv_session_t* s);

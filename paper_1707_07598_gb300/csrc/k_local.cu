@@ -620,11 +620,15 @@ __device__ __forceinline__ int mapped_slot(int s, int a, int dir) {
 
 }  // namespace
 
+// Kernel shapes ("variants"): a warp per entity with 4 or 8 entities per CTA, or a CTA of
+// 128 or 256 threads per entity.  Minimum resident CTAs per SM for the register budget.
+constexpr int min_blocks(int nt, int g) { return nt * g == 128 ? 4 : (nt == 256 ? 3 : 2); }
+
 // -----------------------------------------------------------------------------
 // Basis (forward) kernel
 // -----------------------------------------------------------------------------
 template <int NT, int G>
-__global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_fwd(DevGeom g, LocalLaunch L,
+__global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom g, LocalLaunch L,
                                                      const double* __restrict__ T,
                                                      double* __restrict__ Pw, double* fac,
                                                      int* status) {
@@ -687,7 +691,7 @@ __global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_fwd(DevGeom 
 // Adjoint kernel
 // -----------------------------------------------------------------------------
 template <int NT, int G>
-__global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_adj(DevGeom g, LocalLaunch L,
+__global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_adj(DevGeom g, LocalLaunch L,
                                                      const double* __restrict__ T,
                                                      const double* __restrict__ Pw, double* fac,
                                                      const double* __restrict__ Lam,
@@ -828,7 +832,7 @@ __global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_adj(DevGeom 
 // Tangent kernel
 // -----------------------------------------------------------------------------
 template <int NT, int G>
-__global__ void __launch_bounds__(NT* G, NT == 256 ? 3 : 4) k_local_tan(DevGeom g, LocalLaunch L,
+__global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_tan(DevGeom g, LocalLaunch L,
                                                      const double* __restrict__ T,
                                                      const double* __restrict__ Dl,
                                                      const double* __restrict__ v,
@@ -956,32 +960,43 @@ void launch_k(K kern, int which, const DevGeom& g, const LocalLaunch& L, cudaStr
 }
 }  // namespace
 
+#define MSFV_VARIANT_SWITCH(V, CALL) \
+  switch (V) {                             \
+    case 0: CALL(32, 4); break;            \
+    case 1: CALL(32, 8); break;            \
+    case 2: CALL(128, 1); break;           \
+    default: CALL(256, 1); break;          \
+  }
+
+int local_variant_groups(int v) { return v == 0 ? 4 : (v == 1 ? 8 : 1); }
+
 size_t local_smem_bytes(const DevGeom& g, const LocalLaunch& L) {
-  return L.big ? smem_bytes<256, 1>(g, L) : smem_bytes<32, 4>(g, L);
+  size_t r = 0;
+#define MSFV_SMEM(NT, G) r = smem_bytes<NT, G>(g, L)
+  MSFV_VARIANT_SWITCH(L.variant, MSFV_SMEM)
+#undef MSFV_SMEM
+  return r;
 }
 
-bool local_plan(const DevGeom& g, LocalLaunch& L, int force_gw) {
-  L.big = L.nmax > 64;
+bool local_plan(const DevGeom& g, LocalLaunch& L, int force_gw, int variant) {
+  L.variant = variant >= 0 ? variant : (L.nmax > 64 ? 3 : 0);
   L.gw = force_gw ? 1 : 0;
   if (!L.gw && local_smem_bytes(g, L) > kSmemLimit) L.gw = 1;
   if (local_smem_bytes(g, L) > kSmemLimit) return false;
   const int nslot = 1 << g.d;
   L.scratch_group = scratch_group_doubles(L.nmax, L.bmax, nslot, L.gw, L.recompute);
-  if (L.big) {
-    L.grid[0] = wave_ctas<256, 1>(k_local_fwd<256, 1>, g, L);
-    L.grid[1] = wave_ctas<256, 1>(k_local_adj<256, 1>, g, L);
-    L.grid[2] = wave_ctas<256, 1>(k_local_tan<256, 1>, g, L);
-  } else {
-    L.grid[0] = wave_ctas<32, 4>(k_local_fwd<32, 4>, g, L);
-    L.grid[1] = wave_ctas<32, 4>(k_local_adj<32, 4>, g, L);
-    L.grid[2] = wave_ctas<32, 4>(k_local_tan<32, 4>, g, L);
-  }
+#define MSFV_GRIDS(NT, G)                                      \
+  L.grid[0] = wave_ctas<NT, G>(k_local_fwd<NT, G>, g, L);      \
+  L.grid[1] = wave_ctas<NT, G>(k_local_adj<NT, G>, g, L);      \
+  L.grid[2] = wave_ctas<NT, G>(k_local_tan<NT, G>, g, L)
+  MSFV_VARIANT_SWITCH(L.variant, MSFV_GRIDS)
+#undef MSFV_GRIDS
   return L.grid[0] > 0 && L.grid[1] > 0 && L.grid[2] > 0;
 }
 
 long long local_scratch_doubles(const LocalLaunch& L) {
   if (L.scratch_group == 0) return 0;
-  const int G = L.big ? 1 : 4;
+  const int G = local_variant_groups(L.variant);
   int gmax = 0;
   for (int k = 0; k < 3; ++k) gmax = L.grid[k] > gmax ? L.grid[k] : gmax;
   return (long long)gmax * G * L.scratch_group;
@@ -990,10 +1005,9 @@ long long local_scratch_doubles(const LocalLaunch& L) {
 void launch_local_forward(const DevGeom& g, const LocalLaunch& L, const double* T, double* Pw,
                           double* fac, int* status, cudaStream_t s) {
   if (L.n_ents == 0) return;
-  if (L.big)
-    launch_k<256, 1>(k_local_fwd<256, 1>, 0, g, L, s, T, Pw, fac, status);
-  else
-    launch_k<32, 4>(k_local_fwd<32, 4>, 0, g, L, s, T, Pw, fac, status);
+#define MSFV_FWD(NT, G) launch_k<NT, G>(k_local_fwd<NT, G>, 0, g, L, s, T, Pw, fac, status)
+  MSFV_VARIANT_SWITCH(L.variant, MSFV_FWD)
+#undef MSFV_FWD
 }
 
 void launch_local_adjoint(const DevGeom& g, const LocalLaunch& L, const double* T,
@@ -1002,10 +1016,10 @@ void launch_local_adjoint(const DevGeom& g, const LocalLaunch& L, const double* 
                           double* gTloc, cudaStream_t s) {
   if (L.n_ents == 0) return;
   double* f = const_cast<double*>(fac);  // written only in recompute mode (then it is scratch)
-  if (L.big)
-    launch_k<256, 1>(k_local_adj<256, 1>, 1, g, L, s, T, Pw, f, Lam, rec_p, rec_u, ZT, MU, gTloc);
-  else
-    launch_k<32, 4>(k_local_adj<32, 4>, 1, g, L, s, T, Pw, f, Lam, rec_p, rec_u, ZT, MU, gTloc);
+#define MSFV_ADJ(NT, G) \
+  launch_k<NT, G>(k_local_adj<NT, G>, 1, g, L, s, T, Pw, f, Lam, rec_p, rec_u, ZT, MU, gTloc)
+  MSFV_VARIANT_SWITCH(L.variant, MSFV_ADJ)
+#undef MSFV_ADJ
 }
 
 void launch_local_tangent(const DevGeom& g, const LocalLaunch& L, const double* T,
@@ -1013,10 +1027,9 @@ void launch_local_tangent(const DevGeom& g, const LocalLaunch& L, const double* 
                           const double* fac, double* dPw, cudaStream_t s) {
   if (L.n_ents == 0) return;
   double* f = const_cast<double*>(fac);
-  if (L.big)
-    launch_k<256, 1>(k_local_tan<256, 1>, 2, g, L, s, T, Dl, v, Pw, f, dPw);
-  else
-    launch_k<32, 4>(k_local_tan<32, 4>, 2, g, L, s, T, Dl, v, Pw, f, dPw);
+#define MSFV_TAN(NT, G) launch_k<NT, G>(k_local_tan<NT, G>, 2, g, L, s, T, Dl, v, Pw, f, dPw)
+  MSFV_VARIANT_SWITCH(L.variant, MSFV_TAN)
+#undef MSFV_TAN
 }
 
 }  // namespace msfv

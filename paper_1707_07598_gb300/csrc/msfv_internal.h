@@ -60,7 +60,8 @@ struct LocalLaunch {
   int nmax;           // largest n in this launch
   int bmax;           // largest b in this launch
   int npairs;         // bmax*(bmax+1)/2
-  int big;            // 1: one 256-thread CTA per entity; 0: one warp per entity, 4 per CTA
+  int variant;        // kernel shape: 0 a warp per entity, 4 per CTA; 1 the same, 8 per CTA;
+                      //   2 a 128-thread CTA per entity; 3 a 256-thread CTA per entity
   int gw;             // 1: the factor window, right-hand sides and coefficients live in
                       //    global memory (entities too large for shared memory)
   int recompute;      // 1: factors are not stored; the derivative kernels refactor
@@ -95,10 +96,13 @@ void launch_face_T(const DevGeom& g, const double* m, double* T, double* sig, cu
 void launch_vertices(const DevGeom& g, double* Pw, cudaStream_t s);
 // Dynamic shared memory one launch of the local kernels needs (bytes).
 size_t local_smem_bytes(const DevGeom& g, const LocalLaunch& L);
-// Choose shared- or global-memory windows (global when the shared-memory layout does not
-// fit, or when force_gw), the persistent grids and the scratch per group.  Sets L.big,
-// L.gw, L.grid, L.scratch_group; returns false when even the global layout does not fit.
-bool local_plan(const DevGeom& g, LocalLaunch& L, int force_gw);
+// Choose the kernel shape (variant >= 0, else 256-thread CTAs above 64 unknowns and
+// warps below), shared- or global-memory windows (global when the shared-memory layout
+// does not fit, or when force_gw), the persistent grids and the scratch per group.  Sets
+// L.variant, L.gw, L.grid, L.scratch_group; returns false when nothing fits.
+bool local_plan(const DevGeom& g, LocalLaunch& L, int force_gw, int variant = -1);
+int local_variant_groups(int variant);
+constexpr int kLocalVariants = 4;
 // Scratch doubles one launch class needs (all its thread groups).
 long long local_scratch_doubles(const LocalLaunch& L);
 // Basis (forward) local solves; the factors are stored in fac unless L.recompute.
@@ -148,6 +152,17 @@ struct BandLU {
   int* piv;         // n
   int* status;      // 1 int: 0 ok, 1 zero pivot
 };
+// Gauss-Newton driver kernels (k_gn.cu)
+void launch_reg_apply(const DevGeom& g, const double* x, const double* xref, double alpha,
+                      double beta, double* y, cudaStream_t s);
+void launch_reg_value(const DevGeom& g, const double* x, const double* xref, double scale,
+                      double* partials, double* out, cudaStream_t s);
+void launch_dot(const double* a, const double* b, long long n, double* partials, double* out,
+                cudaStream_t s);
+void launch_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s);
+void launch_step_clip(long long n, const double* m, double step, const double* dx, double lo,
+                      double hi, double* out, cudaStream_t s);
+
 void launch_band_build(const DevGeom& g, const double* Ac, BandLU& B, cudaStream_t s);
 void launch_band_factor(BandLU& B, cudaStream_t s);
 // rhs: Ns vectors of length Nc (index 0 = pinned unknown); solved in place,

@@ -16,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -27,6 +28,17 @@ using namespace msfv;
 namespace {
 
 std::string g_setup_error;
+
+// Kernel shapes chosen by msfv_autotune, per (dim, entity class, largest n, largest b,
+// recompute); later sessions of the same shapes start with them.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
+
+int tuned_variant(int d, int k, int nmax, int bmax, int recompute) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(std::make_tuple(d, k, nmax, bmax, recompute));
+  return it == g_tuned.end() ? -1 : it->second;
+}
 
 const char* kPhaseNames[PH_COUNT] = {
     "face_T",        "vertices",       "basis_edges",  "basis_faces",   "basis_interiors",
@@ -77,7 +89,11 @@ struct msfv_session {
   double* fac = nullptr;    // stored local factors (null in recompute mode)
   double* local_scratch = nullptr;  // per-group scratch of the local kernels
   int* local_ctr = nullptr;         // work counters of the persistent local kernels
+  long long local_scratch_n = 0;    // doubles of local_scratch
   bool recompute = false;           // local factors recomputed by the derivative kernels
+  // Gauss-Newton driver workspace (allocated by the first msfv_gn_step)
+  double *gn_g = nullptr, *gn_x = nullptr, *gn_res = nullptr, *gn_p = nullptr, *gn_q = nullptr,
+         *gn_m = nullptr, *gn_jp = nullptr, *gn_part = nullptr, *gn_sc = nullptr;
   // coarse and per-source buffers
   double *Ac = nullptr, *dAc = nullptr, *t = nullptr, *rq = nullptr, *lam = nullptr,
          *dt = nullptr, *Lam = nullptr;
@@ -344,7 +360,12 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       return fail(nullptr, MSFV_ERR_ARG, "local band too wide (coarsening too large)");
     }
     L.recompute = (desc->factor_mode == 2) ? 1 : 0;
-    if (!local_plan(g, L, force_gw)) {
+    // kernel shape: forced by MSFV_LOCAL_VARIANT, else what msfv_autotune found for this
+    // shape earlier in the process, else the default
+    int var = tuned_variant(d, k, nmax, bmax, L.recompute);
+    const char* venv = getenv("MSFV_LOCAL_VARIANT");
+    if (venv && *venv) var = std::max(0, std::min(kLocalVariants - 1, atoi(venv)));
+    if (!local_plan(g, L, force_gw, var) && (var < 0 || !local_plan(g, L, force_gw, -1))) {
       delete s;
       return fail(nullptr, MSFV_ERR_ARG, "coarsening too large for the local problems");
     }
@@ -489,7 +510,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     s->recompute = true;
     for (int k = 1; k <= d; ++k) {
       s->launch[k].recompute = 1;
-      local_plan(g, s->launch[k], force_gw);
+      local_plan(g, s->launch[k], force_gw, s->launch[k].variant);
     }
     scr = scratch_bytes();
   }
@@ -507,6 +528,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   s->gT = dalloc<double>(s, (size_t)d * N, &ce);
   if (!s->recompute) s->fac = dalloc<double>(s, (size_t)fac_total, &ce);
   if (scr) s->local_scratch = dalloc<double>(s, scr / sizeof(double), &ce);
+  s->local_scratch_n = (long long)(scr / sizeof(double));
   s->local_ctr = dalloc<int>(s, 12, &ce);
   s->Ac = dalloc<double>(s, (size_t)Nc * S3, &ce);
   s->dAc = dalloc<double>(s, (size_t)Nc * S3, &ce);
@@ -1076,4 +1098,210 @@ extern "C" int msfv_batch_destroy(msfv_batch_t* b) {
 
 extern "C" const char* msfv_batch_last_error(const msfv_batch_t* b) {
   return b ? b->err.c_str() : g_batch_error.c_str();
+}
+
+
+// =============================================================================
+// Gauss-Newton-CG step (Sec. 5): (J^T J + alpha K) dm = -(J^T r + alpha K (m - m_ref)),
+// CG on the normal equations with msfv_jvec / msfv_jtvec products, Armijo backtracking
+// on the regularised misfit, bounds by clipping.
+// =============================================================================
+namespace {
+int gn_alloc(msfv_session* s) {
+  if (s->gn_g) return MSFV_OK;
+  cudaError_t ce = cudaSuccess;
+  const size_t N = (size_t)s->dg.N, D = (size_t)s->Ns * s->Nr;
+  s->gn_g = dalloc<double>(s, N, &ce);
+  s->gn_x = dalloc<double>(s, N, &ce);
+  s->gn_res = dalloc<double>(s, N, &ce);
+  s->gn_p = dalloc<double>(s, N, &ce);
+  s->gn_q = dalloc<double>(s, N, &ce);
+  s->gn_m = dalloc<double>(s, N, &ce);
+  s->gn_jp = dalloc<double>(s, D, &ce);
+  s->gn_part = dalloc<double>(s, 1024, &ce);
+  s->gn_sc = dalloc<double>(s, 8, &ce);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    s->gn_g = nullptr;
+    return fail(s, ce == cudaErrorMemoryAllocation ? MSFV_ERR_OOM : MSFV_ERR_CUDA,
+                std::string("gn workspace: ") + cudaGetErrorString(ce));
+  }
+  return MSFV_OK;
+}
+
+// read one device scalar (synchronises the stream)
+int read_scalar(msfv_session* s, const double* dev, double* host) {
+  cudaError_t e = cudaMemcpyAsync(host, dev, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? MSFV_OK : cuda_fail(s, e, "scalar read");
+}
+
+// data misfit (1/2 ||d(m) - d_obs||^2) plus regulariser at m; runs a forward
+int gn_objective(msfv_session* s, const double* m, const double* d_obs, const msfv_gn_opts_t* o,
+                 double* phid, double* phir) {
+  int rc = run_forward(s, m, nullptr, nullptr);
+  if (rc != MSFV_OK) return rc;
+  launch_residual(s->dpred, d_obs, s->Ns * s->Nr, s->r, s->phi, s->stream);
+  launch_reg_value(s->dg, m, o->m_ref_dev, 0.5 * o->alpha, s->gn_part, s->gn_sc + 1, s->stream);
+  s->launches += 3;
+  if ((rc = read_status(s)) != MSFV_OK) return rc;
+  if ((rc = read_scalar(s, s->phi, phid)) != MSFV_OK) return rc;
+  return read_scalar(s, s->gn_sc + 1, phir);
+}
+
+int gn_dot(msfv_session* s, const double* a, const double* b, long long n, double* out) {
+  launch_dot(a, b, n, s->gn_part, s->gn_sc, s->stream);
+  s->launches += 2;
+  return read_scalar(s, s->gn_sc, out);
+}
+}  // namespace
+
+extern "C" int msfv_gn_step(msfv_session_t* s, double* m_dev, const double* d_obs_dev,
+                            const msfv_gn_opts_t* o, msfv_gn_stats_t* out) {
+  if (!s) return MSFV_ERR_ARG;
+  if (!m_dev || !d_obs_dev || !o || !out) return fail(s, MSFV_ERR_ARG, "msfv_gn_step: NULL argument");
+  if (o->alpha < 0 || o->cg_iters < 1 || o->max_backtracks < 0 || !(o->m_min < o->m_max))
+    return fail(s, MSFV_ERR_ARG, "msfv_gn_step: invalid options");
+  int rc = gn_alloc(s);
+  if (rc != MSFV_OK) return rc;
+  const DevGeom& g = s->dg;
+  const long long N = g.N;
+  cudaStream_t st = s->stream;
+  *out = msfv_gn_stats_t{};
+  // objective and gradient at m
+  double phid0 = 0, phir0 = 0;
+  if ((rc = gn_objective(s, m_dev, d_obs_dev, o, &phid0, &phir0)) != MSFV_OK) return rc;
+  if ((rc = run_jtvec(s, s->r, s->gn_g)) != MSFV_OK) return rc;
+  launch_reg_apply(g, m_dev, o->m_ref_dev, o->alpha, 1.0, s->gn_g, st);
+  s->launches += 1;
+  // CG on (J^T J + alpha K) x = -g from x = 0
+  cudaMemsetAsync(s->gn_x, 0, sizeof(double) * N, st);
+  launch_axpby(N, -1.0, s->gn_g, 0.0, s->gn_res, st);
+  launch_axpby(N, 1.0, s->gn_res, 0.0, s->gn_p, st);
+  s->launches += 2;
+  double rr = 0;
+  if ((rc = gn_dot(s, s->gn_res, s->gn_res, N, &rr)) != MSFV_OK) return rc;
+  const double gnorm = sqrt(rr);
+  int it = 0;
+  double rel = gnorm > 0 ? 1.0 : 0.0;
+  while (it < o->cg_iters && rr > 0) {
+    if ((rc = run_jvec(s, s->gn_p, s->gn_jp)) != MSFV_OK) return rc;
+    if ((rc = run_jtvec(s, s->gn_jp, s->gn_q)) != MSFV_OK) return rc;
+    launch_reg_apply(g, s->gn_p, nullptr, o->alpha, 1.0, s->gn_q, st);
+    s->launches += 1;
+    double pq = 0;
+    if ((rc = gn_dot(s, s->gn_p, s->gn_q, N, &pq)) != MSFV_OK) return rc;
+    if (!(pq > 0)) break;  // no positive curvature left along p
+    const double a = rr / pq;
+    launch_axpby(N, a, s->gn_p, 1.0, s->gn_x, st);
+    launch_axpby(N, -a, s->gn_q, 1.0, s->gn_res, st);
+    s->launches += 2;
+    double rr1 = 0;
+    if ((rc = gn_dot(s, s->gn_res, s->gn_res, N, &rr1)) != MSFV_OK) return rc;
+    ++it;
+    rel = sqrt(rr1) / gnorm;
+    if (rel <= o->cg_tol) break;
+    launch_axpby(N, 1.0, s->gn_res, rr1 / rr, s->gn_p, st);
+    s->launches += 1;
+    rr = rr1;
+  }
+  // Armijo backtracking on phi = phi_d + phi_r along x
+  double slope = 0;
+  if ((rc = gn_dot(s, s->gn_g, s->gn_x, N, &slope)) != MSFV_OK) return rc;
+  const double phi0 = phid0 + phir0;
+  double step = 1.0, phid1 = phid0, phir1 = phir0;
+  bool accepted = false;
+  int bt = 0;
+  for (; bt <= o->max_backtracks; ++bt) {
+    launch_step_clip(N, m_dev, step, s->gn_x, o->m_min, o->m_max, s->gn_m, st);
+    s->launches += 1;
+    if ((rc = gn_objective(s, s->gn_m, d_obs_dev, o, &phid1, &phir1)) != MSFV_OK) return rc;
+    if (phid1 + phir1 <= phi0 + 1e-4 * step * slope) {
+      accepted = true;
+      break;
+    }
+    step *= 0.5;
+  }
+  if (accepted) {
+    cudaError_t e = cudaMemcpyAsync(m_dev, s->gn_m, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "gn model update");
+  } else {
+    phid1 = phid0;
+    phir1 = phir0;
+    step = 0.0;
+  }
+  out->phi_d0 = phid0;
+  out->phi_r0 = phir0;
+  out->phi_d1 = phid1;
+  out->phi_r1 = phir1;
+  out->grad_norm = gnorm;
+  out->cg_iters = it;
+  out->cg_rel_res = rel;
+  out->step = step;
+  out->backtracks = accepted ? bt : bt - 1;
+  return check_launch(s, "msfv_gn_step");
+}
+
+
+// =============================================================================
+// autotuning of the local kernels' shape
+// =============================================================================
+extern "C" int msfv_autotune(msfv_session_t* s, const double* m_dev, int* variants_out,
+                             double* ms_out) {
+  if (!s) return MSFV_ERR_ARG;
+  const DevGeom& g = s->dg;
+  cudaStream_t st = s->stream;
+  const double* m = m_dev;
+  if (!m) {
+    cudaMemsetAsync(s->m_tmp, 0, sizeof(double) * (size_t)g.N, st);
+    m = s->m_tmp;
+  }
+  launch_face_T(g, m, s->T, s->sig, st);
+  launch_vertices(g, s->Pw, st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int i = 0; i < 4 * kLocalVariants && ms_out; ++i) ms_out[i] = -1.0;
+  for (int k = 1; k <= g.d; ++k) {
+    LocalLaunch& L = s->launch[k];
+    if (variants_out) variants_out[k] = L.variant;
+    if (L.n_ents == 0) continue;
+    int best = L.variant;
+    float best_ms = 1e30f;
+    for (int v = 0; v < kLocalVariants; ++v) {
+      LocalLaunch T = L;
+      if (!local_plan(g, T, L.gw, v) || T.gw != L.gw) continue;
+      if (local_scratch_doubles(T) > s->local_scratch_n) continue;
+      launch_local_forward(g, T, s->T, s->Pw, s->fac, s->status, st);  // warm-up
+      float t = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, st);
+        launch_local_forward(g, T, s->T, s->Pw, s->fac, s->status, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t = std::min(t, ms);
+      }
+      if (ms_out) ms_out[4 * k + v - 4] = t;
+      if (t < best_ms) {
+        best_ms = t;
+        best = v;
+      }
+    }
+    local_plan(g, L, L.gw, best);
+    if (variants_out) variants_out[k] = best;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tuned[std::make_tuple(g.d, k, L.nmax, L.bmax, L.recompute)] = best;
+    }
+    // the chosen shape once more, so this class's basis is in place for the next class
+    launch_local_forward(g, L, s->T, s->Pw, s->fac, s->status, st);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->have_forward = false;
+  const int rc = check_launch(s, "msfv_autotune");
+  if (rc != MSFV_OK) return rc;
+  return read_status(s);
 }

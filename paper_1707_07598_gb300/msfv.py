@@ -27,6 +27,21 @@ class MSFVError(RuntimeError):
         self.code = code
 
 
+class _GNOpts(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("m_ref_dev", ctypes.c_void_p),
+                ("cg_iters", ctypes.c_int), ("cg_tol", ctypes.c_double),
+                ("max_backtracks", ctypes.c_int), ("m_min", ctypes.c_double),
+                ("m_max", ctypes.c_double)]
+
+
+class _GNStats(ctypes.Structure):
+    _fields_ = [("phi_d0", ctypes.c_double), ("phi_r0", ctypes.c_double),
+                ("phi_d1", ctypes.c_double), ("phi_r1", ctypes.c_double),
+                ("grad_norm", ctypes.c_double), ("cg_iters", ctypes.c_int),
+                ("cg_rel_res", ctypes.c_double), ("step", ctypes.c_double),
+                ("backtracks", ctypes.c_int)]
+
+
 class _Desc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("coarsen", ctypes.c_int),
                 ("n_src", ctypes.c_int), ("src_pos", ctypes.POINTER(ctypes.c_int64)),
@@ -82,6 +97,10 @@ def load(path: Optional[str] = None):
         getattr(L, f).restype = ctypes.c_int
     L.msfv_batch_last_error.argtypes = [vp]
     L.msfv_batch_last_error.restype = ctypes.c_char_p
+    L.msfv_gn_step.argtypes = [vp, vp, vp, ctypes.POINTER(_GNOpts), ctypes.POINTER(_GNStats)]
+    L.msfv_gn_step.restype = ctypes.c_int
+    L.msfv_autotune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    L.msfv_autotune.restype = ctypes.c_int
     for f in ("msfv_setup", "msfv_forward", "msfv_adjoint", "msfv_jvec", "msfv_jtvec",
               "msfv_solve_host", "msfv_destroy", "msfv_set_stream", "msfv_info", "msfv_profile",
               "msfv_phase_times", "msfv_phase_name", "msfv_coarse_trace"):
@@ -215,6 +234,31 @@ class Session:
             self._h, m_host.ctypes.data, d_obs_host.ctypes.data, d_pred_host.ctypes.data,
             grad_host.ctypes.data, ctypes.byref(phi)))
         return d_pred_host, grad_host, phi.value
+
+    VARIANTS = ("warp x4", "warp x8", "cta128", "cta256")
+
+    def autotune(self, m=None) -> dict:
+        """Time every shape of the local basis kernel per entity class and keep the
+        fastest (msfv_autotune).  Returns {class: (chosen shape, {shape: ms})}."""
+        var = (ctypes.c_int * 4)()
+        ms = (ctypes.c_double * 16)()
+        self._check(self._lib.msfv_autotune(self._h, _ptr(m) if m is not None else None, var, ms))
+        out = {}
+        for k in range(1, self.dim + 1):
+            times = {self.VARIANTS[v]: ms[4 * (k - 1) + v] for v in range(4) if ms[4 * (k - 1) + v] >= 0}
+            out[k] = (self.VARIANTS[var[k]], times)
+        return out
+
+    def gn_step(self, m, d_obs, alpha: float, m_ref=None, cg_iters: int = 10,
+                cg_tol: float = 1e-2, max_backtracks: int = 8, bounds=(-10.0, 10.0)) -> dict:
+        """One Gauss-Newton-CG iteration (msfv_gn_step); m is updated in place."""
+        o = _GNOpts(float(alpha), _ptr(m_ref) if m_ref is not None else None, int(cg_iters),
+                    float(cg_tol), int(max_backtracks), float(bounds[0]), float(bounds[1]))
+        st = _GNStats()
+        self._check(self._lib.msfv_gn_step(self._h, _ptr(m), _ptr(d_obs), ctypes.byref(o),
+                                           ctypes.byref(st)))
+        self.version += 1
+        return {k: getattr(st, k) for k, _ in _GNStats._fields_}
 
     # -- introspection ----------------------------------------------------------------
     def info(self) -> dict:

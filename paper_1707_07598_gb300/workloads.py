@@ -283,3 +283,19 @@ def served_requests(rate: float = 50.0, duration: float = 60.0, seed: int = 5,
         iters[k] += 1
         rid += 1
     return out
+
+
+def block_model(n: Sequence[int], background: float = 0.0, amp: float = 2.0):
+    """Two conductive blocks (log-conductivity background + amp) in a homogeneous
+    half-space, for the Gauss-Newton inversion (Sec. 5.1's two-block setting; the
+    block geometry is not given there, so: side 0.25, centres (0.3, 0.5, 0.7) and
+    (0.7, 0.5, 0.7) in 3D, (0.3, 0.6) and (0.7, 0.6) in 2D)."""
+    n = tuple(int(v) for v in n)
+    m = np.full(int(np.prod(n)), float(background))
+    if len(n) == 3:
+        centres = [(0.3, 0.5, 0.7), (0.7, 0.5, 0.7)]
+    else:
+        centres = [(0.3, 0.6), (0.7, 0.6)]
+    for c in centres:
+        m = add_box(m, n, c, 0.25, amp)
+    return m

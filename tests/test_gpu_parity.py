@@ -306,3 +306,39 @@ def test_large_coarse_mesh_192_c4(dev):
     jtr = s.jtvec((d - d_obs).contiguous())
     assert float((jtr - g).norm()) <= 1e-12 * float(g.norm())
     s.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("n,c,ns,nr", [((20, 15), 5, 2, 8), ((16, 16, 16), 8, 3, 20),
+                                       ((9, 9, 6), 3, 2, 7)])
+def test_every_kernel_shape_matches_oracle(dev, monkeypatch, variant, n, c, ns, nr):
+    """Each local-kernel shape (warp x4, warp x8, 128- and 256-thread blocks) is exact."""
+    monkeypatch.setenv("MSFV_LOCAL_VARIANT", str(variant))
+    prob = W.make_problem(n, c, ns, nr, seed=191, top_layer=len(n) == 3)
+    m = W.gaussian_random_field(n, 0.2, 192)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev, factor_mode=2)
+    assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
+    v = W.noise_like(prob.N, 1.0, 193)
+    assert rel(s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy(), orc.jvec(st, v)) < TOL
+    s.close()
+
+
+def test_autotune_picks_a_shape_and_stays_exact(dev):
+    from paper_1707_07598_gb300.msfv import Session
+    prob = W.make_problem((32, 32, 32), 8, 4, 32, seed=195, top_layer=True)
+    m = W.gaussian_random_field(prob.n, 0.15, 196)
+    s = Session(prob)
+    res = s.autotune(torch.from_numpy(m).to(dev))
+    assert set(res) == {1, 2, 3}
+    for k, (choice, times) in res.items():
+        assert choice in times and times[choice] == min(times.values())
+    orc = Oracle(prob)
+    st = orc.forward(m)
+    d = s.forward(torch.from_numpy(m).to(dev)).cpu().numpy()
+    assert rel(d, st['d']) < TOL
+    # a later session of the same shapes starts with the tuned shapes
+    s2 = Session(prob)
+    d2 = s2.forward(torch.from_numpy(m).to(dev)).cpu().numpy()
+    assert rel(d2, st['d']) < TOL
+    s.close()
+    s2.close()

@@ -371,3 +371,58 @@ def test_golden_oracle_outputs_are_reproduced():
         phi, g = o.misfit_gradient(st, np.array(case['d_obs']))
         assert np.allclose(st['d'], np.array(case['d']), rtol=1e-12, atol=1e-14)
         assert np.allclose(g, np.array(case['grad']), rtol=1e-10, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------------
+# Gauss-Newton-CG driver oracle (Sec. 5)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [(5, 4), (4, 3, 5), (6, 6, 6)])
+def test_regulariser_of_a_linear_field_closed_form(n):
+    """m = x-coordinate of the cell centre: every x-face jumps by 1/n_x, so
+    R = alpha/2 (n_x - 1)/n_x (faces of the other axes see no jump)."""
+    from oracle.gn_oracle import reg_value
+    N = int(np.prod(n))
+    x = (np.arange(N) % n[0] + 0.5) / n[0]
+    assert abs(reg_value(n, x, alpha=3.0) - 1.5 * (n[0] - 1) / n[0]) < 1e-13
+    # the same along the last axis
+    last = (np.arange(N) // int(np.prod(n[:-1])) + 0.5) / n[-1]
+    assert abs(reg_value(n, last, alpha=2.0) - (n[-1] - 1) / n[-1]) < 1e-13
+
+
+@pytest.mark.parametrize("n", [(5, 4), (4, 3, 5)])
+def test_regulariser_matrix_is_the_hessian(n):
+    from oracle.gn_oracle import reg_matrix, reg_value
+    K = reg_matrix(n)
+    N = K.shape[0]
+    assert abs(K - K.T).max() < 1e-14                     # symmetric
+    assert np.abs(K @ np.ones(N)).max() < 1e-12           # constants are free
+    rng = np.random.default_rng(3)
+    m, ref = rng.standard_normal(N), rng.standard_normal(N)
+    # R(m) = alpha/2 (m - ref)^T K (m - ref) and grad R = alpha K (m - ref) (central FD)
+    assert abs(reg_value(n, m, ref, 2.0) - (m - ref) @ (K @ (m - ref))) < 1e-10
+    v = rng.standard_normal(N)
+    fd = (reg_value(n, m + 1e-6 * v, ref, 2.0) - reg_value(n, m - 1e-6 * v, ref, 2.0)) / 2e-6
+    assert abs(fd - 2.0 * v @ (K @ (m - ref))) < 1e-6 * max(1.0, abs(fd))
+    # positive semi-definite
+    assert np.linalg.eigvalsh(K.toarray()).min() > -1e-12
+
+
+def test_gauss_newton_cg_direction_equals_a_dense_solve():
+    """With as many CG iterations as unknowns the CG direction is the dense solution of
+    (J^T J + alpha K) x = -g (J assembled column by column from the oracle's jvec)."""
+    from oracle.gn_oracle import gn_step, reg_matrix
+    prob = W.make_problem((6, 6), 3, 2, 8, seed=5, top_layer=False)
+    m = W.gaussian_random_field(prob.n, 0.3, 6)
+    orc = Oracle(prob)
+    st = orc.forward(m)
+    d_obs = st['d'] * 1.05 + 1e-3
+    alpha = 1e-2
+    m1, info = gn_step(orc, m, d_obs, alpha, cg_iters=200, cg_tol=1e-14, max_backtracks=0,
+                       bounds=(-1e9, 1e9))
+    N = prob.N
+    J = np.stack([orc.jvec(st, e).ravel() for e in np.eye(N)], axis=1)
+    K = reg_matrix(prob.n).toarray()
+    g = J.T @ (st['d'] - d_obs).ravel() + alpha * K @ m
+    x = np.linalg.solve(J.T @ J + alpha * K, -g)
+    assert np.linalg.norm(info['x'] - x) <= 1e-8 * np.linalg.norm(x)
+    assert info['phi_d1'] + info['phi_r1'] < info['phi_d0'] + info['phi_r0']
