@@ -247,11 +247,13 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-// Cluster barrier (hardware; release/acquire at cluster scope, plus a device fence
-// for the global-memory vectors read with ld.global.cg by the other CTAs).
+// Cluster barrier (hardware).  barrier.cluster.arrive / wait order every prior memory
+// access of the cluster's threads, global memory included, with release / acquire
+// semantics at cluster scope; the vectors other CTAs wrote are read with ld.global.cg
+// (L2), so no device-wide fence is needed.
 __device__ __forceinline__ void gsync(Ctx& c) {
-  __threadfence();
-  c.cl.sync();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
   if (c.trace_on && c.tid == 0) {
     const long long n = c.trace[0];
     if (n + 1 < c.trace_cap) {
