@@ -114,6 +114,12 @@ int msfv_jvec(msfv_session_t* s, const double* v_dev, double* jv_dev);
  *   w_dev   Ns*Nr doubles (read only);  jtw_dev  N doubles (written). */
 int msfv_jtvec(msfv_session_t* s, const double* w_dev, double* jtw_dev);
 
+/* J^T w with the basis held fixed (Sec. 4.2, Eq. senssimple): the derivative of P(m)
+ * is left out, so only the coarse adjoint and the G(u)^T lambda term remain.  It is the
+ * paper's contrast to the adaptive-basis J^T w of msfv_jtvec (its gradient is the one
+ * Sec. 4.2 shows to be inaccurate).  Same arguments and state rule as msfv_jtvec. */
+int msfv_jtvec_fixed_basis(msfv_session_t* s, const double* w_dev, double* jtw_dev);
+
 /* One forward + gradient solve through HOST buffers: copies m_host and d_obs_host
  * to the device, runs msfv_forward and msfv_adjoint, copies d_pred and the gradient
  * back, and synchronises the stream before returning.

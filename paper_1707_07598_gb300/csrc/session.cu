@@ -728,8 +728,9 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
   return rc;
 }
 
-// J^T w for w (Ns x Nr, device) at the last forward; out: N doubles
-int run_jtvec(msfv_session* s, const double* w, double* out) {
+// J^T w for w (Ns x Nr, device) at the last forward; out: N doubles.  fixed_basis: leave
+// out the derivative of the basis (the local adjoint solves), as in Sec. 4.2.
+int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = false) {
   const DevGeom& g = s->dg;
   cudaStream_t st = s->stream;
   const int d = g.d;
@@ -746,7 +747,7 @@ int run_jtvec(msfv_session* s, const double* w, double* out) {
     cudaMemsetAsync(s->gT, 0, sizeof(double) * (size_t)d * g.N, st);
     s->launches += 2;
   }
-  for (int k = d; k >= 1; --k) {
+  for (int k = d; k >= 1 && !fixed_basis; --k) {
     PhaseScope ps(s, k == d ? PH_ADJ_INTERIOR : (k == 1 ? PH_ADJ_EDGE : PH_ADJ_FACE));
     launch_local_adjoint(g, s->launch[k], s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u, s->ZT,
                          s->X, s->gT, st);
@@ -835,6 +836,13 @@ extern "C" int msfv_jtvec(msfv_session_t* s, const double* w_dev, double* jtw_de
   if (!w_dev || !jtw_dev) return fail(s, MSFV_ERR_ARG, "msfv_jtvec: NULL argument");
   if (!s->have_forward) return fail(s, MSFV_ERR_STATE, "msfv_jtvec before msfv_forward");
   return run_jtvec(s, w_dev, jtw_dev);
+}
+
+extern "C" int msfv_jtvec_fixed_basis(msfv_session_t* s, const double* w_dev, double* jtw_dev) {
+  if (!s) return MSFV_ERR_ARG;
+  if (!w_dev || !jtw_dev) return fail(s, MSFV_ERR_ARG, "msfv_jtvec_fixed_basis: NULL argument");
+  if (!s->have_forward) return fail(s, MSFV_ERR_STATE, "msfv_jtvec_fixed_basis before msfv_forward");
+  return run_jtvec(s, w_dev, jtw_dev, true);
 }
 
 extern "C" int msfv_solve_host(msfv_session_t* s, const double* m_host, const double* d_obs_host,

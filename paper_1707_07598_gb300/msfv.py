@@ -71,6 +71,8 @@ def load(path: Optional[str] = None):
     L.msfv_adjoint.argtypes = [vp, vp, vp, dp]
     L.msfv_jvec.argtypes = [vp, vp, vp]
     L.msfv_jtvec.argtypes = [vp, vp, vp]
+    L.msfv_jtvec_fixed_basis.argtypes = [vp, vp, vp]
+    L.msfv_jtvec_fixed_basis.restype = ctypes.c_int
     L.msfv_solve_host.argtypes = [vp, vp, vp, vp, vp, dp]
     L.msfv_destroy.argtypes = [vp]
     L.msfv_last_error.argtypes = [vp]
@@ -218,6 +220,14 @@ class Session:
         if out is None:
             out = torch.empty(self.N, dtype=torch.float64, device=w.device)
         self._check(self._lib.msfv_jtvec(self._h, _ptr(w), _ptr(out)))
+        return out
+
+    def jtvec_fixed_basis(self, w, out=None):
+        """J^T w with the basis held fixed (the Sec. 4.2 contrast)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.N, dtype=torch.float64, device=w.device)
+        self._check(self._lib.msfv_jtvec_fixed_basis(self._h, _ptr(w), _ptr(out)))
         return out
 
     def solve_host(self, m_host: np.ndarray, d_obs_host: np.ndarray, d_pred_host=None,

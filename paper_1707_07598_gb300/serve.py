@@ -224,13 +224,21 @@ class GpuBackend:
             raise DoesNotFit()
         stream = torch.cuda.Stream(device=self.device)
         prob = spec.problem()
+        # this backend's own device buffers: m_0, dm, m, d_obs and the graph's outputs
+        own = 8 * (4 * prob.N + 2 * prob.n_src * prob.n_rec)
+        if budget_bytes <= own:
+            raise DoesNotFit()
         try:
             sess = Session(prob, stream=stream, factor_mode=self.factor_mode,
-                           hbm_budget_bytes=int(budget_bytes))
+                           hbm_budget_bytes=int(budget_bytes - own))
         except MSFVError as e:
             if e.code == 2:
                 raise DoesNotFit() from e
             raise
+        if int(sess.info()["workspace_bytes"]) + own > budget_bytes:
+            # the library's up-front estimate was short of what it allocated
+            sess.close()
+            raise DoesNotFit()
         with torch.cuda.stream(stream):
             m0 = W.gaussian_random_field_device(prob.n, spec.corr_len, spec.seed, self.device)
             g = torch.Generator(device=self.device)
@@ -248,7 +256,7 @@ class GpuBackend:
             h["d_pred"] = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64,
                                       device=self.device)
             h["grad"] = torch.empty(prob.N, dtype=torch.float64, device=self.device)
-        nbytes = int(sess.info()["workspace_bytes"]) + 8 * (3 * prob.N + 2 * prob.n_src * prob.n_rec)
+        nbytes = int(sess.info()["workspace_bytes"]) + own
         return h, nbytes
 
     def launch(self, h, req):

@@ -342,3 +342,34 @@ def test_autotune_picks_a_shape_and_stays_exact(dev):
     assert rel(d2, st['d']) < TOL
     s.close()
     s2.close()
+
+
+@pytest.mark.parametrize("n,c,ns,nr", [((16, 16), 4, 2, 9), ((16, 16, 16), 8, 3, 20)])
+def test_fixed_basis_jtvec_matches_oracle_and_is_the_worse_gradient(dev, n, c, ns, nr):
+    """J^T w with the basis held fixed (Sec. 4.2) against the oracle, and the contrast the
+    paper draws: the adaptive-basis gradient matches central differences, the fixed-basis
+    one does not (Sec. 4.2's study of the gradient error)."""
+    prob = W.make_problem(n, c, ns, nr, seed=201, top_layer=len(n) == 3)
+    m = W.gaussian_random_field(n, 0.2, 202)
+    orc = Oracle(prob)
+    st = orc.forward(m)
+    from paper_1707_07598_gb300.msfv import Session
+    s = Session(prob)
+    mt = torch.from_numpy(m).to(dev)
+    d = s.forward(mt)
+    w = W.noise_like((prob.n_src, prob.n_rec), 1.0, 203)
+    gf = s.jtvec_fixed_basis(torch.from_numpy(w).to(dev)).cpu().numpy()
+    assert rel(gf, orc.jtvec_fixed_basis(st, w)) < TOL
+    # gradients of phi = <w, d(m)> along random directions: adaptive vs fixed vs FD
+    ga = s.jtvec(torch.from_numpy(w).to(dev)).cpu().numpy()
+    err_a, err_f = [], []
+    wt = torch.from_numpy(w).to(dev)
+    for k in range(5):
+        v = W.noise_like(prob.N, 1.0, 210 + k)
+        vt = torch.from_numpy(v).to(dev)
+        fd = (float((s.forward(mt + 1e-6 * vt) * wt).sum()) -
+              float((s.forward(mt - 1e-6 * vt) * wt).sum())) / 2e-6
+        err_a.append(abs(ga @ v - fd) / abs(fd))
+        err_f.append(abs(gf @ v - fd) / abs(fd))
+    assert max(err_a) < 1e-6 and min(err_f) > 1e-4
+    s.close()
