@@ -426,18 +426,16 @@ __device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int n
       Wc[dl] = acc;
     }
     panel_sync<NT>();
+    // every panel thread takes the pivot's reciprocal itself: no barrier on the chain
+    const double dq = Wc[0];
+    const double rd = 1.0 / dq;
     if (tid == 0) {
-      const double dq = Wc[0];
       if (!(dq > 0.0) && status) atomicExch(status, 1);
-      rdp[q] = 1.0 / dq;
+      rdp[q] = rd;
     }
-    panel_sync<NT>();
-    const double rd = rdp[q];
-    for (int k = tid; k <= b; k += PA) {
+    for (int k = tid + 1; k <= b; k += PA) {
       double outv = 0.0;
-      if (k == 0) {
-        outv = rd;
-      } else if (k <= bq) {
+      if (k <= bq) {
         const double t = Wc[k];
         outv = t * rd;
         tp[q * LPS + q + k] = t;
@@ -445,22 +443,36 @@ __device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int n
       }
       fac_e[(long long)c * FB + k] = outv;
     }
-    for (int i = tid; i < nvs; i += PA) {
-      double z = sm.Z[i * nmax + c];
-      for (int p = 0; p < q; ++p) z = fma(-lp[p * LPS + q], zj[p * 8 + i], z);
-      zj[q * 8 + i] = z;
-      sm.Z[i * nmax + c] = z * rd;
-    }
     panel_sync<NT>();
   }
+  // the pivots' reciprocals (written after every thread has read the pivots: with the
+  // global window the factor storage is the window itself)
+  for (int q = tid; q < Kc; q += PA) fac_e[(long long)(j + q) * FB] = rdp[q];
+  // forward substitution of the panel rows: a unit lower triangle per right-hand side
+  for (int i = tid; i < nvs; i += PA) {
+    double zq[KP];
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+      if (q < Kc) {
+        double z = sm.Z[i * nmax + j + q];
+#pragma unroll
+        for (int p = 0; p < q; ++p) z = fma(-lp[p * LPS + q], zq[p], z);
+        zq[q] = z;
+        zj[q * 8 + i] = z;
+        sm.Z[i * nmax + j + q] = z * rdp[q];
+      }
+    }
+  }
+  panel_sync<NT>();
 }
 
 // Blocked banded LDL^T of L_E with the forward substitution of the nvs right-hand
 // sides in Z fused into the sweep, then the blocked backward substitution.  Columns are
-// factored in panels of KP.  While all other threads apply panel p's rank-KP update to
-// the trailing window and the right-hand sides, the first 64 threads first update the
-// KP columns of panel p+1 and then factor it (look-ahead), so there is one CTA barrier
-// per panel.  The window is a ring of RS = ring_slots(bmax) columns (column c in slot
+// factored in panels of KP.  Per panel p: all threads apply p's rank-KP update to the KP
+// columns of panel p+1 (a short step, so the chain below starts early); then, while the
+// other threads apply p's update to the rest of the trailing window and the right-hand
+// sides, the first 64 threads factor panel p+1 (look-ahead).  Two block barriers per
+// panel.  The window is a ring of RS = ring_slots(bmax) columns (column c in slot
 // c % RS), each holding rows c..c+b.  On return Z holds the solutions; the factor is
 // stored to fac_e: column j at j*(b+1) holds 1/d_j then l_{j+1..j+b, j} (zeros past n).
 template <int NT>
@@ -490,23 +502,28 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short*
     const double* lp = sm.lp + pb * KP * LPS;
     const double* tp = sm.tp + pb * KP * LPS;
     const double* zj = sm.zj + pb * 8 * KP;
-    if (NT == 32 || tid < PA) {
-      // (1) columns base+1 .. base+K1 (the next panel) and their right-hand-side rows
-      for (int k2 = 1; k2 <= K1; ++k2) {
+    // (1) every thread: panel p's update of columns base+1 .. base+K1 (the next panel)
+    // and of their right-hand-side rows
+    {
+      const int ncol = K1 * bj - K1 * (K1 - 1) / 2;  // sum over k2 of (bj - k2 + 1)
+      for (int it = tid; it < ncol; it += NT) {
+        int k2 = 1, off = it;
+        while (off > bj - k2) {
+          off -= bj - k2 + 1;
+          ++k2;
+        }
+        const int k1 = k2 + off;
         int slot = sb + k2 - 1;
         if (slot >= RS) slot -= RS;
         double* Wc = W + slot * B1s;
-        const int ci = Kc - 1 + k2;
-        for (int k1 = k2 + tid; k1 <= bj; k1 += PA) {
-          const int ri = Kc - 1 + k1;
-          double acc = Wc[k1 - k2];
+        const int ri = Kc - 1 + k1, ci = Kc - 1 + k2;
+        double acc = Wc[k1 - k2];
 #pragma unroll
-          for (int q = 0; q < KP; ++q)
-            if (q < Kc) acc = fma(-lp[q * LPS + ri], tp[q * LPS + ci], acc);
-          Wc[k1 - k2] = acc;
-        }
+        for (int q = 0; q < KP; ++q)
+          if (q < Kc) acc = fma(-lp[q * LPS + ri], tp[q * LPS + ci], acc);
+        Wc[k1 - k2] = acc;
       }
-      for (int it = tid; it < nvs * K1; it += PA) {
+      for (int it = tid; it < nvs * K1; it += NT) {
         const int i = it / K1, k = it - (it / K1) * K1 + 1;
         const int ri = Kc - 1 + k;
         double* zp = sm.Z + i * nmax + base + k;
@@ -516,10 +533,11 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short*
           if (q < Kc) acc = fma(-lp[q * LPS + ri], zj[q * 8 + i], acc);
         *zp = acc;
       }
-      panel_sync<NT>();
-      // (2) factor the next panel into the other buffer set
-      if (j + KP < n) factor_panel<NT>(E, sm, nmax, bmax, fac_e, status, j + KP, pb ^ 1, tid);
     }
+    gsync<NT>();
+    // (2) the first 64 threads factor the next panel into the other buffer set
+    if ((NT == 32 || tid < PA) && j + KP < n)
+      factor_panel<NT>(E, sm, nmax, bmax, fac_e, status, j + KP, pb ^ 1, tid);
     if (NT == 32 || tid >= PA) {
       const int t2 = (NT == 32) ? tid : tid - PA;
       constexpr int N2 = (NT == 32) ? 32 : NT - 64;
