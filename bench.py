@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--duration", type=float, default=10.0,
                    help="served: seconds of the arrival stream that are replayed")
     p.add_argument("--fd-dirs", type=int, default=20, help="diff: finite-difference directions")
+    p.add_argument("--policy", default="sjf", choices=["fifo", "sjf"],
+                   help="served: admission order of the continuous-batching loop")
     return p.parse_args()
 
 
@@ -438,8 +440,8 @@ def run_served(args):
     for mode, inflight in (("served", 8), ("plain", 1)):
         clocks = ClockSampler(0)
         clocks.start()
-        st = Server(GpuBackend(dev, use_graph=(inflight > 1)), budget,
-                    max_inflight=inflight).run(reqs)
+        st = Server(GpuBackend(dev, use_graph=(inflight > 1)), budget, max_inflight=inflight,
+                    policy=args.policy if inflight > 1 else "fifo").run(reqs)
         c = clocks.stop()
         if mode == "served":
             clk = c
@@ -457,7 +459,7 @@ def run_served(args):
            "config": {"workload": f"served_poisson_{args.rate:g}_per_s_{args.duration:g}_s",
                       "requests": len(reqs), "sizes": [32, 64, 128, 256],
                       "coarsenings": [4, 8, 16], "sources": "1-64", "hbm_budget_bytes": budget,
-                      "max_inflight": 8},
+                      "max_inflight": 8, "policy": args.policy},
            "served": sv, "plain": res["plain"],
            "speedup_vs_plain": sv["value"] / max(res["plain"]["value"], 1e-12), "clocks": clk}
     print(json.dumps(out))

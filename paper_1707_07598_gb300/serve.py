@@ -75,15 +75,34 @@ class Stats:
         return float(np.percentile(lat, q)) if lat else float("nan")
 
 
+def estimated_work(spec) -> float:
+    """Relative cost of one forward + gradient request.  The local solves cost about
+    n b^2 per dual cell, n ~ (c-1)^d unknowns and half bandwidth b ~ (c-1)^(d-1), over
+    N / c^d dual cells; the coarse solve about 400 flops per coarse node and source."""
+    d = len(spec.n)
+    N = float(np.prod(spec.n))
+    c = max(int(spec.coarsen), 1)
+    cells = N / c ** d
+    local = cells * float(max(c - 1, 1)) ** (3 * d - 2)
+    coarse = cells * 400.0 * spec.n_src
+    return local + coarse
+
+
 class Server:
     """Continuous-batching request loop over a backend with open / launch / done / close.
 
     max_inflight = 1 gives the plain one-at-a-time path (no overlap), with the same
-    admission and eviction rules."""
+    admission and eviction rules.  policy "fifo" admits in arrival order; "sjf" admits
+    the queued requests with the smallest estimated work first (a client's requests
+    still run in order), which keeps small requests from waiting behind large ones."""
 
     def __init__(self, backend, budget_bytes: int, max_inflight: int = 8,
                  clock: Callable[[], float] = time.perf_counter, idle_sleep: float = 2e-4,
-                 keep_results: bool = False, sleep: Callable[[float], None] = time.sleep):
+                 keep_results: bool = False, sleep: Callable[[float], None] = time.sleep,
+                 policy: str = "fifo"):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be 'fifo' or 'sjf'")
+        self.policy = policy
         self.backend = backend
         self.budget = int(budget_bytes)
         self.max_inflight = max(1, int(max_inflight))
@@ -155,10 +174,19 @@ class Server:
                 else:
                     still.append((req, s, tok))
             inflight = still
-            # admissions, in arrival order; a client's requests stay in order
+            # admissions, in arrival order (or smallest work first); a client's requests
+            # stay in order
             blocked = set()
             rest = []
-            for req in queue:
+            order = queue
+            if self.policy == "sjf":
+                first = {}
+                for q in queue:                    # each client's earliest queued request
+                    first.setdefault(q.client, q)
+                heads = sorted(first.values(), key=lambda q: (estimated_work(q.instance), q.arrival))
+                head_ids = {id(q) for q in heads}
+                order = heads + [q for q in queue if id(q) not in head_ids]
+            for req in order:
                 if req.client in blocked or len(inflight) >= self.max_inflight:
                     rest.append(req)
                     blocked.add(req.client)
@@ -185,7 +213,7 @@ class Server:
                 r.status = "running"
                 inflight.append((req, s, self.backend.launch(s.handle, req)))
                 progressed = True
-            queue = rest
+            queue = sorted(rest, key=lambda r: (r.arrival, r.rid))
             if not progressed:
                 if nxt < len(reqs) and not inflight and not queue:
                     wait = reqs[nxt].arrival - (self.clock() - t0)

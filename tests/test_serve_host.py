@@ -123,3 +123,24 @@ def test_served_request_stream_shape():
         seen[q.client] = q.iteration + 1
         assert q.instance.n[0] in (32, 64, 128, 256) and q.instance.coarsen in (4, 8, 16)
         assert 1 <= q.instance.n_src <= 64
+
+
+def test_smallest_work_first_cuts_the_median_latency_under_overload():
+    rs = W.served_requests(rate=400.0, duration=1.0, seed=13, sizes=(16, 32, 64),
+                           coarsenings=(4, 8), max_src=8)
+    out = {}
+    for pol in ("fifo", "sjf"):
+        clk = FakeClock()
+        out[pol] = Server(FakeBackend(clk), 10 ** 9, max_inflight=2, clock=clk,
+                          sleep=clk.sleep, policy=pol).run(rs)
+        assert all(r.status == "done" for r in out[pol].records)
+    assert out["sjf"].percentile(50) < out["fifo"].percentile(50)
+    # client order is still respected under sjf
+    rec = {r.rid: r for r in out["sjf"].records}
+    by_client = {}
+    for q in rs:
+        by_client.setdefault(q.client, []).append(q)
+    for qs in by_client.values():
+        qs.sort(key=lambda q: q.iteration)
+        for a, b in zip(qs, qs[1:]):
+            assert rec[b.rid].start >= rec[a.rid].finish
