@@ -37,11 +37,11 @@ METRIC = "batched/served MSFV fwd+grad solves/s vs plain at 1e-9 rel err; p50/p9
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x 2 flop x max SM clock
 WORKLOAD = "3d_128^3_c8_16dipoles_512rec_fwd+grad"
 # DRAM bytes (read + write) of one k_local_fwd<256,1> launch per fine cell, from the ncu
-# capture of the current kernel at 64^3, c=8 (12.26 MB read + 13.18 MB write over 262144
+# capture of the current kernel at 64^3, c=8 (12.32 MB read + 13.16 MB write over 262144
 # cells; profiles/k_local_fwd_interiors_3d_64cube_c8.md).  The kernel's traffic (factor and
 # basis writes, conductivity reads) grows with the number of cells, so a launch on another
 # mesh is scaled by its cell count.  Set to None whenever the kernel changes.
-INTERIOR_DRAM_BYTES_PER_CELL = (12.25856e6 + 13.181696e6) / 64 ** 3
+INTERIOR_DRAM_BYTES_PER_CELL = (12.322816e6 + 13.156096e6) / 64 ** 3
 
 
 def parse():

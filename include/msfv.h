@@ -32,6 +32,10 @@
  *    gives a one-line message.  No call throws and there is no CPU fallback:
  *    without a usable GPU the calls fail with MSFV_ERR_CUDA.
  *  - All arithmetic is IEEE FP64.
+ *  - Numerical failures (a non-positive local pivot, e.g. from a NaN model value; a
+ *    singular or unconverged coarse solve) are recorded on the device and reported as
+ *    MSFV_ERR_NUMERIC by the next call that reads the status (msfv_adjoint with phi_host,
+ *    msfv_solve_host, msfv_batch_check, msfv_gn_step); msfv_forward clears the record.
  */
 #ifndef MSFV_H
 #define MSFV_H

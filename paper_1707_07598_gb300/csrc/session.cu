@@ -685,6 +685,9 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
   const DevGeom& g = s->dg;
   cudaStream_t st = s->stream;
   const int d = g.d;
+  // numerical status (pivots, coarse convergence) refers to the latest forward and the
+  // derivative calls after it
+  cudaMemsetAsync(s->status, 0, sizeof(int) * (2 + (size_t)s->Ns), st);
   {
     PhaseScope ps(s, PH_FACE_T);
     launch_face_T(g, m, s->T, s->sig, st);

@@ -373,3 +373,35 @@ def test_fixed_basis_jtvec_matches_oracle_and_is_the_worse_gradient(dev, n, c, n
         err_f.append(abs(gf @ v - fd) / abs(fd))
     assert max(err_a) < 1e-6 and min(err_f) > 1e-4
     s.close()
+
+
+def test_error_paths_report_status_without_faulting(dev):
+    """A model with a NaN cell gives MSFV_ERR_NUMERIC (non-positive / NaN local pivot) at
+    the next status read; derivative calls before any forward give MSFV_ERR_STATE; the
+    session stays usable afterwards."""
+    from paper_1707_07598_gb300.msfv import MSFVError, Session
+    prob = W.make_problem((16, 16, 16), 8, 2, 12, seed=221, top_layer=True)
+    s = Session(prob)
+    d_obs = torch.zeros((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev)
+    with pytest.raises(MSFVError) as e:
+        s.adjoint(d_obs)
+    assert e.value.code == 6
+    with pytest.raises(MSFVError) as e:
+        s.jvec(torch.zeros(prob.N, dtype=torch.float64, device=dev))
+    assert e.value.code == 6
+    m = torch.zeros(prob.N, dtype=torch.float64, device=dev)
+    m[1234] = float("nan")
+    s.forward(m)
+    with pytest.raises(MSFVError) as e:
+        s.adjoint(d_obs)
+    assert e.value.code == 3
+    # the next forward with a valid model clears the status: the session recovers
+    m_ok = W.gaussian_random_field(prob.n, 0.2, 222)
+    st = Oracle(prob).forward(m_ok)
+    assert rel(s.forward(torch.from_numpy(m_ok).to(dev)).cpu().numpy(), st['d']) < TOL
+    s.adjoint(d_obs)
+    s.close()
+    # a fresh session on the same device works
+    s2 = Session(prob)
+    assert rel(s2.forward(torch.from_numpy(m_ok).to(dev)).cpu().numpy(), st['d']) < TOL
+    s2.close()
