@@ -529,16 +529,21 @@ __device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV
                               const long long* off, double* mem) {
   const int tr = P.transpose;
   const double om = P.omega;
+  const int nu1 = tr ? P.nu1t : P.nu1, nu2 = tr ? P.nu2t : P.nu2;
   // per local level l >= P.ld: r, x, s at offsets off[l] (3 n_l doubles each)
   for (int l = P.ld; l < P.nlev - 1; ++l) {
     const MGLevelDev& L = LV[l];
     double* r = mem + off[l];
     double* x = r + L.n;
     double* s = x + L.n;
-    for (long long i = c.tid; i < L.n; i += NTH) s[i] = om * L.dinv[i] * r[i];
-    __syncthreads();
-    for (long long i = c.tid; i < L.n; i += NTH)
-      x[i] = fma(om * L.dinv[i], r[i] - apply_row<D>(L, tr, i, SVec{s}), s[i]);
+    if (nu1 >= 2) {
+      for (long long i = c.tid; i < L.n; i += NTH) s[i] = om * L.dinv[i] * r[i];
+      __syncthreads();
+      for (long long i = c.tid; i < L.n; i += NTH)
+        x[i] = fma(om * L.dinv[i], r[i] - apply_row<D>(L, tr, i, SVec{s}), s[i]);
+    } else {
+      for (long long i = c.tid; i < L.n; i += NTH) x[i] = om * L.dinv[i] * r[i];
+    }
     __syncthreads();
     for (long long i = c.tid; i < L.n; i += NTH) s[i] = r[i] - apply_row<D>(L, tr, i, SVec{x});
     __syncthreads();
@@ -572,8 +577,12 @@ __device__ void coarse_vcycle(Ctx& c, const MGParamsDev& P, const MGLevelDev* LV
     for (long long i = c.tid; i < L.n; i += NTH)
       s[i] = fma(om * L.dinv[i], r[i] - apply_row<D>(L, tr, i, SVec{x}), x[i]);
     __syncthreads();
-    for (long long i = c.tid; i < L.n; i += NTH)
-      x[i] = fma(om * L.dinv[i], r[i] - apply_row<D>(L, tr, i, SVec{s}), s[i]);
+    if (nu2 >= 2) {
+      for (long long i = c.tid; i < L.n; i += NTH)
+        x[i] = fma(om * L.dinv[i], r[i] - apply_row<D>(L, tr, i, SVec{s}), s[i]);
+    } else {
+      for (long long i = c.tid; i < L.n; i += NTH) x[i] = s[i];
+    }
     __syncthreads();
   }
 }
@@ -599,24 +608,35 @@ __device__ __forceinline__ void coarse_range(const MGLevelDev& L, const MGLevelD
 // Pre-smoothing of a level spread over the cluster: two damped Jacobi sweeps from zero
 // (the first one, x = om D^-1 r, is folded into the second) and the residual s = r - A x.
 template <int D>
-__device__ __forceinline__ void smooth_down(Ctx& c, const MGLevelDev& L, int tr, double om,
+__device__ __forceinline__ void smooth_down(Ctx& c, const MGLevelDev& L, int tr, double om, int nu1,
                                             const double* r, double* x, double* s) {
   long long b, e;
   chunk(L.n, c.rank, c.G, b, e);
   const long long H = halo(L);
-  c.tag = 2;
-  {
+  if (nu1 >= 2) {
+    c.tag = 2;
+    {
+      const Vec y = stage_range(c, r, b - H, e + H, L.n, L.dinv, om);
+      for (long long i = b + c.tid; i < e; i += NTH) {
+        const double ri = ldcg(r + i);
+        x[i] = fma(om * L.dinv[i], ri - apply_row<D>(L, tr, i, y), y[i]);
+      }
+    }
+    gsync(c);
+    c.tag = 3;
+    {
+      const Vec xv = stage_range(c, x, b - H, e + H, L.n);
+      for (long long i = b + c.tid; i < e; i += NTH) s[i] = ldcg(r + i) - apply_row<D>(L, tr, i, xv);
+    }
+  } else {
+    // one sweep from zero, x = om D^-1 r, is pointwise: the residual uses it directly
+    c.tag = 3;
     const Vec y = stage_range(c, r, b - H, e + H, L.n, L.dinv, om);
     for (long long i = b + c.tid; i < e; i += NTH) {
       const double ri = ldcg(r + i);
-      x[i] = fma(om * L.dinv[i], ri - apply_row<D>(L, tr, i, y), y[i]);
+      x[i] = om * L.dinv[i] * ri;
+      s[i] = ri - apply_row<D>(L, tr, i, y);
     }
-  }
-  gsync(c);
-  c.tag = 3;
-  {
-    const Vec xv = stage_range(c, x, b - H, e + H, L.n);
-    for (long long i = b + c.tid; i < e; i += NTH) s[i] = ldcg(r + i) - apply_row<D>(L, tr, i, xv);
   }
   gsync(c);
 }
@@ -624,8 +644,8 @@ __device__ __forceinline__ void smooth_down(Ctx& c, const MGLevelDev& L, int tr,
 // Coarse-grid correction x += P x_C and two post-smoothing sweeps, spread over the cluster.
 template <int D>
 __device__ __forceinline__ void smooth_up(Ctx& c, const MGLevelDev& L, const MGLevelDev& C, int tr,
-                                          double om, const double* r, double* x, double* s,
-                                          const double* xc) {
+                                          double om, int nu2, const double* r, double* x,
+                                          double* s, const double* xc) {
   long long b, e;
   chunk(L.n, c.rank, c.G, b, e);
   const long long H = halo(L);
@@ -637,18 +657,32 @@ __device__ __forceinline__ void smooth_up(Ctx& c, const MGLevelDev& L, const MGL
     for (long long i = b + c.tid; i < e; i += NTH) x[i] = ldcg(x + i) + prolong_row<D>(L, C, i, cv);
   }
   gsync(c);
-  c.tag = 6;
-  {
-    const Vec xv = stage_range(c, x, b - H, e + H, L.n);
-    for (long long i = b + c.tid; i < e; i += NTH)
-      s[i] = fma(om * L.dinv[i], ldcg(r + i) - apply_row<D>(L, tr, i, xv), xv[i]);
-  }
-  gsync(c);
-  c.tag = 7;
-  {
-    const Vec sv = stage_range(c, s, b - H, e + H, L.n);
-    for (long long i = b + c.tid; i < e; i += NTH)
-      x[i] = fma(om * L.dinv[i], ldcg(r + i) - apply_row<D>(L, tr, i, sv), sv[i]);
+  if (nu2 >= 2) {
+    c.tag = 6;
+    {
+      const Vec xv = stage_range(c, x, b - H, e + H, L.n);
+      for (long long i = b + c.tid; i < e; i += NTH)
+        s[i] = fma(om * L.dinv[i], ldcg(r + i) - apply_row<D>(L, tr, i, xv), xv[i]);
+    }
+    gsync(c);
+    c.tag = 7;
+    {
+      const Vec sv = stage_range(c, s, b - H, e + H, L.n);
+      for (long long i = b + c.tid; i < e; i += NTH)
+        x[i] = fma(om * L.dinv[i], ldcg(r + i) - apply_row<D>(L, tr, i, sv), sv[i]);
+    }
+  } else {
+    // one sweep into s (s is free after the restriction), then copied into x by the
+    // rows' owners: x and s cannot alias within the sweep
+    c.tag = 6;
+    {
+      const Vec xv = stage_range(c, x, b - H, e + H, L.n);
+      for (long long i = b + c.tid; i < e; i += NTH)
+        s[i] = fma(om * L.dinv[i], ldcg(r + i) - apply_row<D>(L, tr, i, xv), xv[i]);
+    }
+    gsync(c);
+    c.tag = 7;
+    for (long long i = b + c.tid; i < e; i += NTH) x[i] = s[i];
   }
   gsync(c);
 }
@@ -686,7 +720,7 @@ __device__ __forceinline__ void vcycle(Ctx& c, const MGParamsDev& P, const MGLev
     const double* r = (l == 0) ? r0 : dist + DOFF[l];
     double* x = (l == 0) ? x0 : dist + DOFF[l] + L.n;
     double* s = (l == 0) ? s0 : dist + DOFF[l] + 2 * L.n;
-    smooth_down<D>(c, L, tr, om, r, x, s);
+    smooth_down<D>(c, L, tr, om, tr ? P.nu1t : P.nu1, r, x, s);
     c.tag = 4;
     if (l + 1 < ld) {
       // restriction into the next distributed level
@@ -716,7 +750,7 @@ __device__ __forceinline__ void vcycle(Ctx& c, const MGParamsDev& P, const MGLev
     double* x = (l == 0) ? x0 : dist + DOFF[l] + L.n;
     double* s = (l == 0) ? s0 : dist + DOFF[l] + 2 * L.n;
     const double* xc = (l + 1 == ld) ? dist + DOFF[ld] : dist + DOFF[l + 1] + C.n;
-    smooth_up<D>(c, L, C, tr, om, r, x, s, xc);
+    smooth_up<D>(c, L, C, tr, om, tr ? P.nu2t : P.nu2, r, x, s, xc);
   }
 }
 
@@ -1033,6 +1067,10 @@ cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose,
   P.tol = H.tol;
   P.tol_true = H.tol_true;
   P.omega = H.omega;
+  P.nu1 = H.nu1;
+  P.nu2 = H.nu2;
+  P.nu1t = H.nu1t;
+  P.nu2t = H.nu2t;
   P.transpose = transpose;
   P.ws = H.ws;
   P.rhs_stride = H.rhs_stride;

@@ -187,6 +187,8 @@ struct MGHost {
   double* invT = nullptr;     // same for the transposed operator
   int m = 24, max_cycles = 4;   // m <= 24 (register-resident Gram-Schmidt)
   double tol = 1e-15, tol_true = 1e-13, omega = 0.85;
+  int nu1 = 2, nu2 = 2;       // pre / post damped-Jacobi sweeps (1 or 2) with A_c
+  int nu1t = 2, nu2t = 2;     //   and with A_c^T
   double* ws = nullptr;       // per right-hand side: V, Z, b_hat, scratch, level-1 correction
   long long rhs_stride = 0;
   int* iters = nullptr;       // per right-hand side: GMRES iterations of the last solve
@@ -204,6 +206,7 @@ struct MGParamsDev {
   const double* invT;
   int m, max_cycles;
   double tol, tol_true, omega;
+  int nu1, nu2, nu1t, nu2t;
   int transpose;
   double* ws;
   long long rhs_stride;

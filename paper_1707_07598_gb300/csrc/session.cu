@@ -485,7 +485,19 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     const char* env = getenv("MSFV_COARSE_SOLVER");
     if (env && !strcmp(env, "band")) s->use_mg = false;
     if (env && !strcmp(env, "mg")) s->use_mg = true;
-    if (s->use_mg) mg_setup_levels(s->mg, g);
+    if (s->use_mg) {
+      mg_setup_levels(s->mg, g);
+      // V-cycle smoothing (pre, post with A_c; pre, post with A_c^T), each 1 or 2 sweeps
+      const char* cyc = getenv("MSFV_MG_CYCLE");
+      int v[4];
+      if (cyc && sscanf(cyc, "%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3]) == 4) {
+        for (int q = 0; q < 4; ++q) v[q] = std::max(1, std::min(2, v[q]));
+        s->mg.nu1 = v[0];
+        s->mg.nu2 = v[1];
+        s->mg.nu1t = v[2];
+        s->mg.nu2t = v[3];
+      }
+    }
   }
   // ---- HBM budget and allocations --------------------------------------------------
   const int S3 = (d == 3) ? 27 : 9;
