@@ -246,7 +246,9 @@ int msfv_set_stream(msfv_session_t* s, void* stream);
  * out[8] / out[9]=largest number of GMRES iterations over the right-hand sides of the
  * last coarse solve with A_c / A_c^T (0 for the banded LU; reading them synchronises
  * the stream), out[10]=thread-block cluster size (CTAs, one per SM) the multigrid
- * GMRES kernel gives each right-hand side, out[11]=1 when the local factors are
+ * GMRES kernel gives each right-hand side -- or, for coarse meshes of 65536 nodes and
+ * more, the CTAs of the cooperative grid that works on all right-hand sides at once
+ * (MSFV_MG_SOLVER=all / cluster at msfv_setup forces either) --, out[11]=1 when the local factors are
  * recomputed (0 stored), out[12]=bit k set when the k-dimensional local problems are
  * factored in global memory.  n_out may be smaller than 13.
  * The environment variable MSFV_LOCAL_WINDOW=global at msfv_setup forces the global-

@@ -960,6 +960,497 @@ __global__ void __launch_bounds__(NTH, 1) k_mg_gmres(MGParamsDev P) {
 }
 #undef MSFV_GS_CASE
 
+// ---- all-SM variant ----------------------------------------------------------------
+// The same right-preconditioned GMRES(m) with the same V(2,2)-cycle, but every CTA of one
+// cooperative grid (one CTA per SM) works on all right-hand sides at once: each phase
+// takes the CTA's rows of one level for every right-hand side, so the FP64 work of a
+// phase is spread over all SMs instead of one cluster per right-hand side.  Phases end
+// with a software grid barrier (bounded wait: an expired wait sets an error flag, every
+// CTA stops and the solve reports "did not converge"); dot products are reduced per CTA
+// through shared memory and then across CTAs in CTA order (deterministic).  Per
+// right-hand side the Arnoldi vectors and the solution keep the cluster solver's layout,
+// and every level >= 1 has its r, x, s in the per-RHS block.  The Givens rotations are
+// replayed identically by every CTA from the reduced values, so all CTAs take the same
+// convergence decisions; CTA 0 keeps the rotated Hessenberg columns and back-substitutes.
+namespace {
+constexpr int NTA = 512;
+
+struct GA {
+  int cta, ncta, tid, ns, tpr, j, lt;  // this thread's right-hand side j (idle when j >= ns)
+  double* stage;                       // staging buffer (shared)
+  long long stage_cap;
+  unsigned* bar;                       // grid barrier: [0] arrivals, [1] generation
+  int* err;                            // set when a barrier wait expired
+};
+
+// Software grid barrier of the cooperative launch (all CTAs co-resident).  Returns false
+// once a wait has expired anywhere.
+__device__ __noinline__ bool gbar(const GA& a) {
+  __syncthreads();
+  if (a.tid == 0) {
+    // arrival with acquire-release semantics at GPU scope (after the block barrier, so the
+    // block's writes are released); the last arrival resets the count and releases the
+    // generation; the others poll it with acquire loads, up to a bounded number of times
+    unsigned g, arrived;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g) : "l"(a.bar + 1) : "memory");
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(a.bar) : "memory");
+    if (arrived == (unsigned)a.ncta - 1u) {
+      asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(a.bar) : "memory");
+      asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(a.bar + 1) : "memory");
+    } else {
+      long long spins = 0;
+      unsigned cur;
+      do {
+        asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(a.bar + 1) : "memory");
+        if (++spins > (1LL << 28)) {
+          atomicExch(a.err, 1);
+          break;
+        }
+      } while (cur == g);
+    }
+  }
+  __syncthreads();
+  return *(volatile int*)a.err == 0;
+}
+
+__device__ __forceinline__ void cta_rows(long long n, const GA& a, long long& b, long long& e) {
+  const long long per = (n + a.ncta - 1) / a.ncta;
+  b = min(n, per * a.cta);
+  e = min(n, b + per);
+}
+
+// View of one right-hand side's vector (global base g), staged or not.
+struct VJ {
+  const double* sm;   // staged rows [lo, ...) of this right-hand side, or null
+  const double* g;
+  long long lo;
+  const double* scale;
+  double om;
+  __device__ __forceinline__ double operator[](long long r) const {
+    if (sm) return sm[r - lo];
+    const double v = ldcg(g + r);
+    return scale ? om * scale[r] * v : v;
+  }
+};
+
+// Stage rows [lo, hi) of a per-RHS vector (RHS jj at ws + jj * rs + off) for every RHS.
+__device__ __forceinline__ VJ stage_all(const GA& a, const double* ws, long long rs, long long off,
+                                        long long lo, long long hi, long long n,
+                                        const double* scale = nullptr, double om = 0.0) {
+  lo = max(0LL, lo);
+  hi = min(n, hi);
+  const long long span = hi - lo;
+  const int jo = min(a.j, a.ns - 1);
+  VJ v{nullptr, ws + (long long)jo * rs + off, lo, scale, om};
+  __syncthreads();
+  if (span > 0 && span * a.ns <= a.stage_cap) {
+    for (long long it = a.tid; it < span * a.ns; it += NTA) {
+      const long long jj = it / span, r = lo + (it - jj * span);
+      double x = ldcg(ws + jj * rs + off + r);
+      if (scale) x *= om * scale[r];
+      a.stage[it] = x;
+    }
+    __syncthreads();
+    v.sm = a.stage + (long long)jo * span;
+  }
+  return v;
+}
+
+// Per-RHS sums of nv (<= 32) per-thread values over the CTA, then over all CTAs in CTA
+// order.  part: global [ncta][ns * 32]; tot: global [ns * 32]; out: shared [ns * 32]
+// (value q of RHS jj at jj * 32 + q).  red: shared, 8 * NTA doubles.  Two grid barriers.
+__device__ __noinline__ bool all_sums(const GA& a, const double* vals, int nv, double* red,
+                                      double* part, double* tot, double* out) {
+  for (int g0 = 0; g0 < nv; g0 += 8) {
+    const int ng = min(8, nv - g0);
+    __syncthreads();
+    for (int k = 0; k < ng; ++k) red[k * NTA + a.tid] = (a.j < a.ns) ? vals[g0 + k] : 0.0;
+    __syncthreads();
+    for (int it = a.tid; it < a.ns * ng; it += NTA) {
+      const int jj = it / ng, k = it - jj * ng;
+      const double* p = red + k * NTA + jj * a.tpr;
+      double s0 = 0.0, s1 = 0.0;
+      int q = 0;
+      for (; q + 1 < a.tpr; q += 2) {
+        s0 += p[q];
+        s1 += p[q + 1];
+      }
+      if (q < a.tpr) s0 += p[q];
+      part[(long long)a.cta * a.ns * 32 + jj * 32 + g0 + k] = s0 + s1;
+    }
+  }
+  if (!gbar(a)) return false;
+  // column c (RHS c / 32, value c % 32) of the partials is added by one warp of CTA
+  // (c mod ncta): lane l takes CTAs l, l + 32, ... and the lanes' sums are combined in a
+  // fixed shuffle tree, so the result does not depend on timing
+  {
+    const int warp = a.tid >> 5, lane = a.tid & 31;
+    int slot = 0;
+    for (int c = a.cta; c < a.ns * 32; c += a.ncta) {
+      if ((c & 31) >= nv) continue;
+      if ((slot++ % (NTA / 32)) != warp) continue;
+      double s0 = 0.0;
+      for (int k = lane; k < a.ncta; k += 32) s0 += ldcg(part + (long long)k * a.ns * 32 + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s0 += __shfl_down_sync(0xffffffffu, s0, o);
+      if (lane == 0) tot[c] = s0;
+    }
+  }
+  if (!gbar(a)) return false;
+  for (int c = a.tid; c < a.ns * 32; c += NTA) out[c] = ((c & 31) < nv) ? ldcg(tot + c) : 0.0;
+  __syncthreads();
+  return true;
+}
+
+struct AllLevels {
+  long long doff[kMaxLevels];  // per-RHS offset of level l's r, x, s (levels >= 1)
+};
+
+// One V(2,2) cycle for every right-hand side: z = M^{-1} v (level-0 vectors at per-RHS
+// offsets vo, zo, so), every level spread over the grid, the coarsest solved densely.
+template <int D>
+__device__ bool vcycle_all(const GA& a, const MGParamsDev& P, const MGLevelDev* LV,
+                           const AllLevels& AL, double* ws, long long rs, long long vo,
+                           long long zo, long long so, bool on) {
+  const int tr = P.transpose;
+  const double om = P.omega;
+  const bool act = a.j < a.ns && on;
+  double* base = ws + (long long)min(a.j, a.ns - 1) * rs;
+  const int nl = P.nlev;
+  if (nl == 1) {
+    const MGLevelDev& L = LV[0];
+    const double* inv = tr ? P.invT : P.inv;
+    long long b, e;
+    cta_rows(L.n, a, b, e);
+    for (long long i = b + a.lt; act && i < e; i += a.tpr) {
+      double acc = 0.0;
+      for (int q = 1; q < (int)L.n; ++q) acc = fma(inv[i * 8 + q], ldcg(base + vo + q), acc);
+      base[zo + i] = acc;
+    }
+    return gbar(a);
+  }
+  for (int l = 0; l < nl - 1; ++l) {
+    const MGLevelDev& L = LV[l];
+    const MGLevelDev& C = LV[l + 1];
+    const long long ro = l == 0 ? vo : AL.doff[l];
+    const long long xo = l == 0 ? zo : AL.doff[l] + L.n;
+    const long long sof = l == 0 ? so : AL.doff[l] + 2 * L.n;
+    long long b, e;
+    cta_rows(L.n, a, b, e);
+    const long long H = halo(L);
+    {
+      const VJ y = stage_all(a, ws, rs, ro, b - H, e + H, L.n, L.dinv, om);
+      for (long long i = b + a.lt; act && i < e; i += a.tpr) {
+        const double ri = ldcg(base + ro + i);
+        base[xo + i] = fma(om * L.dinv[i], ri - apply_row<D>(L, tr, i, y), y[i]);
+      }
+    }
+    if (!gbar(a)) return false;
+    {
+      const VJ xv = stage_all(a, ws, rs, xo, b - H, e + H, L.n);
+      for (long long i = b + a.lt; act && i < e; i += a.tpr)
+        base[sof + i] = ldcg(base + ro + i) - apply_row<D>(L, tr, i, xv);
+    }
+    if (!gbar(a)) return false;
+    {
+      long long bc, ec;
+      cta_rows(C.n, a, bc, ec);
+      const VJ sv{nullptr, base + sof, 0, nullptr, 0.0};
+      for (long long K = bc + a.lt; act && K < ec; K += a.tpr)
+        base[AL.doff[l + 1] + K] = restrict_row<D>(L, C, K, sv);
+    }
+    if (!gbar(a)) return false;
+  }
+  {
+    const MGLevelDev& L = LV[nl - 1];
+    const double* inv = tr ? P.invT : P.inv;
+    const long long ro = AL.doff[nl - 1], xo = AL.doff[nl - 1] + L.n;
+    long long b, e;
+    cta_rows(L.n, a, b, e);
+    for (long long i = b + a.lt; act && i < e; i += a.tpr) {
+      double acc = 0.0;
+      for (int q = 1; q < (int)L.n; ++q) acc = fma(inv[i * 8 + q], ldcg(base + ro + q), acc);
+      base[xo + i] = acc;
+    }
+    if (!gbar(a)) return false;
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    const MGLevelDev& L = LV[l];
+    const MGLevelDev& C = LV[l + 1];
+    const long long ro = l == 0 ? vo : AL.doff[l];
+    const long long xo = l == 0 ? zo : AL.doff[l] + L.n;
+    const long long sof = l == 0 ? so : AL.doff[l] + 2 * L.n;
+    const long long xco = AL.doff[l + 1] + C.n;
+    long long b, e;
+    cta_rows(L.n, a, b, e);
+    const long long H = halo(L);
+    {
+      long long clo, chi;
+      coarse_range(L, C, b, e, clo, chi);
+      const VJ cv = stage_all(a, ws, rs, xco, clo, chi, C.n);
+      for (long long i = b + a.lt; act && i < e; i += a.tpr)
+        base[xo + i] = ldcg(base + xo + i) + prolong_row<D>(L, C, i, cv);
+    }
+    if (!gbar(a)) return false;
+    {
+      const VJ xv = stage_all(a, ws, rs, xo, b - H, e + H, L.n);
+      for (long long i = b + a.lt; act && i < e; i += a.tpr)
+        base[sof + i] =
+            fma(om * L.dinv[i], ldcg(base + ro + i) - apply_row<D>(L, tr, i, xv), xv[i]);
+    }
+    if (!gbar(a)) return false;
+    {
+      const VJ sv = stage_all(a, ws, rs, sof, b - H, e + H, L.n);
+      for (long long i = b + a.lt; act && i < e; i += a.tpr)
+        base[xo + i] =
+            fma(om * L.dinv[i], ldcg(base + ro + i) - apply_row<D>(L, tr, i, sv), sv[i]);
+    }
+    if (!gbar(a)) return false;
+  }
+  return true;
+}
+}  // namespace
+
+// aux: [0..1] barrier, [2] error flag (unsigned/int words); part: ncta * ns * 32 doubles;
+// tot: ns * 32; hcol: ns * MAXM * MAXM (rotated Hessenberg columns); ybuf: ns * MAXM.
+template <int D>
+__global__ void __launch_bounds__(NTA, 1) k_mg_gmres_all(MGParamsDev P, unsigned* aux,
+                                                         double* part, double* tot,
+                                                         double* hcol, double* ybuf) {
+  extern __shared__ double dyn[];
+  __shared__ MGLevelDev LV[kMaxLevels];
+  GA a;
+  a.cta = blockIdx.x;
+  a.ncta = gridDim.x;
+  a.tid = threadIdx.x;
+  a.ns = P.Ns;
+  a.tpr = NTA / P.Ns;
+  a.j = a.tid / a.tpr;
+  a.lt = a.tid - a.j * a.tpr;
+  a.bar = aux;
+  a.err = reinterpret_cast<int*>(aux + 2);
+  const int m = min(P.m, MAXM);
+  const int ns = P.Ns;
+  // shared memory: per-RHS GMRES scalars, the reduction scratch, then staging
+  double* sv = dyn;                    // ns * 32 reduced values
+  double* hs = sv + ns * 32;           // ns * 32 first-pass Gram-Schmidt coefficients
+  double* cs = hs + ns * 32;           // ns * MAXM
+  double* sn = cs + ns * MAXM;         // ns * MAXM
+  double* gv = sn + ns * MAXM;         // ns * (MAXM + 1)
+  double* yv = gv + ns * (MAXM + 1);   // ns * MAXM
+  double* nbv = yv + ns * MAXM;        // ns
+  double* red = nbv + ns;              // 8 * NTA
+  int* ip = reinterpret_cast<int*>(red + 8 * NTA);
+  int* kk = ip;                        // ns: Krylov size of the current cycle
+  int* st = kk + ns;                   // ns: 0 converged, 2 running
+  int* on = st + ns;                   // ns: 1 while still iterating in this cycle
+  int* its = on + ns;                  // ns: iterations
+  a.stage = red + 8 * NTA + (4 * ns + 1) / 2 + 2;
+  a.stage_cap = (long long)(STAGE_CAP + CSM_CAP) - (a.stage - dyn);
+  if (a.tid == 0)
+    for (int l = 0; l < P.nlev; ++l) LV[l] = P.lev[l];
+  AllLevels AL;
+  {
+    long long o = (long long)(2 * P.m + 3) * P.lev[0].n;
+    AL.doff[0] = 0;
+#pragma unroll
+    for (int l = 1; l < kMaxLevels; ++l) {
+      AL.doff[l] = o;
+      if (l < P.nlev) o += 3 * P.lev[l].n;
+    }
+  }
+  __syncthreads();
+  const MGLevelDev& L0 = LV[0];
+  const long long n0 = L0.n, H0 = halo(L0), rs = P.rhs_stride;
+  const bool act = a.j < ns;
+  double* base = P.ws + (long long)min(a.j, ns - 1) * rs;
+  double* x = P.rhs + (long long)min(a.j, ns - 1) * n0;  // solution, in place of b
+  const long long Vo = 0, Zo = (long long)(P.m + 1) * n0, Bo = Zo + (long long)P.m * n0,
+                  So = Bo + n0;
+  long long b, e;
+  cta_rows(n0, a, b, e);
+  bool ok = true;
+  // b_hat = b - (sum b) e_0 (pinned consistent system); ||b_hat|| from the sums
+  {
+    double hp[2] = {0.0, 0.0};
+    for (long long i = b + a.lt; act && i < e; i += a.tpr) {
+      const double v = x[i];
+      base[Bo + i] = v;
+      hp[0] += v;
+      hp[1] = fma(v, v, hp[1]);
+    }
+    ok = all_sums(a, hp, 2, red, part, tot, sv);
+  }
+  if (ok) {
+    for (int jj = a.tid; jj < ns; jj += NTA) {
+      const double sumb = sv[jj * 32], b0 = ldcg(P.rhs + (long long)jj * n0);
+      nbv[jj] = sqrt(fmax(sv[jj * 32 + 1] - b0 * b0 + (b0 - sumb) * (b0 - sumb), 0.0));
+      hs[jj * 32] = sumb;
+      st[jj] = nbv[jj] > 0.0 ? 2 : 0;
+      its[jj] = 0;
+    }
+    ok = gbar(a);  // every CTA has read b_0 before CTA 0 rewrites it
+  }
+  if (ok) {
+    if (a.cta == 0 && act && a.lt == 0) base[Bo] = ldcg(x) - hs[a.j * 32];
+    for (long long i = b + a.lt; act && i < e; i += a.tpr) x[i] = 0.0;
+    ok = gbar(a);
+  }
+  for (int cyc = 0; ok && cyc <= P.max_cycles; ++cyc) {
+    // true residual r = b_hat - A x, its norm, convergence
+    {
+      const VJ xv = stage_all(a, P.rhs, n0, 0, b - H0, e + H0, n0);
+      double hp[1] = {0.0};
+      for (long long i = b + a.lt; act && i < e; i += a.tpr) {
+        const double r = ldcg(base + Bo + i) - apply_row<D>(L0, P.transpose, i, xv);
+        base[Vo + i] = r;
+        hp[0] = fma(r, r, hp[0]);
+      }
+      ok = all_sums(a, hp, 1, red, part, tot, sv);
+    }
+    if (!ok) break;
+    for (int jj = a.tid; jj < ns; jj += NTA) {
+      if (st[jj] == 2 && sqrt(sv[jj * 32]) <= P.tol_true * nbv[jj]) st[jj] = 0;
+      on[jj] = (st[jj] == 2) ? 1 : 0;
+      gv[jj * (MAXM + 1)] = sqrt(sv[jj * 32]);
+      for (int q = 1; q <= m; ++q) gv[jj * (MAXM + 1) + q] = 0.0;
+      kk[jj] = 0;
+    }
+    __syncthreads();
+    bool any = false;
+    for (int jj = 0; jj < ns; ++jj) any = any || st[jj] == 2;
+    if (!any || cyc == P.max_cycles) break;
+    if (act && on[a.j]) {
+      const double ib = 1.0 / gv[a.j * (MAXM + 1)];
+      for (long long i = b + a.lt; i < e; i += a.tpr) base[Vo + i] *= ib;
+    }
+    if (!(ok = gbar(a))) break;
+    for (int k = 0; k < m; ++k) {
+      const long long vk = Vo + (long long)k * n0, zk = Zo + (long long)k * n0,
+                      wk = Vo + (long long)(k + 1) * n0;
+      const bool me = act && on[a.j];
+      if (!(ok = vcycle_all<D>(a, P, LV, AL, P.ws, rs, vk, zk, So, me))) break;
+      {
+        const VJ zv = stage_all(a, P.ws, rs, zk, b - H0, e + H0, n0);
+        for (long long i = b + a.lt; me && i < e; i += a.tpr)
+          base[wk + i] = apply_row<D>(L0, P.transpose, i, zv);
+      }
+      __syncthreads();
+      // classical Gram-Schmidt twice; the norm by Pythagoras
+      double hp[MAXM + 2];
+      for (int q = 0; q <= k + 1; ++q) hp[q] = 0.0;
+      for (long long i = b + a.lt; me && i < e; i += a.tpr) {
+        const double wi = base[wk + i];
+        for (int q = 0; q <= k; ++q) hp[q] = fma(base[Vo + (long long)q * n0 + i], wi, hp[q]);
+      }
+      if (!(ok = all_sums(a, hp, k + 1, red, part, tot, hs))) break;
+      for (int q = 0; q <= k + 1; ++q) hp[q] = 0.0;
+      for (long long i = b + a.lt; me && i < e; i += a.tpr) {
+        double wi = base[wk + i];
+        for (int q = 0; q <= k; ++q) wi = fma(-hs[a.j * 32 + q], base[Vo + (long long)q * n0 + i], wi);
+        base[wk + i] = wi;
+        for (int q = 0; q <= k; ++q) hp[q] = fma(base[Vo + (long long)q * n0 + i], wi, hp[q]);
+        hp[k + 1] = fma(wi, wi, hp[k + 1]);
+      }
+      if (!(ok = all_sums(a, hp, k + 2, red, part, tot, sv))) break;
+      if (me) {
+        double hh = 0.0;
+        for (int q = 0; q <= k; ++q) hh = fma(sv[a.j * 32 + q], sv[a.j * 32 + q], hh);
+        const double hn = sqrt(fmax(sv[a.j * 32 + k + 1] - hh, 0.0));
+        const double ihn = hn > 0.0 ? 1.0 / hn : 0.0;
+        for (long long i = b + a.lt; i < e; i += a.tpr) {
+          double wi = base[wk + i];
+          for (int q = 0; q <= k; ++q) wi = fma(-sv[a.j * 32 + q], base[Vo + (long long)q * n0 + i], wi);
+          base[wk + i] = wi * ihn;
+        }
+      }
+      __syncthreads();
+      // Givens rotations per right-hand side, replayed identically by every CTA
+      for (int jj = a.tid; jj < ns; jj += NTA) {
+        ++its[jj];
+        if (!on[jj]) {
+          --its[jj];
+          continue;
+        }
+        double col[MAXM + 1];
+        double hh = 0.0;
+        for (int q = 0; q <= k; ++q) {
+          col[q] = hs[jj * 32 + q] + sv[jj * 32 + q];
+          hh = fma(sv[jj * 32 + q], sv[jj * 32 + q], hh);
+        }
+        const double hn = sqrt(fmax(sv[jj * 32 + k + 1] - hh, 0.0));
+        col[k + 1] = hn;
+        double* c = cs + jj * MAXM;
+        double* s = sn + jj * MAXM;
+        for (int q = 0; q < k; ++q) {
+          const double t = c[q] * col[q] + s[q] * col[q + 1];
+          col[q + 1] = -s[q] * col[q] + c[q] * col[q + 1];
+          col[q] = t;
+        }
+        const double av = col[k], bv = col[k + 1];
+        const double rr = sqrt(av * av + bv * bv);
+        c[k] = rr > 0.0 ? av / rr : 1.0;
+        s[k] = rr > 0.0 ? bv / rr : 0.0;
+        col[k] = rr;
+        double* g = gv + jj * (MAXM + 1);
+        g[k + 1] = -s[k] * g[k];
+        g[k] = c[k] * g[k];
+        if (a.cta == 0)
+          for (int q = 0; q <= k; ++q) hcol[((long long)jj * MAXM + q) * MAXM + k] = col[q];
+        kk[jj] = k + 1;
+        if (fabs(g[k + 1]) <= P.tol * nbv[jj] || hn == 0.0) on[jj] = 0;
+      }
+      if (!(ok = gbar(a))) break;  // V[k+1] complete everywhere; all CTAs agree on on[]
+      bool more = false;
+      for (int jj = 0; jj < ns; ++jj) more = more || on[jj];
+      if (!more) break;
+    }
+    if (!ok) break;
+    // y = R^{-1} g per right-hand side (CTA 0), then x += Z y
+    if (a.cta == 0)
+      for (int jj = a.tid; jj < ns; jj += NTA) {
+        const int n = kk[jj];
+        const double* g = gv + jj * (MAXM + 1);
+        for (int q = n - 1; q >= 0; --q) {
+          double t = g[q];
+          for (int p = q + 1; p < n; ++p)
+            t = fma(-hcol[((long long)jj * MAXM + q) * MAXM + p], ybuf[jj * MAXM + p], t);
+          ybuf[jj * MAXM + q] = t / hcol[((long long)jj * MAXM + q) * MAXM + q];
+        }
+      }
+    if (!(ok = gbar(a))) break;
+    if (act) {
+      const int n = kk[a.j];
+      for (int q = a.lt; q < n; q += a.tpr) yv[a.j * MAXM + q] = ldcg(ybuf + a.j * MAXM + q);
+    }
+    __syncthreads();
+    if (act) {
+      const int n = kk[a.j];
+      for (long long i = b + a.lt; i < e; i += a.tpr) {
+        double xi = x[i];
+        for (int q = 0; q < n; ++q) xi = fma(yv[a.j * MAXM + q], ldcg(base + Zo + (long long)q * n0 + i), xi);
+        x[i] = xi;
+      }
+    }
+    if (!(ok = gbar(a))) break;
+  }
+  // pin: subtract the solution's entry 0 per right-hand side
+  if (ok) {
+    if (act && a.lt == 0) nbv[a.j] = ldcg(x);
+    ok = gbar(a);
+    if (ok)
+      for (long long i = b + a.lt; act && i < e; i += a.tpr) x[i] -= nbv[a.j];
+  }
+  if (a.cta == 0 && a.tid == 0) {
+    const bool failed = !ok || *(volatile int*)a.err != 0;
+    for (int jj = 0; jj < ns; ++jj) {
+      const int stv = failed ? 2 : st[jj];
+      if (stv && P.status) P.status[jj] = stv;
+      if (P.iters) P.iters[jj] = its[jj];
+    }
+  }
+}
+
 // ---- host side -------------------------------------------------------------------------
 size_t mg_dyn_smem() { return sizeof(double) * (STAGE_CAP + CSM_CAP); }
 static_assert(9 * NTH <= STAGE_CAP, "reduction scratch must fit in the stage buffer");
@@ -1000,7 +1491,27 @@ long long mg_rhs_doubles(const MGHost& H) {
   long long v = (long long)(2 * H.m + 3) * n0;
   for (int l = 1; l < H.ld && l < H.nlev; ++l) v += 3 * H.lev[l].n;
   if (H.nlev > 1) v += H.lev[H.ld].n;
-  return v;
+  // the all-SM variant keeps r, x, s of every level >= 1 in the per-RHS block
+  long long va = (long long)(2 * H.m + 3) * n0;
+  for (int l = 1; l < H.nlev; ++l) va += 3 * H.lev[l].n;
+  return v > va ? v : va;
+}
+
+int mg_all_grid(int d) {
+  const void* fn = (d == 3) ? (const void*)k_mg_gmres_all<3> : (const void*)k_mg_gmres_all<2>;
+  const size_t dyn = mg_dyn_smem();
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+    return 0;
+  int dev = 0, sms = 0, per = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, NTA, dyn) != cudaSuccess) per = 0;
+  if (!coop || per < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;
 }
 
 bool mg_coarse_fits(const MGHost& H) { return mg_coarse_doubles(H) <= CSM_CAP; }
@@ -1083,6 +1594,27 @@ cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose,
   P.cws = H.cws;
   P.cws_stride = H.cws_stride;
   const size_t dyn = mg_dyn_smem();
+  if (H.all && H.ncta > 0 && Ns <= 64) {
+    // all-SM variant: one cooperative grid, one CTA per SM
+    cudaError_t e = cudaMemsetAsync(H.aux, 0, 4 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(H.ncta, 1, 1);
+    cfg.blockDim = dim3(NTA, 1, 1);
+    cfg.dynamicSmemBytes = dyn;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (H.d == 3) {
+      cudaFuncSetAttribute(k_mg_gmres_all<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      return cudaLaunchKernelEx(&cfg, k_mg_gmres_all<3>, P, H.aux, H.part, H.tot, H.hcol, H.ybuf);
+    }
+    cudaFuncSetAttribute(k_mg_gmres_all<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    return cudaLaunchKernelEx(&cfg, k_mg_gmres_all<2>, P, H.aux, H.part, H.tot, H.hcol, H.ybuf);
+  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -198,6 +198,14 @@ struct MGHost {
   int max_clusters = 0;       // co-resident clusters (occupancy API)
   double* cws = nullptr;      // coarse-level vectors in global memory, one block per cluster
   long long cws_stride = 0;   //   group, when they do not fit in shared memory
+  // all-SM variant: one cooperative grid works on every right-hand side
+  int all = 0;                // 1: use it
+  int ncta = 0;               // its grid (one CTA per SM)
+  unsigned* aux = nullptr;    // barrier words and error flag (zeroed per launch)
+  double* part = nullptr;     // ncta * Ns * 32 per-CTA partial sums
+  double* tot = nullptr;      // Ns * 32 reduced sums
+  double* hcol = nullptr;     // Ns * 24 * 24 rotated Hessenberg columns
+  double* ybuf = nullptr;     // Ns * 24 least-squares solutions
 };
 struct MGParamsDev {
   int d, nlev, ld;
@@ -226,6 +234,8 @@ bool mg_coarse_fits(const MGHost& H);
 long long mg_coarse_doubles(const MGHost& H);
 // doubles of one right-hand side's GMRES and distributed-level workspace
 long long mg_rhs_doubles(const MGHost& H);
+// CTAs of the all-SM variant's cooperative grid (0: not available)
+int mg_all_grid(int d);
 int mg_pick_cluster(int d, int Ns, int* max_clusters);
 void launch_mg_setup(const MGHost& H, int* status, cudaStream_t s);
 // rhs: Ns x Nc, solved in place (pinned: entry 0 of each solution is zero);

@@ -597,6 +597,26 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       return fail(nullptr, MSFV_ERR_CUDA, "thread-block clusters unavailable for the coarse solver");
     }
     H.ngroups = std::max(1, std::min(s->Ns, std::max(1, H.max_clusters)));
+    // all-SM variant for large coarse meshes, where the FP64 work of a phase outweighs
+    // its grid barriers (measured on a GB300 with 16 right-hand sides: at Nc = 4096 and
+    // 32768 the cluster kernel is faster, 3.1 / 10.2 ms against 4.9 / 12.1 ms per
+    // solve; at Nc = 110592 the all-SM one, 32.8 against 37.9 ms).  MSFV_MG_SOLVER=all
+    // or cluster overrides.
+    {
+      const char* ms = getenv("MSFV_MG_SOLVER");
+      bool want_all = Nc >= 65536;
+      if (ms && !strcmp(ms, "all")) want_all = true;
+      if (ms && !strcmp(ms, "cluster")) want_all = false;
+      H.ncta = (want_all && s->Ns <= 64) ? mg_all_grid(d) : 0;
+      H.all = H.ncta > 0 ? 1 : 0;
+      if (H.all) {
+        H.aux = dalloc<unsigned>(s, 4, &ce);
+        H.part = dalloc<double>(s, (size_t)H.ncta * s->Ns * 32, &ce);
+        H.tot = dalloc<double>(s, (size_t)s->Ns * 32, &ce);
+        H.hcol = dalloc<double>(s, (size_t)s->Ns * 24 * 24, &ce);
+        H.ybuf = dalloc<double>(s, (size_t)s->Ns * 24, &ce);
+      }
+    }
     const char* cg_env = getenv("MSFV_MG_COARSE_GLOBAL");
     if (!mg_coarse_fits(H) || (cg_env && atoi(cg_env) > 0)) {
       // coarse-level vectors in global memory, one block per cluster group
@@ -908,7 +928,8 @@ extern "C" int msfv_info(const msfv_session_t* s, int64_t* out, int n_out) {
   int64_t v[13] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
                    (int64_t)(s->h_ents[1].size() + s->h_ents[2].size() + s->h_ents[3].size()),
                    (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, s->use_mg ? 1 : 0, it[0], it[1],
-                   s->use_mg ? s->mg.group : 0, s->recompute ? 1 : 0, gw};
+                   s->use_mg ? (s->mg.all ? s->mg.ncta : s->mg.group) : 0,
+                   s->recompute ? 1 : 0, gw};
   for (int i = 0; i < n_out && i < 13; ++i) out[i] = v[i];
   return MSFV_OK;
 }

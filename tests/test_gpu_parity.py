@@ -420,3 +420,21 @@ def test_multigrid_smoothing_variants_match_oracle(dev, monkeypatch, cycle, n, c
     orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
     assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
     s.close()
+
+
+@pytest.mark.parametrize("variant", ["all", "cluster"])
+@pytest.mark.parametrize("n,c,ns,nr", [((16, 16, 16), 4, 3, 20), ((24, 16, 16), 8, 4, 30),
+                                       ((48, 48, 48), 4, 5, 30), ((128, 128), 4, 3, 24),
+                                       ((32, 32), 4, 1, 16)])
+def test_multigrid_solver_variants_match_oracle(dev, monkeypatch, variant, n, c, ns, nr):
+    """The all-SM cooperative multigrid GMRES and the cluster-per-right-hand-side one give
+    the oracle's pinned coarse solution, forward and transposed."""
+    monkeypatch.setenv("MSFV_COARSE_SOLVER", "mg")
+    monkeypatch.setenv("MSFV_MG_SOLVER", variant)
+    prob = W.make_problem(n, c, ns, nr, seed=241, top_layer=len(n) == 3)
+    m = W.gaussian_random_field(n, 0.2, 242)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
+    assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
+    info = s.info()
+    assert 0 < info["coarse_iters"] < 100 and 0 < info["coarse_iters_T"] < 100
+    s.close()
