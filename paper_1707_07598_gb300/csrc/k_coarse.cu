@@ -93,12 +93,9 @@ __global__ void k_face_T(DevGeom g, const double* __restrict__ sig, double* __re
     PER_AXIS(a) {
       double t = 0.0, dl = 0.0;
       if (xc[a] + 1 < g.n[a]) {
-        double geo = (double)g.n[a];
-        PER_AXIS(b)
-          if (b != a) geo /= (double)g.n[b];
         const double sy = sig[x + g.st[a]];
         const double inv = 1.0 / (sx + sy);
-        t = geo * 2.0 * sx * sy * inv;
+        t = g.geo[a] * 2.0 * sx * sy * inv;
         dl = t * sy * inv;
       }
       T[(long long)a * g.N + x] = t;
@@ -136,13 +133,17 @@ void launch_vertices(const DevGeom& g, double* Pw, cudaStream_t s) {
 // One thread per (coarse row I, stencil offset o): sum over the fine faces on the
 // boundary of primal coarse cell I of T_f (phi_J(inside) - phi_J(outside)), J = I + o.
 // tangent != 0: d A_c = R dA P + R A dP with dT_f = Dl v_lower + (T - Dl) v_upper.
+// One warp per entry (I, o): the lanes split the fine faces on the boundary of coarse cell
+// I (axis, side, and the face's cells) and their partial fluxes are combined in a fixed
+// shuffle tree (deterministic).
 __global__ void k_coarse_assemble(DevGeom g, const double* __restrict__ T,
                                   const double* __restrict__ Dl, const double* __restrict__ v,
                                   const double* __restrict__ Pw, const double* __restrict__ dPw,
                                   double* __restrict__ Ac, int tangent) {
   const int S3 = stencil_size(g);
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= g.Nc * S3) return;
+  const long long idx = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (idx >= g.Nc * S3) return;  // whole warps leave together
   // offset-major layout: Ac[o * Nc + I]
   const int o = (int)(idx / g.Nc);
   const long long I = idx - (long long)o * g.Nc;
@@ -155,57 +156,64 @@ __global__ void k_coarse_assemble(DevGeom g, const double* __restrict__ T,
       oo /= 3;
     }
   }
-  double acc = 0.0;
   bool valid = true;
   PER_AXIS(a)
     if (Jc[a] < 0 || Jc[a] >= g.nc[a]) valid = false;
+  double acc = 0.0;
   if (valid) {
-    PER_AXIS(a) {
-      // the two other axes span the face
+    const int n1 = g.c, n2 = (g.d == 3) ? g.c : 1;
+    const int per_face = n1 * n2;
+    const int nf = g.d * 2 * per_face;
+    for (int f = lane; f < nf; f += 32) {
+      const int a = f / (2 * per_face);
+      const int rem = f - a * 2 * per_face;
+      const int side = rem / per_face;
+      const int cell = rem - side * per_face;
+      const int i1 = cell % n1, i2 = cell / n1;
       const int b1 = (a + 1) % g.d;
-      const int n1 = g.c, n2 = (g.d == 3) ? g.c : 1;
-      for (int side = 0; side < 2; ++side) {
-        const int xa = side ? g.c * Ic[a] + g.c - 1 : g.c * Ic[a];
-        const int ya = side ? xa + 1 : xa - 1;
-        if (ya < 0 || ya >= g.n[a]) continue;
-        for (int i2 = 0; i2 < n2; ++i2)
-          for (int i1 = 0; i1 < n1; ++i1) {
-            int xc[3], yc[3];
+      // a is a runtime value: pick per-axis values with selects (no indexed locals)
+      const int Ica = a == 0 ? Ic[0] : (a == 1 ? Ic[1] : Ic[2]);
+      const int na = a == 0 ? g.n[0] : (a == 1 ? g.n[1] : g.n[2]);
+      const long long sta = a == 0 ? g.st[0] : (a == 1 ? g.st[1] : g.st[2]);
+      const int xa = side ? g.c * Ica + g.c - 1 : g.c * Ica;
+      const int ya = side ? xa + 1 : xa - 1;
+      if (ya < 0 || ya >= na) continue;
+      int xc[3], yc[3];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              int val = 0;
-              if (q < g.d) val = (q == a) ? xa : g.c * Ic[q] + (q == b1 ? i1 : i2);
-              xc[q] = val;
-              yc[q] = (q == a) ? ya : val;
-            }
-            const long long x = xc[0] + g.st[1] * xc[1] + g.st[2] * xc[2];
-            const long long y = yc[0] + g.st[1] * yc[1] + g.st[2] * yc[2];
-            const long long lower = side ? x : y;
-            const double t = T[(long long)a * g.N + lower];
-            const double px = phi_at(g, Pw, x, xc, Jc), py = phi_at(g, Pw, y, yc, Jc);
-            if (!tangent) {
-              acc = fma(t, px - py, acc);
-            } else {
-              const double dl = Dl[(long long)a * g.N + lower];
-              const double dT = dl * v[lower] + (t - dl) * v[lower + g.st[a]];
-              const double dpx = phi_at(g, dPw, x, xc, Jc), dpy = phi_at(g, dPw, y, yc, Jc);
-              acc = fma(dT, px - py, acc);
-              acc = fma(t, dpx - dpy, acc);
-            }
-          }
+      for (int q = 0; q < 3; ++q) {
+        int val = 0;
+        if (q < g.d) val = (q == a) ? xa : g.c * Ic[q] + (q == b1 ? i1 : i2);
+        xc[q] = val;
+        yc[q] = (q == a) ? ya : val;
+      }
+      const long long x = xc[0] + g.st[1] * xc[1] + g.st[2] * xc[2];
+      const long long y = yc[0] + g.st[1] * yc[1] + g.st[2] * yc[2];
+      const long long lower = side ? x : y;
+      const double t = T[(long long)a * g.N + lower];
+      const double px = phi_at(g, Pw, x, xc, Jc), py = phi_at(g, Pw, y, yc, Jc);
+      if (!tangent) {
+        acc = fma(t, px - py, acc);
+      } else {
+        const double dl = Dl[(long long)a * g.N + lower];
+        const double dT = dl * v[lower] + (t - dl) * v[lower + sta];
+        const double dpx = phi_at(g, dPw, x, xc, Jc), dpy = phi_at(g, dPw, y, yc, Jc);
+        acc = fma(dT, px - py, acc);
+        acc = fma(t, dpx - dpy, acc);
       }
     }
   }
-  Ac[idx] = acc;
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, sh);
+  if (lane == 0) Ac[idx] = acc;
 }
 
 void launch_coarse_assemble(const DevGeom& g, const double* T, const double* Pw,
                             const double* Dl_or_null, const double* v, const double* dPw,
                             double* Ac, int tangent, cudaStream_t s) {
   // Dl, v and dPw are only read when tangent != 0
-  const long long tot = g.Nc * (g.d == 3 ? 27 : 9);
-  k_coarse_assemble<<<(int)((tot + 127) / 128), 128, 0, s>>>(g, T, Dl_or_null, v, Pw, dPw, Ac,
-                                                             tangent);
+  const long long tot = g.Nc * (g.d == 3 ? 27 : 9);  // one warp per entry
+  k_coarse_assemble<<<(int)((tot * 32 + 255) / 256), 256, 0, s>>>(g, T, Dl_or_null, v, Pw, dPw, Ac,
+                                                                  tangent);
 }
 
 // ---- (e) prolongation --------------------------------------------------------------
@@ -418,33 +426,44 @@ __device__ double term_G(const DevGeom& g, const double* __restrict__ Pw,
                          const double* __restrict__ Lam, long long xl, const int* lc, long long xu,
                          const int* uc) {
   const int S3 = stencil_size(g);
-  int Kl[3] = {0, 0, 0}, Ku[3] = {0, 0, 0};
+  int Kl[3] = {0, 0, 0}, Ku[3] = {0, 0, 0}, vl[3] = {0, 0, 0}, vu[3] = {0, 0, 0};
   PER_AXIS(a) {
     Kl[a] = lc[a] / g.c;
     Ku[a] = uc[a] / g.c;
+    vl[a] = lo_vertex(g, lc[a]);
+    vu[a] = lo_vertex(g, uc[a]);
   }
+  // every slot's weight and Lambda entries are loaded before the accumulation (no
+  // branch between the loads); slots whose vertex lies outside the coarse mesh carry
+  // weight zero and read nothing
   double acc = 0.0;
+#pragma unroll
   for (int side = 0; side < 2; ++side) {
-    const int* xc = side ? uc : lc;
     const long long x = side ? xu : xl;
-    for (int s = 0; s < g.S; ++s) {
-      const double w = Pw[x * g.S + s];
-      if (w == 0.0) continue;
+    double w[8], dl[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      w[s] = 0.0;
+      dl[s] = 0.0;
+      if (s >= g.S) continue;
       long long vid = 0;
       int ol = 0, ou = 0, mul = 1;
       bool ok = true;
       PER_AXIS(a) {
-        const int va = lo_vertex(g, xc[a]) + ((s >> a) & 1);
+        const int va = (side ? vu[a] : vl[a]) + ((s >> a) & 1);
         if (va < 0 || va >= g.nc[a]) ok = false;
         vid += (long long)va * g.cst[a];
         ol += (Kl[a] - va + 1) * mul;
         ou += (Ku[a] - va + 1) * mul;
         mul *= 3;
       }
-      if (!ok) continue;
-      const double dlam = Lam[vid * S3 + ol] - Lam[vid * S3 + ou];
-      acc = side ? fma(-w, dlam, acc) : fma(w, dlam, acc);
+      if (ok) {
+        w[s] = Pw[x * g.S + s];
+        dl[s] = Lam[vid * S3 + ol] - Lam[vid * S3 + ou];
+      }
     }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc = side ? fma(-w[s], dl[s], acc) : fma(w[s], dl[s], acc);
   }
   return -acc;
 }

@@ -76,6 +76,7 @@ struct DevGeom {
   int n[3], nc[3];
   long long N, Nc;
   long long st[3], cst[3];
+  double geo[3];      // area / distance of a face normal to axis a (unit box)
 };
 
 // Phase ids for the event timers.

@@ -276,6 +276,12 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   }
   g.N = N;
   g.Nc = Nc;
+  for (int a = 0; a < 3; ++a) {
+    double geo = (double)g.n[a];
+    for (int b = 0; b < d; ++b)
+      if (b != a) geo /= (double)g.n[b];
+    g.geo[a] = geo;
+  }
   s->Ns = desc->n_src;
   s->Nr = desc->n_rec;
 
