@@ -28,8 +28,12 @@ def _coords(n):
     return out
 
 
-def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec):
-    """Predicted data (Ns, Nr) for model m (real or complex), dense linear algebra."""
+def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec, source_bases=False):
+    """Predicted data (Ns, Nr) for model m (real or complex), dense linear algebra.
+
+    source_bases: also solve, level by level, the tangential systems with the source
+    as forcing and zero vertex values (Sec. 3.2, source bases) and add that field
+    with coefficient one, the reduced right-hand side becoming R (q - A C)."""
     n = tuple(int(v) for v in n)
     d = len(n)
     N = int(np.prod(n))
@@ -62,7 +66,13 @@ def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec):
     nc = tuple(v // c for v in n)
     Nc = int(np.prod(nc))
     cstride = [int(np.prod(nc[:a])) for a in range(d)]
+    Ns = len(src_pos)
+    Qm = np.zeros((N, Ns))
+    for j in range(Ns):
+        Qm[src_pos[j], j] += src_amp[j]
+        Qm[src_neg[j], j] -= src_amp[j]
     Phi = np.zeros((N, Nc), dtype=dt)
+    Csrc = np.zeros((N, Ns), dtype=dt)
     for x in np.nonzero(level == 0)[0]:
         J = sum(((X[x, a] - half) // c) * cstride[a] for a in range(d))
         Phi[x, J] = 1.0
@@ -85,29 +95,28 @@ def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec):
         known = np.nonzero(level < k)[0]
         rhs = -M[:, known] @ Phi[known]
         Phi[rows] = np.linalg.solve(M[:, rows], rhs)
+        if source_bases:
+            Csrc[rows] = np.linalg.solve(M[:, rows], Qm[rows] - M[:, known] @ Csrc[known])
     # restriction, coarse operator, pinned solve
     R = np.zeros((Nc, N))
     for x in range(N):
         I = sum((X[x, a] // c) * cstride[a] for a in range(d))
         R[I, x] = 1.0
     Ac = R @ A @ Phi
-    Ns = len(src_pos)
     out = np.zeros((Ns, len(rec)), dtype=dt)
     for j in range(Ns):
-        q = np.zeros(N)
-        q[src_pos[j]] += src_amp[j]
-        q[src_neg[j]] -= src_amp[j]
-        b = R @ q
+        b = R @ (Qm[:, j] - A @ Csrc[:, j])
         t = np.zeros(Nc, dtype=dt)
         t[1:] = np.linalg.solve(Ac[1:, 1:], b[1:])
-        u = Phi @ t
+        u = Phi @ t + Csrc[:, j]
         out[j] = u[np.asarray(rec)]
     return out, Phi, Ac
 
 
 def data(m, prob):
     d, _, _ = forward_dense(m, prob.n, prob.coarsen, prob.src_pos, prob.src_neg,
-                            prob.src_amp, prob.rec_cell)
+                            prob.src_amp, prob.rec_cell,
+                            source_bases=bool(getattr(prob, 'source_bases', False)))
     return d
 
 

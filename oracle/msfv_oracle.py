@@ -34,6 +34,16 @@ What is computed, step by step (notation of the paper where it has one):
     boundary values phi_dE themselves depend on m and are differentiated first
     (edges -> faces -> interiors).  J^T w runs the same chain in reverse.
 
+Source bases (Sec. 3.2, the second construction listed there), when the problem asks
+for them: every entity also solves its local problem once per source j with the
+restricted source q_j as forcing and zero data on the coarse vertices; the boundary
+data of a face or interior are the source-basis values of its lower-dimensional
+boundary (edges -> faces -> interiors, as for the vertex bases).  The assembled
+source basis C_j enters with coefficient one: u_j = P t_j + C_j, and the reduced
+system keeps the finite-volume restriction, A_c t_j = R (q_j - A C_j).  Its
+sensitivity adds the chain d C_j (same local operators, no new matrices):
+J = Pr^T ( Y(t) + dC + P dt/dm ),  dt/dm = -A_c^{-1} R ( G(u) + A Y(t) + A dC ).
+
 Readings of the paper where it is silent or garbled are listed in the design
 notes of the repository; the ones that matter here: cell-centred FV with
 harmonic face averages, coarse vertex at fine index c*I + floor(c/2) per axis,
@@ -195,6 +205,7 @@ class Oracle:
         self.Nc = int(np.prod(self.nc))
         self.st = strides_of(self.n)
         self.cst = strides_of(self.nc)
+        self.source_bases = bool(getattr(prob, 'source_bases', False))
         self._build_entities()
         self._build_restriction_and_sources()
 
@@ -327,6 +338,21 @@ class Oracle:
                     out[q, i] = blk[e.g_loc[q], p]
         return out
 
+    def gather_source_boundary(self, e, cvals):
+        """Source-basis values (n_bnd, Ns) on the boundary cells of e (zero on vertices)."""
+        out = np.zeros((len(e.bnd), self.prob.n_src), dtype=cvals[0].dtype)
+        for q in range(len(e.bnd)):
+            out[q] = cvals[e.g_ent[q]][e.g_loc[q]]
+        return out
+
+    def scatter_source_boundary(self, e, seeds, contrib):
+        """Add contrib (n_bnd, Ns) to the source-basis seeds of the boundary entities."""
+        for q in range(len(e.bnd)):
+            f = e.g_ent[q]
+            if self.entities[f].dim == 0:
+                continue
+            seeds[f][e.g_loc[q]] += contrib[q]
+
     def scatter_boundary(self, e, seeds, contrib):
         """Add contrib (n_bnd, n_corners) to the seeds of the boundary entities."""
         for q in range(len(e.bnd)):
@@ -345,11 +371,13 @@ class Oracle:
         st = {}
         T, Dx, Dy = transmissibility(m, self.n)
         st['m'], st['T'], st['Dx'], st['Dy'] = m, T, Dx, Dy
-        vals, lus = [], []
+        Ns = self.prob.n_src
+        vals, lus, cvals = [], [], []
         for e in self.entities:
             if e.dim == 0:
                 vals.append(np.ones((1, 1)))
                 lus.append(None)
+                cvals.append(np.zeros((1, Ns)))
                 continue
             L, B = self.local_matrices(e, T)
             lu = spla.splu(L)
@@ -357,18 +385,34 @@ class Oracle:
             rhs = -(B @ phib)
             vals.append(np.asarray(lu.solve(np.asarray(rhs))).reshape(len(e.cells), len(e.corners)))
             lus.append(lu)
-        st['vals'], st['lus'] = vals, lus
+            if self.source_bases:
+                # L_E c_E = q_E - B_E c_bnd, one column per source
+                cb = self.gather_source_boundary(e, cvals)
+                rhs_c = self.Q[:, e.cells].T - B @ cb
+                cvals.append(np.asarray(lu.solve(np.asarray(rhs_c))).reshape(len(e.cells), Ns))
+            else:
+                cvals.append(np.zeros((len(e.cells), Ns)))
+        st['vals'], st['lus'], st['cvals'] = vals, lus, cvals
         P = self.assemble_P(vals)
         A = fine_operator(T, self.n)
         Ac = (self.R @ A @ P).tocsr()
         lu_c = spla.splu(Ac[1:, 1:].tocsc())
-        b = (self.R @ self.Q.T).T                      # (Ns, Nc): R q_j
-        t = np.zeros((self.prob.n_src, self.Nc))
-        for j in range(self.prob.n_src):
+        C = self.assemble_sources(cvals)               # (Ns, N): source bases C_j
+        b = (self.R @ (self.Q - (A @ C.T).T).T).T      # (Ns, Nc): R (q_j - A C_j)
+        t = np.zeros((Ns, self.Nc))
+        for j in range(Ns):
             t[j, 1:] = lu_c.solve(b[j, 1:])
-        U = (P @ t.T).T                                # (Ns, N): u_j = P t_j
-        st.update(P=P, A=A, Ac=Ac, lu_c=lu_c, t=t, U=U, d=U[:, self.rec].copy())
+        U = (P @ t.T).T + C                            # (Ns, N): u_j = P t_j + C_j
+        st.update(P=P, A=A, Ac=Ac, lu_c=lu_c, t=t, C=C, U=U, d=U[:, self.rec].copy())
         return st
+
+    def assemble_sources(self, cvals):
+        """Source bases as fine fields (Ns, N) from the per-entity values."""
+        C = np.zeros((self.prob.n_src, self.N), dtype=cvals[0].dtype)
+        for e, cv in zip(self.entities, cvals):
+            if e.dim > 0:
+                C[:, e.cells] = cv.T
+        return C
 
     def assemble_P(self, vals):
         rows = np.concatenate([np.repeat(e.cells, len(e.corners)) for e in self.entities])
@@ -401,10 +445,12 @@ class Oracle:
         v = np.asarray(v, dtype=np.float64)
         T = st['T']
         dT = self.dT_of(st, v)
-        dvals = []
-        for e, val, lu in zip(self.entities, st['vals'], st['lus']):
+        Ns = self.prob.n_src
+        dvals, dcvals = [], []
+        for e, val, cval, lu in zip(self.entities, st['vals'], st['cvals'], st['lus']):
             if e.dim == 0:
                 dvals.append(np.zeros((1, 1)))
+                dcvals.append(np.zeros((1, Ns)))
                 continue
             L, B = self.local_matrices(e, T)
             dL, dB = self.local_matrices(e, dT)
@@ -412,14 +458,24 @@ class Oracle:
             dphib = self.gather_boundary(e, dvals)
             rhs = -(dL @ val + dB @ phib + B @ dphib)
             dvals.append(np.asarray(lu.solve(np.asarray(rhs))).reshape(val.shape))
+            if self.source_bases:
+                cb = self.gather_source_boundary(e, st['cvals'])
+                dcb = self.gather_source_boundary(e, dcvals)
+                rhs_c = -(dL @ cval + dB @ cb + B @ dcb)
+                dcvals.append(np.asarray(lu.solve(np.asarray(rhs_c))).reshape(cval.shape))
+            else:
+                dcvals.append(np.zeros(cval.shape))
         dP = self.assemble_P(dvals)
+        dC = self.assemble_sources(dcvals)
         dA = fine_operator(dT, self.n)
         dAc = self.R @ dA @ st['P'] + self.R @ st['A'] @ dP
-        out = np.zeros((self.prob.n_src, len(self.rec)))
-        for j in range(self.prob.n_src):
+        out = np.zeros((Ns, len(self.rec)))
+        for j in range(Ns):
             tj = st['t'][j]
-            dtj = self.coarse_solve(st, -(dAc @ tj))
-            du = dP @ tj + st['P'] @ dtj
+            # d(R (q - A C)) = -R (dA C + A dC)
+            rhs = -(dAc @ tj) - self.R @ (dA @ st['C'][j] + st['A'] @ dC[j])
+            dtj = self.coarse_solve(st, rhs)
+            du = dP @ tj + st['P'] @ dtj + dC[j]
             out[j] = du[self.rec]
         return out
 
@@ -447,26 +503,32 @@ class Oracle:
         t = st['t']
         seeds = [None if e.dim == 0 else Y[:, e.cells].T @ t[:, e.corners]
                  for e in self.entities]
+        # source bases enter with coefficient one: their seeds are y_j itself
+        seeds_c = [None if e.dim == 0 else Y[:, e.cells].T for e in self.entities]
         for eid in range(len(self.entities) - 1, -1, -1):
             e = self.entities[eid]
             if e.dim == 0:
                 continue
             val, lu = st['vals'][eid], st['lus'][eid]
-            mu = np.asarray(lu.solve(np.asarray(seeds[eid]))).reshape(val.shape)
-            phib = self.gather_boundary(e, st['vals'])
-            # -mu^T d(L phi + B phi_b)/dT_f = -(mu_a - mu_b)(phi_a - phi_b)
-            inner = e.f_b >= 0
-            mu_b = np.zeros((len(e.f_a), mu.shape[1]))
-            ph_b = np.zeros((len(e.f_a), mu.shape[1]))
-            mu_b[inner] = mu[e.f_b[inner]]
-            ph_b[inner] = val[e.f_b[inner]]
-            ph_b[~inner] = phib[e.f_q[~inner]]
-            contrib = -np.sum((mu[e.f_a] - mu_b) * (val[e.f_a] - ph_b), axis=1)
-            for k in range(len(e.f_a)):
-                gT[e.f_axis[k]][e.f_idx[k]] += contrib[k]
-            # boundary seeds: -B^T mu
             L, B = self.local_matrices(e, T)
-            self.scatter_boundary(e, seeds, -(B.T @ mu))
+            parts = [(val, self.gather_boundary(e, st['vals']), seeds, self.scatter_boundary)]
+            if self.source_bases:
+                parts.append((st['cvals'][eid], self.gather_source_boundary(e, st['cvals']),
+                              seeds_c, self.scatter_source_boundary))
+            for sol, solb, sd, scatter in parts:
+                mu = np.asarray(lu.solve(np.asarray(sd[eid]))).reshape(sol.shape)
+                # -mu^T d(L x + B x_b)/dT_f = -(mu_a - mu_b)(x_a - x_b)
+                inner = e.f_b >= 0
+                mu_b = np.zeros((len(e.f_a), mu.shape[1]))
+                x_b = np.zeros((len(e.f_a), mu.shape[1]))
+                mu_b[inner] = mu[e.f_b[inner]]
+                x_b[inner] = sol[e.f_b[inner]]
+                x_b[~inner] = solb[e.f_q[~inner]]
+                contrib = -np.sum((mu[e.f_a] - mu_b) * (sol[e.f_a] - x_b), axis=1)
+                for k in range(len(e.f_a)):
+                    gT[e.f_axis[k]][e.f_idx[k]] += contrib[k]
+                # boundary seeds: -B^T mu
+                scatter(e, sd, -(B.T @ mu))
         # chain rule through T(m)
         g = np.zeros(self.N)
         for a in range(self.d):

@@ -40,6 +40,7 @@ class Problem:
     src_amp: np.ndarray      # (Ns,) float64
     rec_cell: np.ndarray     # (Nr,) int64 cells sampled by the receivers
     name: str = ""
+    source_bases: bool = False   # add one source basis function per source (Sec. 3.2)
 
     @property
     def dim(self) -> int:
@@ -136,7 +137,8 @@ def _distinct_cells(rng, n, count, top_layer: bool) -> np.ndarray:
 
 
 def make_problem(n: Sequence[int], coarsen: int, n_src: int, n_rec: int, seed: int,
-                 top_layer: bool | None = None, name: str = "") -> Problem:
+                 top_layer: bool | None = None, name: str = "",
+                 source_bases: bool = False) -> Problem:
     """Dipole sources and point receivers at seeded random distinct cells."""
     n = tuple(int(v) for v in n)
     rng = _rng(seed + 7919)
@@ -147,7 +149,8 @@ def make_problem(n: Sequence[int], coarsen: int, n_src: int, n_rec: int, seed: i
     src_neg = ends[n_src:].copy()
     rec = np.sort(_distinct_cells(rng, n, n_rec, top_layer))
     return Problem(n=n, coarsen=int(coarsen), src_pos=src_pos, src_neg=src_neg,
-                   src_amp=np.ones(n_src), rec_cell=rec, name=name)
+                   src_amp=np.ones(n_src), rec_cell=rec, name=name,
+                   source_bases=bool(source_bases))
 
 
 # ---------------------------------------------------------------------------
