@@ -81,6 +81,15 @@ typedef struct msfv_desc {
                                local problem; only per-thread-group scratch is kept) */
   size_t hbm_budget_bytes;  /* 0 = no limit; else setup fails with MSFV_ERR_OOM when
                                the session workspace would exceed it                   */
+  int source_bases;         /* 0: vertex bases only.  1: add one source basis per source
+                               (Sec. 3.2): on every entity that holds a source end or
+                               whose closure contains one, the local problem forced by
+                               the restricted source q_j with zero vertex data (edges ->
+                               faces -> interiors).  The field C_j enters with
+                               coefficient one: u_j = P t_j + C_j, A_c t_j = R (q_j -
+                               A C_j); every derivative call includes its chain.  Needs
+                               the stored local factors (factor_mode 1, or 0 within the
+                               budget; factor_mode 2 is rejected with MSFV_ERR_ARG)    */
 } msfv_desc_t;
 
 typedef struct msfv_session msfv_session_t;
@@ -250,7 +259,9 @@ int msfv_set_stream(msfv_session_t* s, void* stream);
  * more, the CTAs of the cooperative grid that works on all right-hand sides at once
  * (MSFV_MG_SOLVER=all / cluster at msfv_setup forces either) --, out[11]=1 when the local factors are
  * recomputed (0 stored), out[12]=bit k set when the k-dimensional local problems are
- * factored in global memory.  n_out may be smaller than 13.
+ * factored in global memory, out[13]=number of source-basis slots ((entity, source)
+ * pairs; 0 without source bases), out[14]=their values (doubles per copy of C, mu and
+ * dC).  n_out may be smaller than 15.
  * The environment variable MSFV_LOCAL_WINDOW=global at msfv_setup forces the global-
  * memory factorisation for every class (for testing). */
 int msfv_info(const msfv_session_t* s, int64_t* out, int n_out);

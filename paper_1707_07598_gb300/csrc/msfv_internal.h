@@ -83,7 +83,7 @@ struct DevGeom {
 enum Phase {
   PH_FACE_T = 0, PH_VERTEX, PH_EDGE, PH_FACE, PH_INTERIOR, PH_COARSE_ASM, PH_COARSE_SOLVE,
   PH_PROLONG, PH_ADJ_SETUP, PH_ADJ_INTERIOR, PH_ADJ_FACE, PH_ADJ_EDGE, PH_GRAD, PH_TANGENT,
-  PH_COUNT
+  PH_SOURCE, PH_SOURCE_ADJ, PH_COUNT
 };
 
 }  // namespace msfv
@@ -142,6 +142,67 @@ void launch_zt(const DevGeom& g, const double* t, const double* zc, int Ns, int 
                const int64_t* ru_cell, double* ZT, cudaStream_t s);
 void launch_grad(const DevGeom& g, const double* T, const double* Dl, const double* Pw,
                  const double* Lam, const double* gTloc, double* grad, cudaStream_t s);
+// ---- source bases (Sec. 3.2) ---------------------------------------------------------
+// A "slot" is one (entity, source) pair in the support of that source's basis: the
+// entity holding a source end and every entity whose closure contains it.  The values
+// of the slots (C, the adjoint mu, the tangent dC) are stored back to back, each in
+// its entity's local order.
+struct SrcSlot {
+  int j;                  // source
+  int k;                  // dimension of the entity
+  int ent;                // index of the entity in the EntDesc list of dimension k
+  int pad;
+  long long off;          // offset of the slot's values in the slot storage
+  long long side_off[6];  // per side 2a + dir (dir 0: the low side of axis a, 1: high):
+                          //   across a tangential axis the slot of source j of the
+                          //   lower-dimensional boundary entity, across a vertex axis
+                          //   the slot of the higher-dimensional entity; -1: none
+  int side_ent[6];        // that entity's index in its dimension's EntDesc list, -1: none
+};
+
+struct SrcLaunch {
+  const EntDesc* ents[4];   // EntDesc lists per dimension (index 0 unused)
+  const SrcSlot* slots;     // all slots, grouped by dimension, then entity
+  const int* slot0;         // per support entity of this dimension its first slot (n + 1)
+  int n;                    // support entities of this dimension
+  int nmax;                 // their largest number of cells
+  const int64_t* src_pos;
+  const int64_t* src_neg;
+  const double* src_amp;
+};
+
+// (R A x)_{j,I} as a sparse sum over fine faces that cross a coarse-cell boundary:
+// rows (j, I), entries sign * T_f * x[slot value].
+struct SrcFlux {
+  int nrows = 0;
+  const int* row_j = nullptr;
+  const long long* row_I = nullptr;
+  const int* row_ptr = nullptr;     // nrows + 1
+  const long long* e_val = nullptr; // slot-storage offset of the cell value
+  const long long* e_face = nullptr;// a * N + lower cell of the face
+  const double* e_sign = nullptr;
+};
+
+void launch_src_forward(const DevGeom& g, const SrcLaunch& L, int k, const double* T,
+                        const double* fac, double* C, cudaStream_t s);
+void launch_src_adjoint(const DevGeom& g, const SrcLaunch& L, int k, const double* T,
+                        const double* fac, const double* lam, const double* zc, int Nru,
+                        const int* rec_p, const int* rec_u, const double* C, double* MU,
+                        double* gT, int solve, cudaStream_t s);
+void launch_src_tangent(const DevGeom& g, const SrcLaunch& L, int k, const double* T,
+                        const double* Dl, const double* v, const double* fac, const double* C,
+                        double* dC, cudaStream_t s);
+// rhs[j*Nc + I] -= (R A C)_{j,I}   (tangent: -= (R dA C + R A dC)_{j,I})
+void launch_src_flux(const DevGeom& g, const SrcFlux& F, const double* T, const double* Dl,
+                     const double* v, const double* C, const double* dC, double* rhs,
+                     int tangent, cudaStream_t s);
+// out[i] += vals[map[i]] where map[i] >= 0
+void launch_src_gather_add(const long long* map, long long n, const double* vals, double* out,
+                           cudaStream_t s);
+// u[j*N + x] += C_j(x) over every slot
+void launch_src_field(const DevGeom& g, const SrcLaunch& L, int nslots, const double* C,
+                      double* u, cudaStream_t s);
+
 void launch_coarse_tangent_rhs(const DevGeom& g, const double* dAc, const double* t, int Ns,
                                double* rhs, cudaStream_t s);
 

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -43,7 +44,8 @@ int tuned_variant(int d, int k, int nmax, int bmax, int recompute) {
 const char* kPhaseNames[PH_COUNT] = {
     "face_T",        "vertices",       "basis_edges",  "basis_faces",   "basis_interiors",
     "coarse_assemble", "coarse_solve", "prolong",      "adjoint_setup", "adjoint_interiors",
-    "adjoint_faces", "adjoint_edges",  "gradient",     "tangent"};
+    "adjoint_faces", "adjoint_edges",  "gradient",     "tangent",       "source_bases",
+    "source_adjoint"};
 
 struct Piece {
   bool vertex;
@@ -103,6 +105,17 @@ struct msfv_session {
   int *ru_off = nullptr, *ru_idx = nullptr, *cj_off = nullptr, *cj_u = nullptr, *cj_s = nullptr;
   int *rec_p = nullptr, *rec_u = nullptr;
   int* status = nullptr;
+  // source bases (Sec. 3.2): slots, their values and the maps that use them
+  int src_nslots = 0;
+  long long src_nvals = 0;
+  SrcLaunch src_L[4]{};
+  SrcFlux src_F{};
+  SrcSlot* src_slots = nullptr;
+  int* src_slot0[4] = {nullptr, nullptr, nullptr, nullptr};
+  double *srcC = nullptr, *srcMU = nullptr, *srcdC = nullptr;
+  long long* src_recmap = nullptr;   // Ns*Nr: slot-storage offset of receiver i's cell or -1
+  int64_t *src_pos = nullptr, *src_neg = nullptr;
+  double* src_amp = nullptr;
   BandLU band{};
   MGHost mg{};
   bool use_mg = false;
@@ -243,6 +256,10 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       return fail(nullptr, MSFV_ERR_ARG, "receiver cell out of range");
   if (desc->factor_mode < 0 || desc->factor_mode > 2)
     return fail(nullptr, MSFV_ERR_ARG, "factor_mode must be 0, 1 or 2");
+  if (desc->source_bases != 0 && desc->source_bases != 1)
+    return fail(nullptr, MSFV_ERR_ARG, "source_bases must be 0 or 1");
+  if (desc->source_bases && desc->factor_mode == 2)
+    return fail(nullptr, MSFV_ERR_ARG, "source bases need the stored local factors");
 
   msfv_session* s = new msfv_session();
   s->stream = static_cast<cudaStream_t>(stream);
@@ -476,6 +493,158 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     rq[(size_t)j * Nc + coarse_of(desc->src_pos[j])] += amp;
     rq[(size_t)j * Nc + coarse_of(desc->src_neg[j])] -= amp;
   }
+  // ---- source bases: support, slots, side links, flux rows, receiver map -----------
+  std::vector<SrcSlot> slots;
+  std::vector<int> slot0[4];
+  int src_nmax[4] = {0, 0, 0, 0};
+  long long src_nvals = 0;
+  std::vector<int> fl_j, fl_ptr;
+  std::vector<long long> fl_I, fl_val, fl_face;
+  std::vector<double> fl_sign;
+  std::vector<long long> rec_map;
+  if (desc->source_bases) {
+    auto in_mesh = [&](const int* xc) {
+      for (int a = 0; a < 3; ++a)
+        if (xc[a] < 0 || xc[a] >= G.n[a]) return false;
+      return true;
+    };
+    auto ent_at = [&](const int* xc) -> std::pair<int, int> {
+      const auto it =
+          key2ent.find(std::make_tuple(piece_of[0][xc[0]], piece_of[1][xc[1]], piece_of[2][xc[2]]));
+      return it == key2ent.end() ? std::make_pair(0, -1) : it->second;
+    };
+    auto is_tangential = [](const EntDesc& e, int a) {
+      for (int q = 0; q < e.dim; ++q)
+        if (e.perm[q] == a) return true;
+      return false;
+    };
+    auto cell_coords = [&](long long x, int* xc) {
+      xc[0] = (int)(x % G.n[0]);
+      xc[1] = (int)((x / G.n[0]) % G.n[1]);
+      xc[2] = (int)(x / G.st[2]);
+    };
+    // support of source j: the entity of each off-vertex source end and, recursively,
+    // the higher-dimensional entities across its vertex axes
+    std::map<std::pair<int, int>, std::vector<int>> ent_src;
+    for (int j = 0; j < s->Ns; ++j) {
+      std::set<std::pair<int, int>> sup;
+      const int64_t ends[2] = {desc->src_pos[j], desc->src_neg[j]};
+      for (int64_t x : ends) {
+        int xc[3];
+        cell_coords(x, xc);
+        std::vector<std::pair<int, int>> stack{ent_at(xc)};
+        while (!stack.empty()) {
+          const auto ki = stack.back();
+          stack.pop_back();
+          if (ki.second < 0 || !sup.insert(ki).second) continue;
+          const EntDesc& e = s->h_ents[ki.first][ki.second];
+          for (int a = 0; a < d; ++a) {
+            if (is_tangential(e, a)) continue;
+            for (int dir = 0; dir < 2; ++dir) {
+              int yc[3] = {e.org[0], e.org[1], e.org[2]};
+              yc[a] += dir ? 1 : -1;
+              if (in_mesh(yc)) stack.push_back(ent_at(yc));
+            }
+          }
+        }
+      }
+      for (const auto& ki : sup) ent_src[ki].push_back(j);
+    }
+    std::map<std::tuple<int, int, int>, long long> slot_off;
+    for (int k = 1; k <= d; ++k) {
+      for (const auto& kv : ent_src) {
+        if (kv.first.first != k) continue;
+        const EntDesc& e = s->h_ents[k][kv.first.second];
+        slot0[k].push_back((int)slots.size());
+        src_nmax[k] = std::max(src_nmax[k], e.n);
+        for (int j : kv.second) {
+          SrcSlot S{};
+          S.j = j;
+          S.k = k;
+          S.ent = kv.first.second;
+          S.off = src_nvals;
+          src_nvals += e.n;
+          slot_off[std::make_tuple(k, kv.first.second, j)] = S.off;
+          slots.push_back(S);
+        }
+      }
+      slot0[k].push_back((int)slots.size());
+    }
+    // side links: lower-dimensional boundary entities across tangential axes, higher-
+    // dimensional neighbours across vertex axes
+    for (SrcSlot& S : slots) {
+      const EntDesc& e = s->h_ents[S.k][S.ent];
+      for (int q = 0; q < 6; ++q) {
+        S.side_off[q] = -1;
+        S.side_ent[q] = -1;
+      }
+      for (int a = 0; a < d; ++a) {
+        const bool tan = is_tangential(e, a);
+        for (int dir = 0; dir < 2; ++dir) {
+          int yc[3] = {e.org[0], e.org[1], e.org[2]};
+          yc[a] = dir ? e.org[a] + e.len[a] : e.org[a] - 1;
+          if (!in_mesh(yc)) continue;
+          const auto f = ent_at(yc);
+          if (f.second < 0) continue;                    // a coarse vertex: zero data
+          if (f.first != (tan ? S.k - 1 : S.k + 1)) {
+            delete s;
+            return fail(nullptr, MSFV_ERR_ARG, "internal: inconsistent dual-grid sides");
+          }
+          S.side_ent[2 * a + dir] = f.second;
+          const auto it = slot_off.find(std::make_tuple(f.first, f.second, S.j));
+          if (it != slot_off.end()) S.side_off[2 * a + dir] = it->second;
+        }
+      }
+    }
+    // flux rows (j, I) of R A C: faces that cross a coarse-cell boundary
+    std::map<std::pair<int, long long>, std::vector<std::tuple<long long, long long, double>>> rows;
+    for (const SrcSlot& S : slots) {
+      const EntDesc& e = s->h_ents[S.k][S.ent];
+      int off[3], o = 1;
+      for (int q = 0; q < 3; ++q) {
+        off[q] = o;
+        if (q < e.dim) o *= e.len[e.perm[q]];
+      }
+      for (int p = 0; p < e.n; ++p) {
+        int xc[3] = {e.org[0], e.org[1], e.org[2]};
+        for (int q = 0; q < e.dim; ++q) xc[e.perm[q]] += (p / off[q]) % e.len[e.perm[q]];
+        const long long x = xc[0] + G.st[1] * xc[1] + G.st[2] * xc[2];
+        long long Ix = 0;
+        for (int a = 0; a < 3; ++a) Ix += (long long)(xc[a] / c) * G.cst[a];
+        for (int a = 0; a < d; ++a)
+          for (int dir = 0; dir < 2; ++dir) {
+            int yc[3] = {xc[0], xc[1], xc[2]};
+            yc[a] += dir ? 1 : -1;
+            if (!in_mesh(yc) || yc[a] / c == xc[a] / c) continue;
+            long long Iy = 0;
+            for (int b2 = 0; b2 < 3; ++b2) Iy += (long long)(yc[b2] / c) * G.cst[b2];
+            const long long face = (long long)a * N + (dir ? x : x - G.st[a]);
+            rows[{S.j, Ix}].emplace_back(S.off + p, face, 1.0);
+            rows[{S.j, Iy}].emplace_back(S.off + p, face, -1.0);
+          }
+      }
+    }
+    for (const auto& kv : rows) {
+      fl_j.push_back(kv.first.first);
+      fl_I.push_back(kv.first.second);
+      fl_ptr.push_back((int)fl_val.size());
+      for (const auto& t3 : kv.second) {
+        fl_val.push_back(std::get<0>(t3));
+        fl_face.push_back(std::get<1>(t3));
+        fl_sign.push_back(std::get<2>(t3));
+      }
+    }
+    fl_ptr.push_back((int)fl_val.size());
+    // receivers inside a slot's entity read the source basis there
+    rec_map.assign((size_t)s->Ns * s->Nr, -1);
+    for (const SrcSlot& S : slots)
+      for (const auto& pu : ent_rec[S.k][S.ent])
+        for (int q = ru_off[pu.second]; q < ru_off[pu.second + 1]; ++q)
+          rec_map[(size_t)S.j * s->Nr + ru_idx[q]] = S.off + pu.first;
+  }
+  s->src_nslots = (int)slots.size();
+  s->src_nvals = src_nvals;
+
   // banded LU dimensions of the pinned coarse matrix
   s->band.n = Nc - 1;
   s->band.kl = (int)(G.cst[0] + (d >= 2 ? G.cst[1] : 0) + (d == 3 ? G.cst[2] : 0));
@@ -521,6 +690,17 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     return (size_t)m * sizeof(double);
   };
   size_t scr = scratch_bytes();
+  if (desc->source_bases)
+    need += sizeof(double) * (size_t)(3 * src_nvals) + sizeof(SrcSlot) * slots.size() +
+            sizeof(long long) * (rec_map.size() + 2 * fl_val.size() + fl_I.size()) +
+            sizeof(double) * fl_sign.size() + sizeof(int) * (fl_j.size() + fl_ptr.size() + 16) +
+            (sizeof(int64_t) * 2 + sizeof(double)) * (size_t)s->Ns;
+  if (desc->source_bases && desc->factor_mode == 0 && desc->hbm_budget_bytes &&
+      need + s->fac_bytes + scr > desc->hbm_budget_bytes) {
+    delete s;
+    return fail(nullptr, MSFV_ERR_OOM,
+                "source bases need the stored local factors, which exceed hbm_budget_bytes");
+  }
   if (!s->recompute && desc->factor_mode == 0 && desc->hbm_budget_bytes &&
       need + s->fac_bytes + scr > desc->hbm_budget_bytes) {
     // automatic mode: recompute the local factors in the derivative passes when storing
@@ -631,6 +811,26 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     }
   }
   for (int k = 1; k <= d; ++k) s->d_ents[k] = dalloc<EntDesc>(s, s->h_ents[k].size(), &ce);
+  if (s->src_nslots) {
+    s->src_slots = dalloc<SrcSlot>(s, slots.size(), &ce);
+    for (int k = 1; k <= d; ++k) s->src_slot0[k] = dalloc<int>(s, slot0[k].size(), &ce);
+    s->srcC = dalloc<double>(s, (size_t)src_nvals, &ce);
+    s->srcMU = dalloc<double>(s, (size_t)src_nvals, &ce);
+    s->srcdC = dalloc<double>(s, (size_t)src_nvals, &ce);
+    s->src_recmap = dalloc<long long>(s, rec_map.size(), &ce);
+    s->src_pos = dalloc<int64_t>(s, (size_t)s->Ns, &ce);
+    s->src_neg = dalloc<int64_t>(s, (size_t)s->Ns, &ce);
+    s->src_amp = dalloc<double>(s, (size_t)s->Ns, &ce);
+    if (!fl_j.empty()) {
+      s->src_F.nrows = (int)fl_j.size();
+      s->src_F.row_j = dalloc<int>(s, fl_j.size(), &ce);
+      s->src_F.row_I = dalloc<long long>(s, fl_I.size(), &ce);
+      s->src_F.row_ptr = dalloc<int>(s, fl_ptr.size(), &ce);
+      s->src_F.e_val = dalloc<long long>(s, fl_val.size(), &ce);
+      s->src_F.e_face = dalloc<long long>(s, fl_face.size(), &ce);
+      s->src_F.e_sign = dalloc<double>(s, fl_sign.size(), &ce);
+    }
+  }
   if (ce != cudaSuccess) {
     const bool oom = (ce == cudaErrorMemoryAllocation);
     std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(ce);
@@ -651,6 +851,25 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   if (ce == cudaSuccess) ce = upload(s->rec_u, rec_u, st);
   if (ce == cudaSuccess) ce = upload(s->rq, rq, st);
   for (int k = 1; k <= d && ce == cudaSuccess; ++k) ce = upload(s->d_ents[k], s->h_ents[k], st);
+  if (s->src_nslots && ce == cudaSuccess) {
+    std::vector<int64_t> sp(desc->src_pos, desc->src_pos + s->Ns), sn(desc->src_neg, desc->src_neg + s->Ns);
+    std::vector<double> sa((size_t)s->Ns, 1.0);
+    if (desc->src_amp) sa.assign(desc->src_amp, desc->src_amp + s->Ns);
+    ce = upload(s->src_slots, slots, st);
+    for (int k = 1; k <= d && ce == cudaSuccess; ++k) ce = upload(s->src_slot0[k], slot0[k], st);
+    if (ce == cudaSuccess) ce = upload(s->src_recmap, rec_map, st);
+    if (ce == cudaSuccess) ce = upload(s->src_pos, sp, st);
+    if (ce == cudaSuccess) ce = upload(s->src_neg, sn, st);
+    if (ce == cudaSuccess) ce = upload(s->src_amp, sa, st);
+    if (ce == cudaSuccess && s->src_F.nrows) {
+      ce = upload(const_cast<int*>(s->src_F.row_j), fl_j, st);
+      if (ce == cudaSuccess) ce = upload(const_cast<long long*>(s->src_F.row_I), fl_I, st);
+      if (ce == cudaSuccess) ce = upload(const_cast<int*>(s->src_F.row_ptr), fl_ptr, st);
+      if (ce == cudaSuccess) ce = upload(const_cast<long long*>(s->src_F.e_val), fl_val, st);
+      if (ce == cudaSuccess) ce = upload(const_cast<long long*>(s->src_F.e_face), fl_face, st);
+      if (ce == cudaSuccess) ce = upload(const_cast<double*>(s->src_F.e_sign), fl_sign, st);
+    }
+  }
   if (ce == cudaSuccess) ce = cudaMemsetAsync(s->status, 0, (2 + s->Ns) * sizeof(int), st);
   if (ce == cudaSuccess && s->mg.trace)
     ce = cudaMemsetAsync(s->mg.trace, 0, sizeof(long long) * s->mg.trace_cap, st);
@@ -666,6 +885,17 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     s->launch[k].ents = s->d_ents[k];
     s->launch[k].counter = s->local_ctr + 3 * k;
     s->launch[k].scratch = s->launch[k].scratch_group ? s->local_scratch : nullptr;
+  }
+  for (int k = 0; k <= 3; ++k) {
+    SrcLaunch& SL = s->src_L[k];
+    for (int q = 1; q <= d; ++q) SL.ents[q] = s->d_ents[q];
+    SL.slots = s->src_slots;
+    SL.slot0 = (k >= 1 && k <= d) ? s->src_slot0[k] : nullptr;
+    SL.n = (k >= 1 && k <= d && s->src_nslots) ? (int)slot0[k].size() - 1 : 0;
+    SL.nmax = (k >= 1 && k <= d) ? src_nmax[k] : 0;
+    SL.src_pos = s->src_pos;
+    SL.src_neg = s->src_neg;
+    SL.src_amp = s->src_amp;
   }
   *out = s;
   return MSFV_OK;
@@ -741,6 +971,15 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
     launch_local_forward(g, s->launch[k], s->T, s->Pw, s->fac, s->status, st);
     s->launches += s->launch[k].n_ents ? 1 : 0;
   }
+  if (s->src_nslots) {
+    // source bases C_j on their support (edges, faces, interiors), with the factors the
+    // vertex-basis kernels just stored
+    PhaseScope ps(s, PH_SOURCE);
+    for (int k = 1; k <= d; ++k) {
+      launch_src_forward(g, s->src_L[k], k, s->T, s->fac, s->srcC, st);
+      s->launches += s->src_L[k].n ? 1 : 0;
+    }
+  }
   {
     PhaseScope ps(s, PH_COARSE_ASM);
     launch_coarse_assemble(g, s->T, s->Pw, nullptr, nullptr, nullptr, s->Ac, 0, st);
@@ -749,6 +988,10 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
   {
     PhaseScope ps(s, PH_COARSE_SOLVE);
     cudaMemcpyAsync(s->t, s->rq, sizeof(double) * (size_t)s->Ns * g.Nc, cudaMemcpyDeviceToDevice, st);
+    if (s->src_nslots) {   // R (q_j - A C_j)
+      launch_src_flux(g, s->src_F, s->T, nullptr, nullptr, s->srcC, nullptr, s->t, 0, st);
+      s->launches += s->src_F.nrows ? 1 : 0;
+    }
     coarse_prepare(s);
     coarse_solve(s, s->t, 0);
   }
@@ -756,12 +999,20 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
     PhaseScope ps(s, PH_PROLONG);
     launch_prolong_receivers(g, s->Pw, s->t, s->Ns, s->rec, s->Nr, s->dpred, st);
     s->launches += 1;
+    if (s->src_nslots) {   // u_j = P t_j + C_j at the receivers
+      launch_src_gather_add(s->src_recmap, (long long)s->Ns * s->Nr, s->srcC, s->dpred, st);
+      s->launches += 1;
+    }
     if (d_pred)
       cudaMemcpyAsync(d_pred, s->dpred, sizeof(double) * (size_t)s->Ns * s->Nr,
                       cudaMemcpyDeviceToDevice, st);
     if (u) {
       launch_prolong_full(g, s->Pw, s->t, s->Ns, u, st);
       s->launches += 1;
+      if (s->src_nslots) {
+        launch_src_field(g, s->src_L[0], s->src_nslots, s->srcC, u, st);
+        s->launches += 1;
+      }
     }
   }
   const int rc = check_launch(s, "msfv_forward");
@@ -794,6 +1045,16 @@ int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = 
                          s->X, s->gT, st);
     s->launches += s->launch[k].n_ents ? 1 : 0;
   }
+  if (s->src_nslots) {
+    // source bases: G(C_j)^T lambda_j on their faces and (adaptive basis) the local
+    // adjoint chain interiors -> faces -> edges, added to the face gradient
+    PhaseScope ps(s, PH_SOURCE_ADJ);
+    for (int k = d; k >= 1; --k) {
+      launch_src_adjoint(g, s->src_L[k], k, s->T, s->fac, s->lam, s->zc, s->Nru, s->rec_p,
+                         s->rec_u, s->srcC, s->srcMU, s->gT, fixed_basis ? 0 : 1, st);
+      s->launches += s->src_L[k].n ? 1 : 0;
+    }
+  }
   {
     PhaseScope ps(s, PH_GRAD);
     launch_grad(g, s->T, Dl, s->Pw, s->Lam, s->gT, out, st);
@@ -813,12 +1074,24 @@ int run_jvec(msfv_session* s, const double* v, double* jv) {
     launch_local_tangent(g, s->launch[k], s->T, Dl, v, s->Pw, s->fac, s->X, st);
     s->launches += s->launch[k].n_ents ? 1 : 0;
   }
+  for (int k = 1; k <= d && s->src_nslots; ++k) {
+    launch_src_tangent(g, s->src_L[k], k, s->T, Dl, v, s->fac, s->srcC, s->srcdC, st);
+    s->launches += s->src_L[k].n ? 1 : 0;
+  }
   launch_coarse_assemble(g, s->T, s->Pw, Dl, v, s->X, s->dAc, 1, st);
   launch_coarse_tangent_rhs(g, s->dAc, s->t, s->Ns, s->dt, st);
   s->launches += 2;
+  if (s->src_nslots) {   // - R (dA C_j + A dC_j)
+    launch_src_flux(g, s->src_F, s->T, Dl, v, s->srcC, s->srcdC, s->dt, 1, st);
+    s->launches += s->src_F.nrows ? 1 : 0;
+  }
   coarse_solve(s, s->dt, 0);
   launch_prolong_tangent(g, s->Pw, s->X, s->t, s->dt, s->Ns, s->rec, s->Nr, jv, st);
   s->launches += 1;
+  if (s->src_nslots) {
+    launch_src_gather_add(s->src_recmap, (long long)s->Ns * s->Nr, s->srcdC, jv, st);
+    s->launches += 1;
+  }
   return check_launch(s, "msfv_jvec");
 }
 
@@ -931,12 +1204,12 @@ extern "C" int msfv_info(const msfv_session_t* s, int64_t* out, int n_out) {
   }
   int gw = 0;
   for (int k = 1; k <= s->dg.d; ++k) gw |= s->launch[k].gw ? (1 << k) : 0;
-  int64_t v[13] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
+  int64_t v[15] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
                    (int64_t)(s->h_ents[1].size() + s->h_ents[2].size() + s->h_ents[3].size()),
                    (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, s->use_mg ? 1 : 0, it[0], it[1],
                    s->use_mg ? (s->mg.all ? s->mg.ncta : s->mg.group) : 0,
-                   s->recompute ? 1 : 0, gw};
-  for (int i = 0; i < n_out && i < 13; ++i) out[i] = v[i];
+                   s->recompute ? 1 : 0, gw, s->src_nslots, s->src_nvals};
+  for (int i = 0; i < n_out && i < 15; ++i) out[i] = v[i];
   return MSFV_OK;
 }
 

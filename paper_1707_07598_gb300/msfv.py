@@ -48,7 +48,8 @@ class _Desc(ctypes.Structure):
                 ("src_neg", ctypes.POINTER(ctypes.c_int64)),
                 ("src_amp", ctypes.POINTER(ctypes.c_double)),
                 ("n_rec", ctypes.c_int), ("rec_cell", ctypes.POINTER(ctypes.c_int64)),
-                ("factor_mode", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t)]
+                ("factor_mode", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("source_bases", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -162,6 +163,7 @@ class Session:
         d.rec_cell = self._rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         d.factor_mode = int(factor_mode)
         d.hbm_budget_bytes = int(hbm_budget_bytes)
+        d.source_bases = 1 if getattr(prob, "source_bases", False) else 0
         h = ctypes.c_void_p()
         self._h = None
         rc = L.msfv_setup(ctypes.byref(d), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h))
@@ -272,11 +274,11 @@ class Session:
 
     # -- introspection ----------------------------------------------------------------
     def info(self) -> dict:
-        out = (ctypes.c_int64 * 13)()
-        self._check(self._lib.msfv_info(self._h, out, 13))
+        out = (ctypes.c_int64 * 15)()
+        self._check(self._lib.msfv_info(self._h, out, 15))
         keys = ["N", "Nc", "Ns", "Nr", "n_local_problems", "workspace_bytes", "factor_bytes",
                 "coarse_solver", "coarse_iters", "coarse_iters_T", "coarse_group_ctas",
-                "recompute", "global_window_mask"]
+                "recompute", "global_window_mask", "source_slots", "source_values"]
         return dict(zip(keys, list(out)))
 
     def profile(self, enable: bool = True):

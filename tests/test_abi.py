@@ -52,6 +52,7 @@ def _desc(**kw):
     d.rec_cell = r.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     d.factor_mode = kw.get("fm", 0)
     d.hbm_budget_bytes = kw.get("budget", 0)
+    d.source_bases = kw.get("sb", 0)
     d._keep = (pos, neg, rec, r)
     return d
 
@@ -68,6 +69,9 @@ def _desc(**kw):
     (dict(fm=3), "factor_mode"),
     (dict(dim=3, n=(34, 34, 34), c=17), "too wide"),
     (dict(budget=1000), "hbm_budget"),
+    (dict(sb=2), "source_bases"),
+    (dict(sb=1, fm=2), "stored local factors"),
+    (dict(sb=1, budget=1000), "stored local factors"),
 ])
 def test_setup_rejects_bad_descriptors_on_the_host(lib, kw, frag):
     d = _desc(**kw)
