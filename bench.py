@@ -54,11 +54,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="plain",
-                   choices=["plain", "batched", "served", "diff", "gn"],
+                   choices=["plain", "batched", "served", "diff", "gn", "sources"],
                    help="plain: the one-instance 128^3 step (default); batched: independent "
                         "instances in one CUDA graph vs one at a time; served: the Poisson "
                         "request stream; diff: 256^3, c=16 gradient, J v, J^T w; gn: 5 "
-                        "Gauss-Newton-CG iterations on the 128^3 two-block model")
+                        "Gauss-Newton-CG iterations on the 128^3 two-block model; sources: "
+                        "the 128^3 step with source bases beside the plain one")
     p.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     p.add_argument("--rate", type=float, default=50.0, help="served: requests per second")
     p.add_argument("--duration", type=float, default=10.0,
@@ -579,6 +580,75 @@ def run_gn(args):
     s.close()
     return 0
 
+def run_sources(args):
+    """The default workload (128^3, c = 8, 16 dipoles, 512 receivers) with source bases
+    (Sec. 3.2): one forward + gradient per step, timed like the default line, beside the
+    same steps without source bases on the same inputs."""
+    torch, dev = _gpu_setup()
+    from paper_1707_07598_gb300.msfv import Session
+    n = args.n
+    prob, m_np = W.config_3d_128(n=n)
+    stream = torch.cuda.current_stream(dev)
+    m = torch.from_numpy(m_np).to(dev)
+    m_true = torch.from_numpy(W.config_3d_128(seed=3, n=n)[1]).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for sb in (False, True):
+        prob.source_bases = sb
+        sess = Session(prob, stream=stream)
+        d_true = sess.forward(m_true).clone()
+        noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, 4)).to(dev)
+        d_obs = d_true + 0.01 * d_true.abs() * noise
+        grad = torch.empty(prob.N, dtype=torch.float64, device=dev)
+        d_pred = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            sess.forward(m, d_pred)
+            sess.adjoint(d_obs, grad, want_phi=False)
+        torch.cuda.synchronize(dev)
+        sess.profile(True)
+        sess.phase_times(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        l0 = sess.launch_count()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            sess.forward(m, d_pred)
+            sess.adjoint(d_obs, grad, want_phi=False)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        launches = sess.launch_count() - l0
+        clk = clocks.stop()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        ph = sess.phase_times(reset=True)
+        info = sess.info()
+        res[sb] = {"ms": sum(ms) / len(ms), "p50": float(np.percentile(ms, 50)),
+                   "p99": float(np.percentile(ms, 99)), "launches": launches, "clocks": clk,
+                   "phases": {k: v[0] / args.steps for k, v in ph.items() if v[1]},
+                   "slots": info["source_slots"], "values": info["source_values"],
+                   "iters": (info["coarse_iters"], info["coarse_iters_T"])}
+        sess.close()
+    r1, r0 = res[True], res[False]
+    out = {"metric": METRIC, "value": 1000.0 / r1["ms"], "unit": "solves/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r1["ms"],
+           "p50_ms": r1["p50"], "p99_ms": r1["p99"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"3d_{n}^3_c8_16dipoles_512rec_fwd+grad_source_bases",
+                      "source_bases": True, "l2": "flushed before every timed step (512 MiB write)",
+                      "factor_mode": "store"},
+           "gpu_launches": r1["launches"], "clocks": r1["clocks"],
+           "source_slots": r1["slots"], "source_values": r1["values"],
+           "plain": {"value": 1000.0 / r0["ms"], "ms_per_step": r0["ms"]},
+           "overhead": r1["ms"] / r0["ms"] - 1.0,
+           "phases_ms_per_step": r1["phases"],
+           "coarse_iters": {"source_bases": r1["iters"], "plain": r0["iters"]}}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -591,6 +661,8 @@ def main():
         return run_diff(args)
     if args.workload == "gn":
         return run_gn(args)
+    if args.workload == "sources":
+        return run_sources(args)
     return run_ours(args)
 
 
