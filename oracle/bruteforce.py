@@ -136,3 +136,87 @@ def misfit_gradient_complex_step(m, prob, d_obs, eps=1e-30):
         e[k] = 1.0
         g[k] = np.sum(r * jvec_complex_step(m, prob, e, eps))
     return g
+
+
+# ---------------------------------------------------------------------------
+# Nodal Galerkin variant (Sec. 3.1-3.2 with Lagrange boundary data on primal blocks)
+# ---------------------------------------------------------------------------
+
+def forward_dense_nodal(m, n, c, src_pos, src_neg, src_amp, rec):
+    """Predicted data (Ns, Nr) of the nodal Galerkin multiscale model, dense, written
+    cell by cell: A = sum_c sigma_c K_c where K_c couples the two ends of each of the
+    cell's 2^(d-1) d edges with weight (area / length) / 2^(d-1).  All block-interior
+    nodes are solved in one dense system at once; the other nodes carry multilinear
+    hats.  Complex m flows through (complex-step derivatives)."""
+    n = tuple(int(v) for v in n)
+    d = len(n)
+    nn = tuple(v + 1 for v in n)
+    Nn = int(np.prod(nn))
+    sn = [int(np.prod(nn[:a])) for a in range(d)]
+    Xc = _coords(n)
+    sig = np.exp(m)
+    dt = np.result_type(sig.dtype, np.float64)
+    A = np.zeros((Nn, Nn), dtype=dt)
+    h = [1.0 / v for v in n]
+    for cell in range(len(sig)):
+        base = sum(Xc[cell, a] * sn[a] for a in range(d))
+        for a in range(d):
+            geo = np.prod([h[b] for b in range(d) if b != a]) / h[a] / 2 ** (d - 1)
+            others = [b for b in range(d) if b != a]
+            for offs in np.ndindex(*([2] * len(others))):
+                lo = base + sum(o * sn[b] for b, o in zip(others, offs))
+                hi = lo + sn[a]
+                wgt = geo * sig[cell]
+                A[lo, lo] += wgt
+                A[hi, hi] += wgt
+                A[lo, hi] -= wgt
+                A[hi, lo] -= wgt
+    Xn = _coords(nn)
+    ncn = tuple(v // c + 1 for v in n)
+    Ncn = int(np.prod(ncn))
+    scn = [int(np.prod(ncn[:a])) for a in range(d)]
+    # hats everywhere, then the interior nodes of all blocks replaced by one solve
+    S = np.ones((Nn, Ncn), dtype=dt)
+    for J in range(Ncn):
+        Jc = [(J // scn[a]) % ncn[a] for a in range(d)]
+        for a in range(d):
+            S[:, J] *= np.maximum(0.0, 1.0 - np.abs(Xn[:, a] - c * Jc[a]) / c)
+    inner = np.all(Xn % c != 0, axis=1) if c > 1 else np.zeros(Nn, dtype=bool)
+    if inner.any():
+        I = np.nonzero(inner)[0]
+        O = np.nonzero(~inner)[0]
+        S[I] = np.linalg.solve(A[np.ix_(I, I)], -A[np.ix_(I, O)] @ S[O])
+    Ak = S.T @ A @ S
+    Ns = len(src_pos)
+    out = np.zeros((Ns, len(rec)), dtype=dt)
+    for j in range(Ns):
+        q = np.zeros(Nn)
+        q[src_pos[j]] += src_amp[j]
+        q[src_neg[j]] -= src_amp[j]
+        b = S.T @ q
+        t = np.zeros(Ncn, dtype=dt)
+        t[1:] = np.linalg.solve(Ak[1:, 1:], b[1:])
+        out[j] = (S @ t)[np.asarray(rec)]
+    return out, S, Ak, A
+
+
+def data_nodal(m, prob):
+    d, _, _, _ = forward_dense_nodal(m, prob.n, prob.coarsen, prob.src_pos, prob.src_neg,
+                                     prob.src_amp, prob.rec_cell)
+    return d
+
+
+def jvec_complex_step_nodal(m, prob, v, eps=1e-30):
+    mc = np.asarray(m, dtype=np.complex128) + 1j * eps * np.asarray(v)
+    return np.imag(data_nodal(mc, prob)) / eps
+
+
+def misfit_gradient_complex_step_nodal(m, prob, d_obs, eps=1e-30):
+    N = len(m)
+    r = np.real(data_nodal(np.asarray(m, dtype=np.complex128), prob)) - d_obs
+    g = np.zeros(N)
+    for k in range(N):
+        e = np.zeros(N)
+        e[k] = 1.0
+        g[k] = np.sum(r * jvec_complex_step_nodal(m, prob, e, eps))
+    return g

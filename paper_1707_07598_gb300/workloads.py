@@ -41,6 +41,8 @@ class Problem:
     rec_cell: np.ndarray     # (Nr,) int64 cells sampled by the receivers
     name: str = ""
     source_bases: bool = False   # add one source basis function per source (Sec. 3.2)
+    nodal: bool = False          # nodal Galerkin variant: sources / receivers index the
+                                 # (n+1)^d nodes, m the n^d cells
 
     @property
     def dim(self) -> int:
@@ -138,19 +140,21 @@ def _distinct_cells(rng, n, count, top_layer: bool) -> np.ndarray:
 
 def make_problem(n: Sequence[int], coarsen: int, n_src: int, n_rec: int, seed: int,
                  top_layer: bool | None = None, name: str = "",
-                 source_bases: bool = False) -> Problem:
-    """Dipole sources and point receivers at seeded random distinct cells."""
+                 source_bases: bool = False, nodal: bool = False) -> Problem:
+    """Dipole sources and point receivers at seeded random distinct cells (nodes of the
+    (n+1)^d node lattice when nodal)."""
     n = tuple(int(v) for v in n)
     rng = _rng(seed + 7919)
     if top_layer is None:
         top_layer = len(n) == 3
-    ends = _distinct_cells(rng, n, 2 * n_src, top_layer)
+    lat = tuple(v + 1 for v in n) if nodal else n
+    ends = _distinct_cells(rng, lat, 2 * n_src, top_layer)
     src_pos = ends[:n_src].copy()
     src_neg = ends[n_src:].copy()
-    rec = np.sort(_distinct_cells(rng, n, n_rec, top_layer))
+    rec = np.sort(_distinct_cells(rng, lat, n_rec, top_layer))
     return Problem(n=n, coarsen=int(coarsen), src_pos=src_pos, src_neg=src_neg,
                    src_amp=np.ones(n_src), rec_cell=rec, name=name,
-                   source_bases=bool(source_bases))
+                   source_bases=bool(source_bases), nodal=bool(nodal))
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,163 @@
+"""Pins of the nodal Galerkin oracle (the paper's own variant: nodal operator, Lagrange
+boundary data on primal blocks, A_k = S^T A S, sensitivities with the X_k term).
+
+* the dense brute force (cell-by-cell assembly, all block interiors in one system):
+  operator, basis and data; J v and the misfit gradient by complex step; dot product;
+* the X_k term: leaving it out breaks J v whenever a source sits inside a block;
+* constant sigma: the basis is exactly the multilinear (Lagrange) interpolation;
+* Galerkin properties: S^T (q - A U) = 0 off the pinned row, A_k symmetric, and U has
+  the smallest energy error against the fine solve over the span of S;
+* c = 1: S = I and the model is the fine nodal solve;
+* identity receivers (Sec. 4.4): the adaptive Jacobian matches complex step, the
+  fixed-basis one does not.
+CPU only."""
+import numpy as np
+import pytest
+
+from oracle import bruteforce as BF
+from oracle.galerkin_oracle import NodalOracle
+from paper_1707_07598_gb300 import workloads as W
+
+TINY = [((8, 8), 2, 2, 5), ((8, 8), 4, 2, 6), ((6, 9), 3, 2, 5), ((12, 8), 4, 3, 7),
+        ((4, 4, 4), 2, 2, 5), ((8, 4, 4), 4, 2, 6), ((6, 6, 6), 3, 2, 5), ((6, 6), 1, 2, 4)]
+
+
+def _tiny(n, c, ns, nr, seed=3):
+    prob = W.make_problem(n, c, ns, nr, seed=seed, top_layer=False, nodal=True)
+    m = W.gaussian_random_field(n, 0.3, seed + 2)
+    return prob, m
+
+
+def _node(nn, *xs):
+    s, o = 1, 0
+    for a, x in enumerate(xs):
+        o += x * s
+        s *= nn[a]
+    return o
+
+
+@pytest.mark.parametrize("n,c,ns,nr", TINY)
+def test_forward_matches_dense_brute_force(n, c, ns, nr):
+    prob, m = _tiny(n, c, ns, nr)
+    st = NodalOracle(prob).forward(m)
+    d_bf, S, Ak, A = BF.forward_dense_nodal(m, n, c, prob.src_pos, prob.src_neg, prob.src_amp,
+                                            prob.rec_cell)
+    assert np.abs(st['A'].toarray() - A).max() <= 1e-13 * np.abs(A).max()
+    assert np.abs(st['S'].toarray() - S).max() <= 1e-12
+    assert np.abs(st['Ak'].toarray() - Ak).max() <= 1e-12 * np.abs(Ak).max()
+    assert np.linalg.norm(st['d'] - d_bf) <= 1e-12 * np.linalg.norm(d_bf)
+
+
+@pytest.mark.parametrize("n,c,ns,nr", TINY)
+def test_jvec_matches_complex_step_and_dot_product(n, c, ns, nr):
+    prob, m = _tiny(n, c, ns, nr)
+    o = NodalOracle(prob)
+    st = o.forward(m)
+    v = W.noise_like(prob.N, 1.0, 17)
+    jv = o.jvec(st, v)
+    ref = BF.jvec_complex_step_nodal(m, prob, v)
+    assert np.linalg.norm(jv - ref) <= 1e-11 * np.linalg.norm(ref)
+    w = W.noise_like((prob.n_src, prob.n_rec), 1.0, 19)
+    lhs, rhs = np.sum(w * jv), o.jtvec(st, w) @ v
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + np.linalg.norm(w) * np.linalg.norm(v) * 1e-3)
+
+
+@pytest.mark.parametrize("n,c,ns,nr", [((8, 8), 4, 2, 6), ((6, 6), 3, 2, 5), ((4, 4, 4), 2, 2, 4)])
+def test_gradient_matches_complex_step(n, c, ns, nr):
+    prob, m = _tiny(n, c, ns, nr, seed=5)
+    o = NodalOracle(prob)
+    st = o.forward(m)
+    d_obs = st['d'] + W.noise_like(st['d'].shape, 0.05 * np.abs(st['d']).max(), 6)
+    _, g = o.misfit_gradient(st, d_obs)
+    g_ref = BF.misfit_gradient_complex_step_nodal(m, prob, d_obs)
+    assert np.linalg.norm(g - g_ref) <= 1e-11 * np.linalg.norm(g_ref)
+
+
+def test_the_x_term_is_needed_when_a_source_is_inside_a_block():
+    n, c = (12, 12), 4
+    nn = (13, 13)
+    prob = W.Problem(n=n, coarsen=c, src_pos=np.array([_node(nn, 5, 6)]),   # block interior
+                     src_neg=np.array([_node(nn, 8, 3)]), src_amp=np.array([1.0]),
+                     rec_cell=np.arange(0, 169, 4, dtype=np.int64), nodal=True)
+    m = W.gaussian_random_field(n, 0.3, 9)
+    o = NodalOracle(prob)
+    st = o.forward(m)
+    v = W.noise_like(prob.N, 1.0, 10)
+    ref = BF.jvec_complex_step_nodal(m, prob, v)
+    assert np.linalg.norm(o.jvec(st, v) - ref) <= 1e-11 * np.linalg.norm(ref)
+    assert np.linalg.norm(o.jvec(st, v, with_x=False) - ref) > 1e-3 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("n,c", [((12, 8), 4), ((6, 6, 9), 3)])
+def test_constant_sigma_gives_the_lagrange_interpolation(n, c):
+    prob = W.make_problem(n, c, 1, 3, seed=1, top_layer=False, nodal=True)
+    o = NodalOracle(prob)
+    st = o.forward(np.full(prob.N, 0.4))
+    assert np.abs(st['S'].toarray() - o.Hat.toarray()).max() <= 1e-13
+
+
+@pytest.mark.parametrize("n,c,ns,nr", [((16, 16), 4, 3, 10), ((8, 8, 8), 4, 2, 9)])
+def test_galerkin_orthogonality_symmetry_and_energy_optimality(n, c, ns, nr):
+    prob, m = _tiny(n, c, ns, nr, seed=11)
+    o = NodalOracle(prob)
+    st = o.forward(m)
+    A, S, Ak = st['A'], st['S'], st['Ak']
+    assert abs(Ak - Ak.T).max() <= 1e-14 * abs(Ak).max()
+    for j in range(ns):
+        res = S.T @ (o.Q[j] - A @ st['U'][j])
+        assert np.abs(res[1:]).max() <= 1e-12 * np.abs(S.T @ o.Q[j]).max()
+    # energy error against the fine solve (same pinned node 0) is smallest at t
+    fine = W.Problem(n=n, coarsen=1, src_pos=prob.src_pos, src_neg=prob.src_neg,
+                     src_amp=prob.src_amp, rec_cell=prob.rec_cell, nodal=True)
+    Uf = NodalOracle(fine).forward(m)['U']
+    rng = np.random.default_rng(0)
+    for j in range(ns):
+        e0 = Uf[j] - st['U'][j]
+        E0 = e0 @ (A @ e0)
+        for _ in range(5):
+            dt = rng.normal(size=o.Ncn)
+            dt[0] = 0.0
+            e1 = e0 - S @ (1e-3 * dt * np.abs(st['t'][j]).max())
+            assert e1 @ (A @ e1) >= E0 * (1 - 1e-12)
+
+
+def test_coarsening_one_is_the_fine_nodal_solve():
+    n = (6, 5)
+    prob = W.make_problem(n, 1, 2, 6, seed=13, top_layer=False, nodal=True)
+    m = W.gaussian_random_field(n, 0.3, 14)
+    st = NodalOracle(prob).forward(m)
+    assert np.array_equal(st['S'].toarray(), np.eye(42))
+    _, _, _, A = BF.forward_dense_nodal(m, n, 1, prob.src_pos, prob.src_neg, prob.src_amp,
+                                        prob.rec_cell)
+    for j in range(2):
+        q = np.zeros(42)
+        q[prob.src_pos[j]] += 1.0
+        q[prob.src_neg[j]] -= 1.0
+        u = np.zeros(42)
+        u[1:] = np.linalg.solve(A[1:, 1:], q[1:])
+        assert np.abs(st['U'][j] - u).max() <= 1e-12 * np.abs(u).max()
+
+
+def test_identity_receivers_adaptive_matches_fixed_does_not():
+    """Sec. 4.4: one dipole, every node a receiver, a conductive block; along a smooth
+    non-constant direction the adaptive Jacobian equals complex step while the
+    fixed-basis one misses by far more than rounding."""
+    n, c = (12, 12, 6), 3
+    nn = tuple(v + 1 for v in n)
+    Nn = int(np.prod(nn))
+    prob = W.Problem(n=n, coarsen=c, src_pos=np.array([_node(nn, 2, 6, 6)]),
+                     src_neg=np.array([_node(nn, 10, 6, 6)]), src_amp=np.array([1.0]),
+                     rec_cell=np.arange(Nn, dtype=np.int64), nodal=True)
+    X = np.stack(np.unravel_index(np.arange(prob.N), n[::-1])[::-1], axis=1)
+    box = np.all((X >= [4, 4, 2]) & (X < [8, 8, 4]), axis=1)
+    m = np.where(box, np.log(0.1), np.log(0.01))
+    o = NodalOracle(prob)
+    st = o.forward(m)
+    v = np.sin(np.pi * X[:, 0] / n[0]) * np.cos(np.pi * X[:, 1] / n[1])
+    w = W.noise_like((1, Nn), 1.0, 3)
+    ref = BF.jvec_complex_step_nodal(m, prob, v)
+    g_ad = o.jtvec(st, w)
+    g_fx = o.jtvec_fixed_basis(st, w)
+    fd = np.sum(w * ref)
+    assert abs(g_ad @ v - fd) <= 1e-10 * abs(fd)
+    assert abs(g_fx @ v - fd) > 1e-4 * abs(fd)
