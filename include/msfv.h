@@ -90,6 +90,19 @@ typedef struct msfv_desc {
                                A C_j); every derivative call includes its chain.  Needs
                                the stored local factors (factor_mode 1, or 0 within the
                                budget; factor_mode 2 is rejected with MSFV_ERR_ARG)    */
+  int discretization;       /* 0: cell-centred finite volumes with the MSFV dual-grid
+                               basis and R A P (the path above).  1: the paper's own
+                               variant: nodal operator A = G^T diag(w) G on the
+                               (n+1)^d nodes, w_e = (area/length) 2^(1-d) * sum of
+                               sigma over the cells sharing edge e; Lagrange (multi-
+                               linear) data on the faces of the primal blocks of c^d
+                               cells, local solves inside them; A_k = S^T A S, b_j =
+                               S^T q_j, coarse node 0 (the origin) pinned; derivatives
+                               with the X_k term (Sec. 4.3).  m and the gradient stay
+                               on the n^d cells; src_pos / src_neg / rec_cell and u_dev
+                               index the nodes (x fastest).  Needs stored factors
+                               (factor_mode 2 and source_bases are rejected);
+                               msfv_gn_step is not available                           */
 } msfv_desc_t;
 
 typedef struct msfv_session msfv_session_t;
@@ -234,7 +247,8 @@ const char* msfv_batch_last_error(const msfv_batch_t* b);
  * be NULL) receives the chosen shape per class index 1..dim; ms_out (host, 16 doubles,
  * may be NULL) the best time of shape v for class k at 4*(k-1)+v (-1: not run).
  * Synchronises the stream; the session must run msfv_forward again before derivative
- * calls.  MSFV_LOCAL_VARIANT=0..3 at msfv_setup forces a shape for every class. */
+ * calls.  MSFV_LOCAL_VARIANT=0..3 at msfv_setup forces a shape for every class.  Not
+ * available for the nodal variant (MSFV_ERR_ARG). */
 int msfv_autotune(msfv_session_t* s, const double* m_dev, int* variants_out, double* ms_out);
 
 /* Free the session and its device workspace (synchronises its stream). NULL is ok. */

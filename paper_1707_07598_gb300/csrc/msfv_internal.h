@@ -79,6 +79,30 @@ struct DevGeom {
   double geo[3];      // area / distance of a face normal to axis a (unit box)
 };
 
+// Cells and primal blocks of the nodal Galerkin variant (the DevGeom of a nodal session
+// describes the (n+1)^d node lattice, coarse vertices at multiples of c).
+struct NodalGeom {
+  int n[3];             // cells per axis (1 on unused axes)
+  long long cst[3];     // cell strides
+  long long Ncell;
+  int nb[3];            // primal blocks per axis
+  long long nblocks;
+  double geo[3];        // area / length of an edge along axis a (unit box)
+};
+
+void launch_nodal_weights(const DevGeom& g, const NodalGeom& ng, const double* m, const double* v,
+                          double* sig, double* w, cudaStream_t s);
+void launch_nodal_hats(const DevGeom& g, double* Pw, cudaStream_t s);
+void launch_nodal_rhs(const DevGeom& g, const double* Pw, const int64_t* pos, const int64_t* neg,
+                      const double* amp, int Ns, double* b, cudaStream_t s);
+void launch_galerkin(const DevGeom& g, const NodalGeom& ng, const double* sig, const double* v,
+                     const double* Pw, const double* dPw, double* M, double* Ak, cudaStream_t s);
+void launch_nodal_zt(const DevGeom& g, const double* t, const double* mu, const double* zc,
+                     const double* qpt, int Ns, int Nru, const int64_t* ru_cell, double* ZT,
+                     cudaStream_t s);
+void launch_nodal_grad(const DevGeom& g, const NodalGeom& ng, const double* U, const double* Lf,
+                       int Ns, const double* sig, double* gT, double* grad, cudaStream_t s);
+
 // Phase ids for the event timers.
 enum Phase {
   PH_FACE_T = 0, PH_VERTEX, PH_EDGE, PH_FACE, PH_INTERIOR, PH_COARSE_ASM, PH_COARSE_SOLVE,

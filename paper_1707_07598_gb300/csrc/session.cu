@@ -54,10 +54,10 @@ struct Piece {
   int start, len;
 };
 
-// Vertex coordinates c*K + c/2 and the open intervals between them (per axis).
-std::vector<Piece> axis_pieces(int n, int c) {
+// Vertex coordinates c*K + half and the open intervals between them (per axis): half =
+// c/2 for the cell-centred dual grid, 0 for the nodal variant's primal blocks.
+std::vector<Piece> axis_pieces(int n, int c, int half, int nc) {
   std::vector<Piece> out;
-  const int half = c / 2, nc = n / c;
   if (half > 0) out.push_back({false, -1, -1, 0, 0, half});
   for (int K = 0; K < nc; ++K) {
     const int pos = c * K + half;
@@ -105,6 +105,12 @@ struct msfv_session {
   int *ru_off = nullptr, *ru_idx = nullptr, *cj_off = nullptr, *cj_u = nullptr, *cj_s = nullptr;
   int *rec_p = nullptr, *rec_u = nullptr;
   int* status = nullptr;
+  // nodal Galerkin variant
+  bool nodal = false;
+  NodalGeom ng{};
+  long long Nm = 0;                  // model size (cells)
+  double *blockM = nullptr, *Ufine = nullptr, *Lfine = nullptr, *ones = nullptr,
+         *qpt = nullptr;
   // source bases (Sec. 3.2): slots, their values and the maps that use them
   int src_nslots = 0;
   long long src_nvals = 0;
@@ -246,6 +252,23 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     return fail(nullptr, MSFV_ERR_ARG, "need n_src >= 1 and source arrays");
   if (desc->n_rec < 1 || !desc->rec_cell)
     return fail(nullptr, MSFV_ERR_ARG, "need n_rec >= 1 and a receiver array");
+  if (desc->discretization != 0 && desc->discretization != 1)
+    return fail(nullptr, MSFV_ERR_ARG, "discretization must be 0 or 1");
+  const bool nodal = desc->discretization == 1;
+  const long long Ncell = N;
+  if (nodal) {   // fields on the (n+1)^d nodes, coarse nodes at multiples of c
+    N = 1;
+    Nc = 1;
+    for (int a = 0; a < d; ++a) {
+      N *= desc->n[a] + 1;
+      Nc *= desc->n[a] / c + 1;
+    }
+    if (N >= (1LL << 31)) return fail(nullptr, MSFV_ERR_ARG, "mesh too large (N must be < 2^31)");
+    if (desc->source_bases)
+      return fail(nullptr, MSFV_ERR_ARG, "source bases are not available for the nodal variant");
+    if (desc->factor_mode == 2)
+      return fail(nullptr, MSFV_ERR_ARG, "the nodal variant needs the stored local factors");
+  }
   for (int j = 0; j < desc->n_src; ++j) {
     const int64_t p = desc->src_pos[j], q = desc->src_neg[j];
     if (p < 0 || p >= N || q < 0 || q >= N || p == q)
@@ -266,11 +289,30 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   Geom& G = s->geo;
   G.d = d;
   G.c = c;
-  G.half = c / 2;
+  G.half = nodal ? 0 : c / 2;
   G.S = 1 << d;
   for (int a = 0; a < 3; ++a) {
-    G.n[a] = (a < d) ? desc->n[a] : 1;
-    G.nc[a] = (a < d) ? desc->n[a] / c : 1;
+    G.n[a] = (a < d) ? desc->n[a] + (nodal ? 1 : 0) : 1;
+    G.nc[a] = (a < d) ? desc->n[a] / c + (nodal ? 1 : 0) : 1;
+  }
+  s->nodal = nodal;
+  s->Nm = Ncell;
+  {
+    NodalGeom& ng = s->ng;
+    ng.Ncell = Ncell;
+    ng.nblocks = 1;
+    long long cs = 1;
+    for (int a = 0; a < 3; ++a) {
+      ng.n[a] = (a < d) ? desc->n[a] : 1;
+      ng.cst[a] = cs;
+      cs *= ng.n[a];
+      ng.nb[a] = (a < d) ? desc->n[a] / c : 1;
+      ng.nblocks *= ng.nb[a];
+      double geo = (a < d) ? (double)desc->n[a] : 0.0;
+      for (int b = 0; b < d; ++b)
+        if (b != a) geo /= (double)desc->n[b];
+      ng.geo[a] = geo;
+    }
   }
   G.N = N;
   G.Nc = Nc;
@@ -306,7 +348,8 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   std::vector<Piece> pieces[3];
   std::vector<int> piece_of[3];
   for (int a = 0; a < 3; ++a) {
-    pieces[a] = (a < d) ? axis_pieces(G.n[a], c) : std::vector<Piece>{{true, 0, 0, 0, 0, 1}};
+    pieces[a] = (a < d) ? axis_pieces(G.n[a], c, G.half, G.nc[a])
+                        : std::vector<Piece>{{true, 0, 0, 0, 0, 1}};
     piece_of[a].assign(G.n[a], -1);
     for (int q = 0; q < (int)pieces[a].size(); ++q)
       for (int x = pieces[a][q].start; x < pieces[a][q].start + pieces[a][q].len; ++x)
@@ -361,6 +404,11 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   const int force_gw = (win_env && !strcmp(win_env, "global")) ? 1 : 0;
   for (int k = 1; k <= d; ++k) {
     auto& v = s->h_ents[k];
+    if (nodal && k < d) {   // block faces and edges carry Lagrange data: no local problem
+      v.clear();
+      s->launch[k] = LocalLaunch{};
+      continue;
+    }
     std::stable_sort(v.begin(), v.end(), [](const EntDesc& x, const EntDesc& y) {
       const double cx = (double)x.n * x.b * x.b + 32.0 * x.n * x.b;
       const double cy = (double)y.n * y.b * y.b + 32.0 * y.n * y.b;
@@ -408,6 +456,11 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   // ---- receivers ------------------------------------------------------------------
   std::vector<int64_t> rec(desc->rec_cell, desc->rec_cell + desc->n_rec);
   std::vector<int64_t> ru(rec);
+  if (nodal)   // adjoint seed points: receivers and source nodes (the X_k term)
+    for (int j = 0; j < desc->n_src; ++j) {
+      ru.push_back(desc->src_pos[j]);
+      ru.push_back(desc->src_neg[j]);
+    }
   std::sort(ru.begin(), ru.end());
   ru.erase(std::unique(ru.begin(), ru.end()), ru.end());
   s->Nru = (int)ru.size();
@@ -476,6 +529,18 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     }
   }
   cj_off[Nc] = (int)cj_u.size();
+  // nodal variant: source values at the seed points (the X_k term's seeds)
+  std::vector<double> qpt;
+  if (nodal) {
+    qpt.assign((size_t)s->Ns * ru.size(), 0.0);
+    for (int j = 0; j < s->Ns; ++j) {
+      const double amp = desc->src_amp ? desc->src_amp[j] : 1.0;
+      const size_t up = std::lower_bound(ru.begin(), ru.end(), desc->src_pos[j]) - ru.begin();
+      const size_t un = std::lower_bound(ru.begin(), ru.end(), desc->src_neg[j]) - ru.begin();
+      qpt[(size_t)j * ru.size() + up] += amp;
+      qpt[(size_t)j * ru.size() + un] -= amp;
+    }
+  }
   // coarse right-hand sides R q_j
   std::vector<double> rq((size_t)s->Ns * Nc, 0.0);
   auto coarse_of = [&](long long x) {
@@ -695,6 +760,16 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
             sizeof(long long) * (rec_map.size() + 2 * fl_val.size() + fl_I.size()) +
             sizeof(double) * fl_sign.size() + sizeof(int) * (fl_j.size() + fl_ptr.size() + 16) +
             (sizeof(int64_t) * 2 + sizeof(double)) * (size_t)s->Ns;
+  if (nodal)
+    need += sizeof(double) * ((size_t)s->ng.nblocks * Ssz * Ssz + 2 * (size_t)s->Ns * N + N +
+                              qpt.size()) +
+            (sizeof(int64_t) * 2 + sizeof(double)) * (size_t)s->Ns;
+  if (nodal && desc->factor_mode == 0 && desc->hbm_budget_bytes &&
+      need + s->fac_bytes + scr > desc->hbm_budget_bytes) {
+    delete s;
+    return fail(nullptr, MSFV_ERR_OOM,
+                "the nodal variant needs the stored local factors, which exceed hbm_budget_bytes");
+  }
   if (desc->source_bases && desc->factor_mode == 0 && desc->hbm_budget_bytes &&
       need + s->fac_bytes + scr > desc->hbm_budget_bytes) {
     delete s;
@@ -811,6 +886,18 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     }
   }
   for (int k = 1; k <= d; ++k) s->d_ents[k] = dalloc<EntDesc>(s, s->h_ents[k].size(), &ce);
+  if (nodal) {
+    s->blockM = dalloc<double>(s, (size_t)s->ng.nblocks * Ssz * Ssz, &ce);
+    s->Ufine = dalloc<double>(s, (size_t)s->Ns * N, &ce);
+    s->Lfine = dalloc<double>(s, (size_t)s->Ns * N, &ce);
+    s->ones = dalloc<double>(s, N, &ce);
+    s->qpt = dalloc<double>(s, qpt.size(), &ce);
+  }
+  if (nodal || s->src_nslots) {
+    s->src_pos = dalloc<int64_t>(s, (size_t)s->Ns, &ce);
+    s->src_neg = dalloc<int64_t>(s, (size_t)s->Ns, &ce);
+    s->src_amp = dalloc<double>(s, (size_t)s->Ns, &ce);
+  }
   if (s->src_nslots) {
     s->src_slots = dalloc<SrcSlot>(s, slots.size(), &ce);
     for (int k = 1; k <= d; ++k) s->src_slot0[k] = dalloc<int>(s, slot0[k].size(), &ce);
@@ -818,9 +905,6 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     s->srcMU = dalloc<double>(s, (size_t)src_nvals, &ce);
     s->srcdC = dalloc<double>(s, (size_t)src_nvals, &ce);
     s->src_recmap = dalloc<long long>(s, rec_map.size(), &ce);
-    s->src_pos = dalloc<int64_t>(s, (size_t)s->Ns, &ce);
-    s->src_neg = dalloc<int64_t>(s, (size_t)s->Ns, &ce);
-    s->src_amp = dalloc<double>(s, (size_t)s->Ns, &ce);
     if (!fl_j.empty()) {
       s->src_F.nrows = (int)fl_j.size();
       s->src_F.row_j = dalloc<int>(s, fl_j.size(), &ce);
@@ -851,16 +935,26 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   if (ce == cudaSuccess) ce = upload(s->rec_u, rec_u, st);
   if (ce == cudaSuccess) ce = upload(s->rq, rq, st);
   for (int k = 1; k <= d && ce == cudaSuccess; ++k) ce = upload(s->d_ents[k], s->h_ents[k], st);
-  if (s->src_nslots && ce == cudaSuccess) {
+  if ((nodal || s->src_nslots) && ce == cudaSuccess) {
     std::vector<int64_t> sp(desc->src_pos, desc->src_pos + s->Ns), sn(desc->src_neg, desc->src_neg + s->Ns);
     std::vector<double> sa((size_t)s->Ns, 1.0);
     if (desc->src_amp) sa.assign(desc->src_amp, desc->src_amp + s->Ns);
+    ce = upload(s->src_pos, sp, st);
+    if (ce == cudaSuccess) ce = upload(s->src_neg, sn, st);
+    if (ce == cudaSuccess) ce = upload(s->src_amp, sa, st);
+  }
+  if (nodal && ce == cudaSuccess) {
+    ce = upload(s->qpt, qpt, st);
+    if (ce == cudaSuccess) ce = upload(s->ones, std::vector<double>((size_t)N, 1.0), st);
+    // the coarse-stencil collapse of the cell-centred adjoint is not used: its array
+    // stays zero so the shared local adjoint kernel adds nothing from it
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(s->Lam, 0, sizeof(double) * (size_t)Nc * S3, st);
+    if (ce == cudaSuccess) cudaStreamSynchronize(st);
+  }
+  if (s->src_nslots && ce == cudaSuccess) {
     ce = upload(s->src_slots, slots, st);
     for (int k = 1; k <= d && ce == cudaSuccess; ++k) ce = upload(s->src_slot0[k], slot0[k], st);
     if (ce == cudaSuccess) ce = upload(s->src_recmap, rec_map, st);
-    if (ce == cudaSuccess) ce = upload(s->src_pos, sp, st);
-    if (ce == cudaSuccess) ce = upload(s->src_neg, sn, st);
-    if (ce == cudaSuccess) ce = upload(s->src_amp, sa, st);
     if (ce == cudaSuccess && s->src_F.nrows) {
       ce = upload(const_cast<int*>(s->src_F.row_j), fl_j, st);
       if (ce == cudaSuccess) ce = upload(const_cast<long long*>(s->src_F.row_I), fl_I, st);
@@ -949,7 +1043,123 @@ void coarse_prepare(msfv_session* s) {
   }
 }
 
+// ---- nodal Galerkin variant ------------------------------------------------------------
+int run_forward_nodal(msfv_session* s, const double* m, double* d_pred, double* u) {
+  const DevGeom& g = s->dg;
+  cudaStream_t st = s->stream;
+  const int d = g.d;
+  cudaMemsetAsync(s->status, 0, sizeof(int) * (2 + (size_t)s->Ns), st);
+  {
+    PhaseScope ps(s, PH_FACE_T);   // edge weights w and sigma
+    launch_nodal_weights(g, s->ng, m, nullptr, s->sig, s->T, st);
+    s->launches += 1;
+  }
+  {
+    PhaseScope ps(s, PH_VERTEX);   // Lagrange hats on the block boundaries
+    launch_nodal_hats(g, s->Pw, st);
+    s->launches += 1;
+  }
+  if (s->launch[d].n_ents) {       // block-interior solves (A_II x_I = -A_IB x_B)
+    PhaseScope ps(s, PH_INTERIOR);
+    launch_local_forward(g, s->launch[d], s->T, s->Pw, s->fac, s->status, st);
+    s->launches += 1;
+  }
+  {
+    PhaseScope ps(s, PH_COARSE_ASM);   // A_k = S^T A S
+    launch_galerkin(g, s->ng, s->sig, nullptr, s->Pw, nullptr, s->blockM, s->Ac, st);
+    s->launches += 2;
+  }
+  {
+    PhaseScope ps(s, PH_COARSE_SOLVE);   // b_j = S^T q_j, pinned solve
+    cudaMemsetAsync(s->t, 0, sizeof(double) * (size_t)s->Ns * g.Nc, st);
+    launch_nodal_rhs(g, s->Pw, s->src_pos, s->src_neg, s->src_amp, s->Ns, s->t, st);
+    s->launches += 1;
+    coarse_prepare(s);
+    coarse_solve(s, s->t, 0);
+  }
+  {
+    PhaseScope ps(s, PH_PROLONG);
+    launch_prolong_receivers(g, s->Pw, s->t, s->Ns, s->rec, s->Nr, s->dpred, st);
+    s->launches += 1;
+    if (d_pred)
+      cudaMemcpyAsync(d_pred, s->dpred, sizeof(double) * (size_t)s->Ns * s->Nr,
+                      cudaMemcpyDeviceToDevice, st);
+    if (u) {
+      launch_prolong_full(g, s->Pw, s->t, s->Ns, u, st);
+      s->launches += 1;
+    }
+  }
+  const int rc = check_launch(s, "msfv_forward");
+  if (rc == MSFV_OK) s->have_forward = true;
+  return rc;
+}
+
+// J^T w: -G(U)^T lambda on every edge, plus (adaptive basis) the block-interior adjoint
+// solves seeded at the receiver and source nodes with sum_j t_j(v) z_j + mu_j(v) q_j
+// (inside a block A S vanishes, so y_j = z_j and r_j = q_j there); then edges -> cells
+int run_jtvec_nodal(msfv_session* s, const double* w, double* out, bool fixed_basis) {
+  const DevGeom& g = s->dg;
+  cudaStream_t st = s->stream;
+  const int d = g.d;
+  {
+    PhaseScope ps(s, PH_ADJ_SETUP);
+    launch_receiver_gather(w, s->Ns, s->Nr, s->ru_off, s->ru_idx, s->Nru, s->zc, st);
+    launch_coarse_adjoint_rhs(g, s->Pw, s->zc, s->Ns, s->Nru, s->cj_off, s->cj_u, s->cj_s,
+                              s->ru_cell, s->lam, st);
+    s->launches += 2;
+    coarse_solve(s, s->lam, 1);
+    cudaMemsetAsync(s->gT, 0, sizeof(double) * (size_t)d * g.N, st);
+    if (!fixed_basis) {
+      launch_nodal_zt(g, s->t, s->lam, s->zc, s->qpt, s->Ns, s->Nru, s->ru_cell, s->ZT, st);
+      s->launches += 1;
+    }
+  }
+  if (!fixed_basis && s->launch[d].n_ents) {
+    PhaseScope ps(s, PH_ADJ_INTERIOR);
+    launch_local_adjoint(g, s->launch[d], s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u, s->ZT,
+                         s->X, s->gT, st);
+    s->launches += 1;
+  }
+  {
+    PhaseScope ps(s, PH_GRAD);
+    launch_prolong_full(g, s->Pw, s->t, s->Ns, s->Ufine, st);
+    launch_prolong_full(g, s->Pw, s->lam, s->Ns, s->Lfine, st);
+    launch_nodal_grad(g, s->ng, s->Ufine, s->Lfine, s->Ns, s->sig, s->gT, out, st);
+    s->launches += 4;
+  }
+  return check_launch(s, "msfv_jtvec");
+}
+
+// J v: dw, dS (block-interior tangents), dA_k = dS^T A S + S^T dA S + S^T A dS,
+// dt = A_k^{-1} (dS^T q - dA_k t), Pr^T (dS t + S dt)
+int run_jvec_nodal(msfv_session* s, const double* v, double* jv) {
+  const DevGeom& g = s->dg;
+  cudaStream_t st = s->stream;
+  const int d = g.d;
+  double* dW = s->T + (size_t)d * g.N;   // the second half of T is free in this variant
+  PhaseScope ps(s, PH_TANGENT);
+  launch_nodal_weights(g, s->ng, nullptr, v, s->sig, dW, st);
+  cudaMemsetAsync(s->X, 0, sizeof(double) * (size_t)g.N * g.S, st);
+  s->launches += 1;
+  if (s->launch[d].n_ents) {
+    // the shared tangent kernel forms dT = Dl v_lo + (T - Dl) v_hi; with T = Dl = dw
+    // and v = 1 that is dw (T itself is used elsewhere in it only against the boundary
+    // tangents, which are zero: block boundaries carry fixed Lagrange data)
+    launch_local_tangent(g, s->launch[d], dW, dW, s->ones, s->Pw, s->fac, s->X, st);
+    s->launches += 1;
+  }
+  launch_galerkin(g, s->ng, s->sig, v, s->Pw, s->X, s->blockM, s->dAc, st);
+  launch_coarse_tangent_rhs(g, s->dAc, s->t, s->Ns, s->dt, st);
+  launch_nodal_rhs(g, s->X, s->src_pos, s->src_neg, s->src_amp, s->Ns, s->dt, st);
+  s->launches += 4;
+  coarse_solve(s, s->dt, 0);
+  launch_prolong_tangent(g, s->Pw, s->X, s->t, s->dt, s->Ns, s->rec, s->Nr, jv, st);
+  s->launches += 1;
+  return check_launch(s, "msfv_jvec");
+}
+
 int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
+  if (s->nodal) return run_forward_nodal(s, m, d_pred, u);
   const DevGeom& g = s->dg;
   cudaStream_t st = s->stream;
   const int d = g.d;
@@ -1023,6 +1233,7 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
 // J^T w for w (Ns x Nr, device) at the last forward; out: N doubles.  fixed_basis: leave
 // out the derivative of the basis (the local adjoint solves), as in Sec. 4.2.
 int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = false) {
+  if (s->nodal) return run_jtvec_nodal(s, w, out, fixed_basis);
   const DevGeom& g = s->dg;
   cudaStream_t st = s->stream;
   const int d = g.d;
@@ -1064,6 +1275,7 @@ int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = 
 }
 
 int run_jvec(msfv_session* s, const double* v, double* jv) {
+  if (s->nodal) return run_jvec_nodal(s, v, jv);
   const DevGeom& g = s->dg;
   cudaStream_t st = s->stream;
   const int d = g.d;
@@ -1166,7 +1378,7 @@ extern "C" int msfv_solve_host(msfv_session_t* s, const double* m_host, const do
     return fail(s, MSFV_ERR_ARG, "msfv_solve_host: NULL argument");
   cudaStream_t st = s->stream;
   const size_t nd = sizeof(double) * (size_t)s->Ns * s->Nr;
-  cudaError_t e = cudaMemcpyAsync(s->m_tmp, m_host, sizeof(double) * (size_t)s->dg.N,
+  cudaError_t e = cudaMemcpyAsync(s->m_tmp, m_host, sizeof(double) * (size_t)s->Nm,
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s->dobs_tmp, d_obs_host, nd, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(s, e, "msfv_solve_host upload");
@@ -1178,7 +1390,7 @@ extern "C" int msfv_solve_host(msfv_session_t* s, const double* m_host, const do
   if (rc != MSFV_OK) return rc;
   e = cudaMemcpyAsync(d_pred_host, s->dpred, nd, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(grad_host, s->grad_tmp, sizeof(double) * (size_t)s->dg.N,
+    e = cudaMemcpyAsync(grad_host, s->grad_tmp, sizeof(double) * (size_t)s->Nm,
                         cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && phi_host)
     e = cudaMemcpyAsync(phi_host, s->phi, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -1485,6 +1697,7 @@ extern "C" int msfv_gn_step(msfv_session_t* s, double* m_dev, const double* d_ob
   if (!m_dev || !d_obs_dev || !o || !out) return fail(s, MSFV_ERR_ARG, "msfv_gn_step: NULL argument");
   if (o->alpha < 0 || o->cg_iters < 1 || o->max_backtracks < 0 || !(o->m_min < o->m_max))
     return fail(s, MSFV_ERR_ARG, "msfv_gn_step: invalid options");
+  if (s->nodal) return fail(s, MSFV_ERR_ARG, "msfv_gn_step: not available for the nodal variant");
   int rc = gn_alloc(s);
   if (rc != MSFV_OK) return rc;
   const DevGeom& g = s->dg;
@@ -1572,6 +1785,7 @@ extern "C" int msfv_gn_step(msfv_session_t* s, double* m_dev, const double* d_ob
 extern "C" int msfv_autotune(msfv_session_t* s, const double* m_dev, int* variants_out,
                              double* ms_out) {
   if (!s) return MSFV_ERR_ARG;
+  if (s->nodal) return fail(s, MSFV_ERR_ARG, "msfv_autotune: not available for the nodal variant");
   const DevGeom& g = s->dg;
   cudaStream_t st = s->stream;
   const double* m = m_dev;

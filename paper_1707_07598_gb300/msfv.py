@@ -49,7 +49,7 @@ class _Desc(ctypes.Structure):
                 ("src_amp", ctypes.POINTER(ctypes.c_double)),
                 ("n_rec", ctypes.c_int), ("rec_cell", ctypes.POINTER(ctypes.c_int64)),
                 ("factor_mode", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
-                ("source_bases", ctypes.c_int)]
+                ("source_bases", ctypes.c_int), ("discretization", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -143,7 +143,10 @@ class Session:
         self.prob = prob
         n = tuple(int(v) for v in prob.n)
         self.dim = len(n)
-        self.N = int(np.prod(n))
+        self.N = int(np.prod(n))                      # model cells
+        self.nodal = bool(getattr(prob, "nodal", False))
+        # field values per source: nodes of the (n+1)^d lattice in the nodal variant
+        self.Nf = int(np.prod([v + 1 for v in n])) if self.nodal else self.N
         self.Ns = int(prob.n_src)
         self.Nr = int(prob.n_rec)
         self._src_pos = np.ascontiguousarray(prob.src_pos, dtype=np.int64)
@@ -164,6 +167,7 @@ class Session:
         d.factor_mode = int(factor_mode)
         d.hbm_budget_bytes = int(hbm_budget_bytes)
         d.source_bases = 1 if getattr(prob, "source_bases", False) else 0
+        d.discretization = 1 if getattr(prob, "nodal", False) else 0
         h = ctypes.c_void_p()
         self._h = None
         rc = L.msfv_setup(ctypes.byref(d), ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h))

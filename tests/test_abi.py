@@ -53,6 +53,7 @@ def _desc(**kw):
     d.factor_mode = kw.get("fm", 0)
     d.hbm_budget_bytes = kw.get("budget", 0)
     d.source_bases = kw.get("sb", 0)
+    d.discretization = kw.get("disc", 0)
     d._keep = (pos, neg, rec, r)
     return d
 
@@ -72,6 +73,10 @@ def _desc(**kw):
     (dict(sb=2), "source_bases"),
     (dict(sb=1, fm=2), "stored local factors"),
     (dict(sb=1, budget=1000), "stored local factors"),
+    (dict(disc=2), "discretization"),
+    (dict(disc=1, sb=1), "not available for the nodal"),
+    (dict(disc=1, fm=2), "stored local factors"),
+    (dict(disc=1, budget=1000), "stored local factors"),
 ])
 def test_setup_rejects_bad_descriptors_on_the_host(lib, kw, frag):
     d = _desc(**kw)
