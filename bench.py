@@ -54,12 +54,13 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="plain",
-                   choices=["plain", "batched", "served", "diff", "gn", "sources"],
+                   choices=["plain", "batched", "served", "diff", "gn", "sources", "nodal"],
                    help="plain: the one-instance 128^3 step (default); batched: independent "
                         "instances in one CUDA graph vs one at a time; served: the Poisson "
                         "request stream; diff: 256^3, c=16 gradient, J v, J^T w; gn: 5 "
                         "Gauss-Newton-CG iterations on the 128^3 two-block model; sources: "
-                        "the 128^3 step with source bases beside the plain one")
+                        "the 128^3 step with source bases beside the plain one; nodal: "
+                        "the paper's nodal Galerkin variant on the same survey shape")
     p.add_argument("--instances", type=int, default=64, help="batched: number of instances")
     p.add_argument("--rate", type=float, default=50.0, help="served: requests per second")
     p.add_argument("--duration", type=float, default=10.0,
@@ -649,6 +650,69 @@ def run_sources(args):
     return 0
 
 
+def run_nodal(args):
+    """The paper's own variant (nodal operator, Lagrange block data, Galerkin A_k) on the
+    default survey shape: 128^3 cells (129^3 nodes), c = 8, 16 dipoles and 512
+    receivers on the top surface; one forward + gradient per step, timed like the
+    default line."""
+    torch, dev = _gpu_setup()
+    from paper_1707_07598_gb300.msfv import Session
+    n = args.n
+    prob = W.make_problem((n, n, n), 8, 16, 512, seed=2, top_layer=True, nodal=True)
+    m_np = W.config_3d_128(n=n)[1]
+    stream = torch.cuda.current_stream(dev)
+    sess = Session(prob, stream=stream)
+    m = torch.from_numpy(m_np).to(dev)
+    m_true = torch.from_numpy(W.config_3d_128(seed=3, n=n)[1]).to(dev)
+    d_true = sess.forward(m_true).clone()
+    noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, 4)).to(dev)
+    d_obs = d_true + 0.01 * d_true.abs() * noise
+    grad = torch.empty(prob.N, dtype=torch.float64, device=dev)
+    d_pred = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        sess.forward(m, d_pred)
+        sess.adjoint(d_obs, grad, want_phi=False)
+    torch.cuda.synchronize(dev)
+    sess.profile(True)
+    sess.phase_times(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    l0 = sess.launch_count()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        sess.forward(m, d_pred)
+        sess.adjoint(d_obs, grad, want_phi=False)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = sess.launch_count() - l0
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ph = sess.phase_times(reset=True)
+    info = sess.info()
+    mean = sum(ms) / len(ms)
+    out = {"metric": METRIC, "value": 1000.0 / mean, "unit": "solves/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean,
+           "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": f"3d_{n}^3_c8_16dipoles_512rec_fwd+grad_nodal_galerkin",
+                      "discretization": "nodal", "nodes": [n + 1] * 3,
+                      "l2": "flushed before every timed step (512 MiB write)",
+                      "factor_mode": "store"},
+           "gpu_launches": launches, "clocks": clk,
+           "phases_ms_per_step": {k: v[0] / args.steps for k, v in ph.items() if v[1]},
+           "coarse": {"solver": "mg-gmres" if info["coarse_solver"] else "banded-lu",
+                      "iters_fwd": info["coarse_iters"], "iters_adj": info["coarse_iters_T"]}}
+    print(json.dumps(out))
+    sess.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -663,6 +727,8 @@ def main():
         return run_gn(args)
     if args.workload == "sources":
         return run_sources(args)
+    if args.workload == "nodal":
+        return run_nodal(args)
     return run_ours(args)
 
 

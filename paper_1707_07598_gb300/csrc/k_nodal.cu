@@ -37,12 +37,6 @@ __device__ __forceinline__ long long stride_of(const long long* st, int a) {
   return a == 0 ? st[0] : (a == 1 ? st[1] : st[2]);
 }
 
-// weight of slot bit `bit` along one axis at node coordinate xa (multilinear hat)
-__device__ __forceinline__ double hat1(int xa, int c, int bit) {
-  const int r = xa % c;
-  return bit ? (double)r / c : 1.0 - (double)r / c;
-}
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -79,11 +73,16 @@ __device__ __forceinline__ double edge_cells(const DevGeom& g, const NodalGeom& 
 
 }  // namespace
 
-// w on every lattice edge, per axis by lower node, and sigma = exp(m) on the cells
-// (m != null); or, with m == null, the tangent of w along v from the stored sigma
-__global__ void k_nodal_weights(DevGeom g, NodalGeom ng, const double* __restrict__ m,
-                                const double* __restrict__ v, double* __restrict__ sig,
-                                double* __restrict__ w) {
+__global__ void k_nodal_sigma(NodalGeom ng, const double* __restrict__ m, double* __restrict__ sig) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ng.Ncell;
+       c += (long long)gridDim.x * blockDim.x)
+    sig[c] = exp(m[c]);
+}
+
+// w on every lattice edge, per axis by lower node, from sigma; or (v != null) its
+// tangent along v
+__global__ void k_nodal_weights(DevGeom g, NodalGeom ng, const double* __restrict__ v,
+                                const double* __restrict__ sig, double* __restrict__ w) {
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < g.N;
        x += (long long)gridDim.x * blockDim.x) {
     int xc[3];
@@ -95,33 +94,37 @@ __global__ void k_nodal_weights(DevGeom g, NodalGeom ng, const double* __restric
       double val = 0.0;
       if (xc[a] + 1 < g.n[a]) {
         const double scale = ng.geo[a] / (g.d == 3 ? 4.0 : 2.0);
-        const double s = m ? edge_cells(g, ng, xc, a, lo, ng.n,
-                                        [&](long long c) { return exp(m[c]); })
+        const double s = v ? edge_cells(g, ng, xc, a, lo, ng.n,
+                                        [&](long long c) { return sig[c] * v[c]; })
                            : edge_cells(g, ng, xc, a, lo, ng.n,
-                                        [&](long long c) { return sig[c] * v[c]; });
+                                        [&](long long c) { return sig[c]; });
         val = scale * s;
       }
       w[(long long)a * g.N + x] = val;
     }
   }
-  if (m)
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ng.Ncell;
-         c += (long long)gridDim.x * blockDim.x)
-      sig[c] = exp(m[c]);
 }
 
 // multilinear hats in the basis weights of every node (block interiors are overwritten
-// by the local solves)
+// by the local solves); per axis the two weights 1 - r/c and r/c, then their products
 __global__ void k_nodal_hats(DevGeom g, double* __restrict__ Pw) {
+  const double rc = 1.0 / (double)g.c;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < g.N;
        x += (long long)gridDim.x * blockDim.x) {
     int xc[3];
     lattice(g.n, x, xc);
-    for (int s = 0; s < g.S; ++s) {
-      double wv = 1.0;
+    double w0[3], w1[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (a < g.d) wv *= hat1(xc[a], g.c, (s >> a) & 1);
+    for (int a = 0; a < 3; ++a) {
+      const double f = (double)(xc[a] % g.c) * rc;
+      w1[a] = a < g.d ? f : 0.0;
+      w0[a] = a < g.d ? 1.0 - f : 1.0;
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      if (s >= g.S) continue;
+      const double wv = ((s & 1) ? w1[0] : w0[0]) * ((s & 2) ? w1[1] : w0[1]) *
+                        ((s & 4) ? w1[2] : w0[2]);
       Pw[x * g.S + s] = wv;
     }
   }
@@ -402,7 +405,8 @@ int grid_for(long long n) {
 
 void launch_nodal_weights(const DevGeom& g, const NodalGeom& ng, const double* m, const double* v,
                           double* sig, double* w, cudaStream_t s) {
-  k_nodal_weights<<<grid_for(g.N > ng.Ncell ? g.N : ng.Ncell), kThreads, 0, s>>>(g, ng, m, v, sig, w);
+  if (m) k_nodal_sigma<<<grid_for(ng.Ncell), kThreads, 0, s>>>(ng, m, sig);
+  k_nodal_weights<<<grid_for(g.N), kThreads, 0, s>>>(g, ng, v, sig, w);
 }
 
 void launch_nodal_hats(const DevGeom& g, double* Pw, cudaStream_t s) {

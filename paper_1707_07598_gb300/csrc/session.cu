@@ -111,6 +111,11 @@ struct msfv_session {
   long long Nm = 0;                  // model size (cells)
   double *blockM = nullptr, *Ufine = nullptr, *Lfine = nullptr, *ones = nullptr,
          *qpt = nullptr;
+  // block interiors holding a receiver or source node: elsewhere the adjoint seeds are
+  // zero (A S vanishes inside a block), so the adjoint solves run on these only
+  std::vector<EntDesc> h_ents_adj;
+  EntDesc* d_ents_adj = nullptr;
+  LocalLaunch launch_adj{};
   // source bases (Sec. 3.2): slots, their values and the maps that use them
   int src_nslots = 0;
   long long src_nvals = 0;
@@ -520,6 +525,17 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
         rec_u.push_back(pr.second);
       }
     }
+  if (nodal && d >= 1) {
+    for (const auto& e : s->h_ents[d])
+      if (e.rec_cnt > 0) s->h_ents_adj.push_back(e);
+    s->launch_adj = s->launch[d];
+    s->launch_adj.n_ents = (int)s->h_ents_adj.size();
+    if (s->launch_adj.n_ents &&
+        !local_plan(g, s->launch_adj, force_gw, s->launch[d].variant)) {
+      delete s;
+      return fail(nullptr, MSFV_ERR_ARG, "coarsening too large for the local problems");
+    }
+  }
   std::vector<int> cj_off(Nc + 1, 0), cj_u, cj_s;
   for (long long J = 0; J < Nc; ++J) {
     cj_off[J] = (int)cj_u.size();
@@ -886,6 +902,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     }
   }
   for (int k = 1; k <= d; ++k) s->d_ents[k] = dalloc<EntDesc>(s, s->h_ents[k].size(), &ce);
+  if (!s->h_ents_adj.empty()) s->d_ents_adj = dalloc<EntDesc>(s, s->h_ents_adj.size(), &ce);
   if (nodal) {
     s->blockM = dalloc<double>(s, (size_t)s->ng.nblocks * Ssz * Ssz, &ce);
     s->Ufine = dalloc<double>(s, (size_t)s->Ns * N, &ce);
@@ -935,6 +952,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   if (ce == cudaSuccess) ce = upload(s->rec_u, rec_u, st);
   if (ce == cudaSuccess) ce = upload(s->rq, rq, st);
   for (int k = 1; k <= d && ce == cudaSuccess; ++k) ce = upload(s->d_ents[k], s->h_ents[k], st);
+  if (ce == cudaSuccess && s->d_ents_adj) ce = upload(s->d_ents_adj, s->h_ents_adj, st);
   if ((nodal || s->src_nslots) && ce == cudaSuccess) {
     std::vector<int64_t> sp(desc->src_pos, desc->src_pos + s->Ns), sn(desc->src_neg, desc->src_neg + s->Ns);
     std::vector<double> sa((size_t)s->Ns, 1.0);
@@ -979,6 +997,11 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     s->launch[k].ents = s->d_ents[k];
     s->launch[k].counter = s->local_ctr + 3 * k;
     s->launch[k].scratch = s->launch[k].scratch_group ? s->local_scratch : nullptr;
+  }
+  if (nodal) {
+    s->launch_adj.ents = s->d_ents_adj;
+    s->launch_adj.counter = s->launch[d].counter;
+    s->launch_adj.scratch = s->launch[d].scratch;
   }
   for (int k = 0; k <= 3; ++k) {
     SrcLaunch& SL = s->src_L[k];
@@ -1050,9 +1073,9 @@ int run_forward_nodal(msfv_session* s, const double* m, double* d_pred, double* 
   const int d = g.d;
   cudaMemsetAsync(s->status, 0, sizeof(int) * (2 + (size_t)s->Ns), st);
   {
-    PhaseScope ps(s, PH_FACE_T);   // edge weights w and sigma
+    PhaseScope ps(s, PH_FACE_T);   // sigma and the edge weights w
     launch_nodal_weights(g, s->ng, m, nullptr, s->sig, s->T, st);
-    s->launches += 1;
+    s->launches += 2;
   }
   {
     PhaseScope ps(s, PH_VERTEX);   // Lagrange hats on the block boundaries
@@ -1114,9 +1137,9 @@ int run_jtvec_nodal(msfv_session* s, const double* w, double* out, bool fixed_ba
       s->launches += 1;
     }
   }
-  if (!fixed_basis && s->launch[d].n_ents) {
+  if (!fixed_basis && s->launch_adj.n_ents) {
     PhaseScope ps(s, PH_ADJ_INTERIOR);
-    launch_local_adjoint(g, s->launch[d], s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u, s->ZT,
+    launch_local_adjoint(g, s->launch_adj, s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u, s->ZT,
                          s->X, s->gT, st);
     s->launches += 1;
   }
