@@ -158,16 +158,60 @@ __global__ void k_nodal_rhs(DevGeom g, const double* __restrict__ Pw, const int6
   }
 }
 
+// Corner differences of the basis along edge (x, x + e_a) for the corners of block B:
+// dp[v] = phi_v(x) - phi_v(y) from Pw (and ddp from dPw when given).
+__device__ __forceinline__ void corner_diffs(const DevGeom& g, const int* B, const int* xc, int a,
+                                             const double* __restrict__ Pw,
+                                             const double* __restrict__ dPw, double* dp,
+                                             double* ddp) {
+  const int S = g.S;
+  const long long x = xc[0] * g.st[0] + xc[1] * g.st[1] + xc[2] * g.st[2];
+  const long long y = x + stride_of(g.st, a);
+  // corner offsets of B relative to the lower coarse vertex of x and of y per axis
+  int ox[3], oy[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int lx = b < g.d ? xc[b] / g.c : 0;
+    const int ly = (b == a) ? (xc[b] + 1) / g.c : lx;
+    ox[b] = B[b] - lx;
+    oy[b] = B[b] - ly;
+  }
+#pragma unroll
+  for (int cv = 0; cv < 8; ++cv) {
+    dp[cv] = 0.0;
+    if (ddp) ddp[cv] = 0.0;
+    if (cv >= S) continue;
+    // slot of corner cv (B + bits) at x and at y = x + e_a
+    int sx = 0, sy = 0;
+    bool okx = true, oky = true;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b >= g.d) continue;
+      const int bit = (cv >> b) & 1;
+      const int bx = ox[b] + bit, by = oy[b] + bit;
+      if (bx < 0 || bx > 1) okx = false;
+      if (by < 0 || by > 1) oky = false;
+      sx |= (bx & 1) << b;
+      sy |= (by & 1) << b;
+    }
+    dp[cv] = (okx ? Pw[x * S + sx] : 0.0) - (oky ? Pw[y * S + sy] : 0.0);
+    if (ddp) ddp[cv] = (okx ? dPw[x * S + sx] : 0.0) - (oky ? dPw[y * S + sy] : 0.0);
+  }
+}
+
 // Per block B the 2^d x 2^d matrix of the Galerkin operator restricted to B's cells:
 //     M_B(v, v') = sum_{edges e of B's cells} w_e^B dphi_v(e) dphi_v'(e),
 // w_e^B counting only the cells of B.  Tangent mode (dPw != null):
 //     sum w_e^B (ddphi_v dphi_v' + dphi_v ddphi_v') + dw_e^B dphi_v dphi_v'.
-// One CTA per block, edges over the threads, fixed-order reductions.
+// One CTA per block: the threads evaluate a chunk of edges into shared memory, then
+// thread (v, v') adds the chunk's products to its own entry (fixed order, no atomics).
+constexpr int kChunk = kAsmThreads;
+
 __global__ void __launch_bounds__(kAsmThreads)
 k_block_assemble(DevGeom g, NodalGeom ng, const double* __restrict__ sig,
                  const double* __restrict__ v, const double* __restrict__ Pw,
                  const double* __restrict__ dPw, double* __restrict__ M) {
-  __shared__ double red[kAsmThreads / 32][64];
+  __shared__ double D[8][kChunk], DD[8][kChunk], Wb[kChunk];
   const int S = g.S;
   const long long blk = blockIdx.x;
   int B[3] = {0, 0, 0};
@@ -186,92 +230,80 @@ k_block_assemble(DevGeom g, NodalGeom ng, const double* __restrict__ sig,
     chi[a] = a < g.d ? clo[a] + g.c : 1;
     ext[a] = a < g.d ? g.c + 1 : 1;     // nodes of the block closure per axis
   }
-  const long long nodes = (long long)ext[0] * ext[1] * ext[2];
-  double acc[36];
-#pragma unroll
-  for (int k = 0; k < 36; ++k) acc[k] = 0.0;
+  const int nodes = ext[0] * ext[1] * ext[2];     // at most 17^3 (c <= 16)
+  const int total = nodes * g.d;
+  const int e01 = ext[0] * ext[1];
   const double cscale = 1.0 / (g.d == 3 ? 4.0 : 2.0);
-  for (long long it = threadIdx.x; it < nodes * g.d; it += kAsmThreads) {
-    const int a = (int)(it / nodes);
-    const long long r = it - (long long)a * nodes;
-    int xc[3];
-    xc[0] = clo[0] + (int)(r % ext[0]);
-    xc[1] = clo[1] + (int)((r / ext[0]) % ext[1]);
-    xc[2] = clo[2] + (int)(r / ((long long)ext[0] * ext[1]));
-    const int xa = a == 0 ? xc[0] : (a == 1 ? xc[1] : xc[2]);
-    const int ca = a == 0 ? chi[0] : (a == 1 ? chi[1] : chi[2]);
-    if (xa >= ca) continue;                          // the edge leaves the block
-    const double wB = ng.geo[a] * cscale *
-                      edge_cells(g, ng, xc, a, clo, chi, [&](long long c) { return sig[c]; });
-    const double dwB = v ? ng.geo[a] * cscale *
-                               edge_cells(g, ng, xc, a, clo, chi,
-                                          [&](long long c) { return sig[c] * v[c]; })
-                         : 0.0;
-    if (wB == 0.0 && dwB == 0.0) continue;
-    const long long x = xc[0] * g.st[0] + xc[1] * g.st[1] + xc[2] * g.st[2];
-    const long long y = x + stride_of(g.st, a);
-    int yc[3] = {xc[0], xc[1], xc[2]};
-    if (a == 0) yc[0] += 1;
-    if (a == 1) yc[1] += 1;
-    if (a == 2) yc[2] += 1;
-    double dp[8], ddp[8];
-#pragma unroll
-    for (int cv = 0; cv < 8; ++cv) {
-      dp[cv] = 0.0;
-      ddp[cv] = 0.0;
-      if (cv >= S) continue;
-      // slot of corner cv (B + bits) at x and at y
-      int sx = 0, sy = 0;
-      bool okx = true, oky = true;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        if (b >= g.d) continue;
-        const int vb = B[b] + ((cv >> b) & 1);
-        const int bx = vb - xc[b] / g.c, by = vb - yc[b] / g.c;
-        if (bx < 0 || bx > 1) okx = false;
-        if (by < 0 || by > 1) oky = false;
-        sx |= (bx & 1) << b;
-        sy |= (by & 1) << b;
-      }
-      const double px = okx ? Pw[x * S + sx] : 0.0, py = oky ? Pw[y * S + sy] : 0.0;
-      dp[cv] = px - py;
-      if (dPw) ddp[cv] = (okx ? dPw[x * S + sx] : 0.0) - (oky ? dPw[y * S + sy] : 0.0);
+  const int tid = threadIdx.x;
+  // thread (part, k): entry k = (ep, eq), ep <= eq, of the upper triangle, over the
+  // edges e = part, part + 3, ... of each chunk; parts are added in order at the end
+  const int NP = S * (S + 1) / 2;
+  const int part = tid / NP, kk = tid - (tid / NP) * NP;
+  const bool owner = part < 3;
+  int ep = 0, eq = 0;
+  {
+    int r = kk;
+    while (r >= S - ep) {
+      r -= S - ep;
+      ++ep;
     }
-    int k = 0;
-#pragma unroll
-    for (int p = 0; p < 8; ++p)
-#pragma unroll
-      for (int q = p; q < 8; ++q) {
-        if (q < S) {
-          double t = dwB * dp[p] * dp[q];
-          if (dPw) t = fma(wB, fma(ddp[p], dp[q], dp[p] * ddp[q]), t);
-          else t = wB * dp[p] * dp[q];
-          acc[k] += t;
-        }
-        ++k;
-      }
+    eq = ep + r;
   }
-  // fixed-order reduction: warps by shuffles, then warp partials in order
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int npairs = S * (S + 1) / 2;
-  int k = 0;
+  double acc = 0.0;
+  for (int c0 = 0; c0 < total; c0 += kChunk) {
+    const int it = c0 + tid;
+    double wB = 0.0, dwB = 0.0, dp[8], ddp[8];
 #pragma unroll
-  for (int p = 0; p < 8; ++p)
-#pragma unroll
-    for (int q = p; q < 8; ++q) {
-      const double s = warp_sum(acc[k]);
-      if (lane == 0 && q < S) red[wid][p * 8 + q] = s;
-      ++k;
+    for (int k = 0; k < 8; ++k) {
+      dp[k] = 0.0;
+      ddp[k] = 0.0;
     }
+    if (it < total) {
+      const int a = it / nodes;
+      const int r = it - a * nodes;
+      const int r2 = r / e01, r01 = r - r2 * e01;
+      const int r1 = r01 / ext[0];
+      int xc[3];
+      xc[0] = clo[0] + (r01 - r1 * ext[0]);
+      xc[1] = clo[1] + r1;
+      xc[2] = clo[2] + r2;
+      const int xa = a == 0 ? xc[0] : (a == 1 ? xc[1] : xc[2]);
+      const int ca = a == 0 ? chi[0] : (a == 1 ? chi[1] : chi[2]);
+      if (xa < ca) {                                   // the edge stays in the block
+        const double ga = a == 0 ? ng.geo[0] : (a == 1 ? ng.geo[1] : ng.geo[2]);
+        wB = ga * cscale * edge_cells(g, ng, xc, a, clo, chi, [&](long long c) { return sig[c]; });
+        if (v)
+          dwB = ga * cscale *
+                edge_cells(g, ng, xc, a, clo, chi, [&](long long c) { return sig[c] * v[c]; });
+        corner_diffs(g, B, xc, a, Pw, dPw, dp, dPw ? ddp : nullptr);
+      }
+    }
+    // entry (p, q) of the chunk is sum_e X_p D_q (+ D_p X_q in tangent mode) with
+    // X = w dphi, or X = w ddphi + dw/2 dphi for the tangent: one or two FMAs per entry
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      D[k][tid] = dp[k];
+      DD[k][tid] = dPw ? fma(wB, ddp[k], 0.5 * dwB * dp[k]) : wB * dp[k];
+    }
+    __syncthreads();
+    if (owner) {
+      if (dPw) {
+        for (int e = part; e < kChunk; e += 3)
+          acc = fma(DD[ep][e], D[eq][e], fma(D[ep][e], DD[eq][e], acc));
+      } else {
+        for (int e = part; e < kChunk; e += 3) acc = fma(DD[ep][e], D[eq][e], acc);
+      }
+    }
+    __syncthreads();
+  }
+  // the three parts of each entry, in order; both triangles written
+  if (owner) Wb[part * NP + kk] = acc;
   __syncthreads();
-  for (int e = threadIdx.x; e < S * S; e += kAsmThreads) {
-    const int p = e / S, q = e - (e / S) * S;
-    const int lo = p < q ? p : q, hi = p < q ? q : p;
-    double s = 0.0;
-    for (int w = 0; w < kAsmThreads / 32; ++w) s += red[w][lo * 8 + hi];
-    M[blk * S * S + e] = s;
+  if (owner && part == 0) {
+    const double tot = (Wb[kk] + Wb[NP + kk]) + Wb[2 * NP + kk];
+    M[blk * S * S + ep * S + eq] = tot;
+    M[blk * S * S + eq * S + ep] = tot;
   }
-  (void)npairs;
 }
 
 // A_k entry (I, I + o), offset-major A[o * Nc + I]: sum of M_B over the blocks that
@@ -347,23 +379,67 @@ __global__ void k_nodal_zt(DevGeom g, const double* __restrict__ t, const double
   ZT[idx] = acc;
 }
 
-// gT[e] -= sum_j (lambda_j(x) - lambda_j(y)) (U_j(x) - U_j(y)): the G(U)^T lambda term
-__global__ void k_nodal_edge_grad(DevGeom g, const double* __restrict__ U,
-                                  const double* __restrict__ Lf, int Ns, double* __restrict__ gT) {
+// MT[B][v][v'] = sum_j mu_j(B + v) t_j(B + v') for every block B (corner offsets v, v')
+__global__ void k_block_mt(DevGeom g, NodalGeom ng, const double* __restrict__ mu,
+                           const double* __restrict__ t, int Ns, double* __restrict__ MT) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int SS = g.S * g.S;
+  if (idx >= ng.nblocks * SS) return;
+  const long long blk = idx / SS;
+  const int e = (int)(idx - blk * SS), p = e / g.S, q = e - (e / g.S) * g.S;
+  int B[3];
+  lattice(ng.nb, blk, B);
+  long long Jp = 0, Jq = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.d) continue;
+    Jp += (long long)(B[a] + ((p >> a) & 1)) * g.cst[a];
+    Jq += (long long)(B[a] + ((q >> a) & 1)) * g.cst[a];
+  }
+  // symmetric part: only dphi^T MT dphi is needed
+  double acc = 0.0;
+  for (int j = 0; j < Ns; ++j) {
+    acc = fma(mu[(long long)j * g.Nc + Jp], t[(long long)j * g.Nc + Jq], acc);
+    acc = fma(mu[(long long)j * g.Nc + Jq], t[(long long)j * g.Nc + Jp], acc);
+  }
+  MT[idx] = 0.5 * acc;
+}
+
+// gT[e] -= sum_j (lambda_j(x) - lambda_j(y)) (U_j(x) - U_j(y)) = dphi^T MT_B dphi, with
+// lambda_j = S mu_j, U_j = S t_j and B a block whose closure holds the edge (on a block
+// face only the face's corners carry non-zero differences, and those are shared)
+__global__ void k_nodal_edge_grad(DevGeom g, NodalGeom ng, const double* __restrict__ Pw,
+                                  const double* __restrict__ MT, double* __restrict__ gT) {
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < g.N;
        x += (long long)gridDim.x * blockDim.x) {
     int xc[3];
     lattice(g.n, x, xc);
+    int B[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= g.d) continue;
+      const int b = xc[a] / g.c;
+      B[a] = b < ng.nb[a] ? b : ng.nb[a] - 1;
+    }
+    const long long blk = B[0] + (long long)ng.nb[0] * (B[1] + (long long)ng.nb[1] * B[2]);
+    const double* mt = MT + blk * g.S * g.S;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (a >= g.d || xc[a] + 1 >= g.n[a]) continue;
-      const long long y = x + stride_of(g.st, a);
+      double dp[8];
+      corner_diffs(g, B, xc, a, Pw, nullptr, dp, nullptr);
+      // dphi^T MT dphi with MT symmetric: 2 sum_p dphi_p (MT_pp dphi_p / 2 + sum_{q>p} ...)
       double acc = 0.0;
-      for (int j = 0; j < Ns; ++j) {
-        const long long o = (long long)j * g.N;
-        acc = fma(Lf[o + x] - Lf[o + y], U[o + x] - U[o + y], acc);
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        if (p >= g.S) continue;
+        double r = 0.5 * mt[p * g.S + p] * dp[p];
+#pragma unroll
+        for (int q = p + 1; q < 8; ++q)
+          if (q < g.S) r = fma(mt[p * g.S + q], dp[q], r);
+        acc = fma(dp[p], r, acc);
       }
-      gT[(long long)a * g.N + x] -= acc;
+      gT[(long long)a * g.N + x] -= 2.0 * acc;
     }
   }
 }
@@ -433,9 +509,12 @@ void launch_nodal_zt(const DevGeom& g, const double* t, const double* mu, const 
   k_nodal_zt<<<(int)((tot + 127) / 128), 128, 0, s>>>(g, t, mu, zc, qpt, Ns, Nru, ru_cell, ZT);
 }
 
-void launch_nodal_grad(const DevGeom& g, const NodalGeom& ng, const double* U, const double* Lf,
-                       int Ns, const double* sig, double* gT, double* grad, cudaStream_t s) {
-  k_nodal_edge_grad<<<grid_for(g.N), kThreads, 0, s>>>(g, U, Lf, Ns, gT);
+void launch_nodal_grad(const DevGeom& g, const NodalGeom& ng, const double* Pw, const double* t,
+                       const double* mu, int Ns, double* MT, const double* sig, double* gT,
+                       double* grad, cudaStream_t s) {
+  const long long tot = ng.nblocks * g.S * g.S;
+  k_block_mt<<<(int)((tot + 127) / 128), 128, 0, s>>>(g, ng, mu, t, Ns, MT);
+  k_nodal_edge_grad<<<grid_for(g.N), kThreads, 0, s>>>(g, ng, Pw, MT, gT);
   k_nodal_cell_grad<<<grid_for(ng.Ncell), kThreads, 0, s>>>(g, ng, sig, gT, grad);
 }
 

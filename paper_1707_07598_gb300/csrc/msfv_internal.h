@@ -100,8 +100,9 @@ void launch_galerkin(const DevGeom& g, const NodalGeom& ng, const double* sig, c
 void launch_nodal_zt(const DevGeom& g, const double* t, const double* mu, const double* zc,
                      const double* qpt, int Ns, int Nru, const int64_t* ru_cell, double* ZT,
                      cudaStream_t s);
-void launch_nodal_grad(const DevGeom& g, const NodalGeom& ng, const double* U, const double* Lf,
-                       int Ns, const double* sig, double* gT, double* grad, cudaStream_t s);
+void launch_nodal_grad(const DevGeom& g, const NodalGeom& ng, const double* Pw, const double* t,
+                       const double* mu, int Ns, double* MT, const double* sig, double* gT,
+                       double* grad, cudaStream_t s);
 
 // Phase ids for the event timers.
 enum Phase {

@@ -109,8 +109,7 @@ struct msfv_session {
   bool nodal = false;
   NodalGeom ng{};
   long long Nm = 0;                  // model size (cells)
-  double *blockM = nullptr, *Ufine = nullptr, *Lfine = nullptr, *ones = nullptr,
-         *qpt = nullptr;
+  double *blockM = nullptr, *blockMT = nullptr, *ones = nullptr, *qpt = nullptr;
   // block interiors holding a receiver or source node: elsewhere the adjoint seeds are
   // zero (A S vanishes inside a block), so the adjoint solves run on these only
   std::vector<EntDesc> h_ents_adj;
@@ -777,8 +776,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
             sizeof(double) * fl_sign.size() + sizeof(int) * (fl_j.size() + fl_ptr.size() + 16) +
             (sizeof(int64_t) * 2 + sizeof(double)) * (size_t)s->Ns;
   if (nodal)
-    need += sizeof(double) * ((size_t)s->ng.nblocks * Ssz * Ssz + 2 * (size_t)s->Ns * N + N +
-                              qpt.size()) +
+    need += sizeof(double) * (2 * (size_t)s->ng.nblocks * Ssz * Ssz + N + qpt.size()) +
             (sizeof(int64_t) * 2 + sizeof(double)) * (size_t)s->Ns;
   if (nodal && desc->factor_mode == 0 && desc->hbm_budget_bytes &&
       need + s->fac_bytes + scr > desc->hbm_budget_bytes) {
@@ -905,8 +903,7 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   if (!s->h_ents_adj.empty()) s->d_ents_adj = dalloc<EntDesc>(s, s->h_ents_adj.size(), &ce);
   if (nodal) {
     s->blockM = dalloc<double>(s, (size_t)s->ng.nblocks * Ssz * Ssz, &ce);
-    s->Ufine = dalloc<double>(s, (size_t)s->Ns * N, &ce);
-    s->Lfine = dalloc<double>(s, (size_t)s->Ns * N, &ce);
+    s->blockMT = dalloc<double>(s, (size_t)s->ng.nblocks * Ssz * Ssz, &ce);
     s->ones = dalloc<double>(s, N, &ce);
     s->qpt = dalloc<double>(s, qpt.size(), &ce);
   }
@@ -1145,10 +1142,8 @@ int run_jtvec_nodal(msfv_session* s, const double* w, double* out, bool fixed_ba
   }
   {
     PhaseScope ps(s, PH_GRAD);
-    launch_prolong_full(g, s->Pw, s->t, s->Ns, s->Ufine, st);
-    launch_prolong_full(g, s->Pw, s->lam, s->Ns, s->Lfine, st);
-    launch_nodal_grad(g, s->ng, s->Ufine, s->Lfine, s->Ns, s->sig, s->gT, out, st);
-    s->launches += 4;
+    launch_nodal_grad(g, s->ng, s->Pw, s->t, s->lam, s->Ns, s->blockMT, s->sig, s->gT, out, st);
+    s->launches += 3;
   }
   return check_launch(s, "msfv_jtvec");
 }

@@ -111,3 +111,42 @@ def test_served_request_matches_oracle(dev):
     sto = orc.forward(m)
     _, gref = orc.misfit_gradient(sto, d_obs.cpu().numpy())
     assert rel(r0.result[0], sto['d']) < TOL and rel(r0.result[1], gref) < TOL
+
+
+def test_batch_and_autograd_carry_the_variants(dev):
+    """A graph batch mixing a plain session, one with source bases and one of the nodal
+    variant gives each the bits it gets alone; the autograd binding's gradient on the
+    variants matches their oracles."""
+    from oracle.galerkin_oracle import NodalOracle
+    from paper_1707_07598_gb300.autograd import misfit
+    from paper_1707_07598_gb300.msfv import Batch, Session
+    probs = [W.make_problem((16, 16, 16), 8, 3, 20, seed=170, top_layer=True),
+             W.make_problem((16, 16, 16), 4, 3, 20, seed=171, top_layer=False, source_bases=True),
+             W.make_problem((16, 16, 16), 4, 3, 20, seed=172, top_layer=False, nodal=True)]
+    ms, dobs, sessions, refs = [], [], [], []
+    for k, prob in enumerate(probs):
+        m = W.gaussian_random_field(prob.n, 0.2, 180 + k)
+        orc = NodalOracle(prob) if prob.nodal else Oracle(prob)
+        st = orc.forward(m)
+        d_obs = st['d'] * 1.02
+        refs.append((st['d'], orc.misfit_gradient(st, d_obs)[1]))
+        ms.append(torch.from_numpy(m).to(dev))
+        dobs.append(torch.from_numpy(d_obs).to(dev))
+        sessions.append(Session(prob, stream=torch.cuda.Stream(dev)))
+    b = Batch(sessions, ms, dobs)
+    b.run()
+    b.check()
+    for k, prob in enumerate(probs):
+        assert rel(b.d_pred[k].cpu().numpy(), refs[k][0]) < TOL
+        assert rel(b.grad[k].cpu().numpy(), refs[k][1]) < TOL
+        s = Session(prob)
+        d = s.forward(ms[k])
+        _, g = s.adjoint(dobs[k], want_phi=False)
+        assert torch.equal(d, b.d_pred[k]) and torch.equal(g, b.grad[k])
+        mm = ms[k].clone().requires_grad_(True)
+        misfit(mm, dobs[k], s).backward()
+        assert rel(mm.grad.cpu().numpy(), refs[k][1]) < TOL
+        s.close()
+    b.close()
+    for s in sessions:
+        s.close()
