@@ -244,7 +244,8 @@ const char* msfv_batch_last_error(const msfv_batch_t* b);
  * of 128 or 256 threads per entity -- on this session's problem at the model m_dev
  * (device, N doubles; NULL = m = 0) and keeps the fastest for the session and for later
  * sessions of the same entity shapes in this process.  variants_out (host, 4 ints, may
- * be NULL) receives the chosen shape per class index 1..dim; ms_out (host, 16 doubles,
+ * be NULL) receives the chosen shape per class index 1..dim (-1 for a class that runs the
+ * mixed-precision kernel, which has one shape); ms_out (host, 16 doubles,
  * may be NULL) the best time of shape v for class k at 4*(k-1)+v (-1: not run).
  * Synchronises the stream; the session must run msfv_forward again before derivative
  * calls.  MSFV_LOCAL_VARIANT=0..3 at msfv_setup forces a shape for every class.  Not

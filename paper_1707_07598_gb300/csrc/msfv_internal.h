@@ -167,6 +167,17 @@ void launch_zt(const DevGeom& g, const double* t, const double* zc, int Ns, int 
                const int64_t* ru_cell, double* ZT, cudaStream_t s);
 void launch_grad(const DevGeom& g, const double* T, const double* Dl, const double* Pw,
                  const double* Lam, const double* gTloc, double* grad, cudaStream_t s);
+// ---- mixed-precision top-dimensional local problems (FP32 factor, FP64 refinement) ----
+bool mixed_fits(const LocalLaunch& L);
+void launch_mixed_forward(const DevGeom& g, const LocalLaunch& L, const double* T, double* Pw,
+                          float* fac32, int* status, cudaStream_t s);
+void launch_mixed_adjoint(const DevGeom& g, const LocalLaunch& L, const double* T, const double* Pw,
+                          const float* fac32, const double* Lam, const int* rec_p, const int* rec_u,
+                          const double* ZT, double* MU, double* gTloc, cudaStream_t s);
+void launch_mixed_tangent(const DevGeom& g, const LocalLaunch& L, const double* Top,
+                          const double* T, const double* Dl, const double* v, const double* Pw,
+                          const float* fac32, double* dPw, cudaStream_t s);
+
 // ---- source bases (Sec. 3.2) ---------------------------------------------------------
 // A "slot" is one (entity, source) pair in the support of that source's basis: the
 // entity holding a source end and every entity whose closure contains it.  The values

@@ -93,6 +93,9 @@ struct msfv_session {
   int* local_ctr = nullptr;         // work counters of the persistent local kernels
   long long local_scratch_n = 0;    // doubles of local_scratch
   bool recompute = false;           // local factors recomputed by the derivative kernels
+  // top-dimensional local problems in mixed precision (FP32 factor, FP64 refinement)
+  bool mixed_top = false;
+  float* fac32 = nullptr;
   // Gauss-Newton driver workspace (allocated by the first msfv_gn_step)
   double *gn_g = nullptr, *gn_x = nullptr, *gn_res = nullptr, *gn_p = nullptr, *gn_q = nullptr,
          *gn_m = nullptr, *gn_jp = nullptr, *gn_part = nullptr, *gn_sc = nullptr;
@@ -784,6 +787,22 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     return fail(nullptr, MSFV_ERR_OOM,
                 "the nodal variant needs the stored local factors, which exceed hbm_budget_bytes");
   }
+  // mixed precision for the top-dimensional class (MSFV_LOCAL_PRECISION=mixed at setup)
+  // when its factors can be stored and its window fits in shared memory: its factors are
+  // then stored in FP32 only, the lower classes' in FP64.  Off by default: on a GB300 the
+  // FP64 kernels are still faster (7.0 against 9.3 ms for the 128^3 interiors)
+  long long fac_lower = 0;
+  for (int k = 1; k < d; ++k)
+    for (const auto& e : s->h_ents[k]) fac_lower += (long long)e.n * (e.b + 1);
+  bool mixed_ok = false;
+  {
+    const char* prec = getenv("MSFV_LOCAL_PRECISION");
+    const bool want = prec && !strcmp(prec, "mixed");
+    mixed_ok = want && desc->factor_mode != 2 && !desc->source_bases &&
+               s->launch[d].n_ents > 0 && !s->launch[d].gw && mixed_fits(s->launch[d]);
+  }
+  if (mixed_ok)
+    s->fac_bytes = sizeof(double) * (size_t)fac_lower + sizeof(float) * (size_t)(fac_total - fac_lower);
   if (desc->source_bases && desc->factor_mode == 0 && desc->hbm_budget_bytes &&
       need + s->fac_bytes + scr > desc->hbm_budget_bytes) {
     delete s;
@@ -802,6 +821,12 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     scr = scratch_bytes();
   }
   if (s->recompute) s->fac_bytes = 0;
+  s->mixed_top = mixed_ok && !s->recompute;
+  if (s->mixed_top) {
+    // top-class factor offsets become offsets into the FP32 store
+    for (auto& e : s->h_ents[d]) e.fac -= fac_lower;
+    for (auto& e : s->h_ents_adj) e.fac -= fac_lower;
+  }
   need += s->fac_bytes + scr + sizeof(int) * 12;
   if (desc->hbm_budget_bytes && need > desc->hbm_budget_bytes) {
     delete s;
@@ -813,7 +838,9 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   s->Pw = dalloc<double>(s, (size_t)N * Ssz, &ce);
   s->X = dalloc<double>(s, (size_t)N * Ssz, &ce);
   s->gT = dalloc<double>(s, (size_t)d * N, &ce);
-  if (!s->recompute) s->fac = dalloc<double>(s, (size_t)fac_total, &ce);
+  if (!s->recompute)
+    s->fac = dalloc<double>(s, (size_t)std::max(1LL, s->mixed_top ? fac_lower : fac_total), &ce);
+  if (s->mixed_top) s->fac32 = dalloc<float>(s, (size_t)(fac_total - fac_lower), &ce);
   if (scr) s->local_scratch = dalloc<double>(s, scr / sizeof(double), &ce);
   s->local_scratch_n = (long long)(scr / sizeof(double));
   s->local_ctr = dalloc<int>(s, 12, &ce);
@@ -1081,7 +1108,10 @@ int run_forward_nodal(msfv_session* s, const double* m, double* d_pred, double* 
   }
   if (s->launch[d].n_ents) {       // block-interior solves (A_II x_I = -A_IB x_B)
     PhaseScope ps(s, PH_INTERIOR);
-    launch_local_forward(g, s->launch[d], s->T, s->Pw, s->fac, s->status, st);
+    if (s->mixed_top)
+      launch_mixed_forward(g, s->launch[d], s->T, s->Pw, s->fac32, s->status, st);
+    else
+      launch_local_forward(g, s->launch[d], s->T, s->Pw, s->fac, s->status, st);
     s->launches += 1;
   }
   {
@@ -1136,8 +1166,12 @@ int run_jtvec_nodal(msfv_session* s, const double* w, double* out, bool fixed_ba
   }
   if (!fixed_basis && s->launch_adj.n_ents) {
     PhaseScope ps(s, PH_ADJ_INTERIOR);
-    launch_local_adjoint(g, s->launch_adj, s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u, s->ZT,
-                         s->X, s->gT, st);
+    if (s->mixed_top)
+      launch_mixed_adjoint(g, s->launch_adj, s->T, s->Pw, s->fac32, s->Lam, s->rec_p, s->rec_u,
+                           s->ZT, s->X, s->gT, st);
+    else
+      launch_local_adjoint(g, s->launch_adj, s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u,
+                           s->ZT, s->X, s->gT, st);
     s->launches += 1;
   }
   {
@@ -1163,7 +1197,10 @@ int run_jvec_nodal(msfv_session* s, const double* v, double* jv) {
     // the shared tangent kernel forms dT = Dl v_lo + (T - Dl) v_hi; with T = Dl = dw
     // and v = 1 that is dw (T itself is used elsewhere in it only against the boundary
     // tangents, which are zero: block boundaries carry fixed Lagrange data)
-    launch_local_tangent(g, s->launch[d], dW, dW, s->ones, s->Pw, s->fac, s->X, st);
+    if (s->mixed_top)
+      launch_mixed_tangent(g, s->launch[d], s->T, dW, dW, s->ones, s->Pw, s->fac32, s->X, st);
+    else
+      launch_local_tangent(g, s->launch[d], dW, dW, s->ones, s->Pw, s->fac, s->X, st);
     s->launches += 1;
   }
   launch_galerkin(g, s->ng, s->sig, v, s->Pw, s->X, s->blockM, s->dAc, st);
@@ -1196,7 +1233,10 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
   }
   for (int k = 1; k <= d; ++k) {
     PhaseScope ps(s, k == d ? PH_INTERIOR : (k == 1 ? PH_EDGE : PH_FACE));
-    launch_local_forward(g, s->launch[k], s->T, s->Pw, s->fac, s->status, st);
+    if (k == d && s->mixed_top)
+      launch_mixed_forward(g, s->launch[k], s->T, s->Pw, s->fac32, s->status, st);
+    else
+      launch_local_forward(g, s->launch[k], s->T, s->Pw, s->fac, s->status, st);
     s->launches += s->launch[k].n_ents ? 1 : 0;
   }
   if (s->src_nslots) {
@@ -1270,8 +1310,12 @@ int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = 
   }
   for (int k = d; k >= 1 && !fixed_basis; --k) {
     PhaseScope ps(s, k == d ? PH_ADJ_INTERIOR : (k == 1 ? PH_ADJ_EDGE : PH_ADJ_FACE));
-    launch_local_adjoint(g, s->launch[k], s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u, s->ZT,
-                         s->X, s->gT, st);
+    if (k == d && s->mixed_top)
+      launch_mixed_adjoint(g, s->launch[k], s->T, s->Pw, s->fac32, s->Lam, s->rec_p, s->rec_u,
+                           s->ZT, s->X, s->gT, st);
+    else
+      launch_local_adjoint(g, s->launch[k], s->T, s->Pw, s->fac, s->Lam, s->rec_p, s->rec_u,
+                           s->ZT, s->X, s->gT, st);
     s->launches += s->launch[k].n_ents ? 1 : 0;
   }
   if (s->src_nslots) {
@@ -1301,7 +1345,10 @@ int run_jvec(msfv_session* s, const double* v, double* jv) {
   PhaseScope ps(s, PH_TANGENT);
   cudaMemsetAsync(s->X, 0, sizeof(double) * (size_t)g.N * g.S, st);
   for (int k = 1; k <= d; ++k) {
-    launch_local_tangent(g, s->launch[k], s->T, Dl, v, s->Pw, s->fac, s->X, st);
+    if (k == d && s->mixed_top)
+      launch_mixed_tangent(g, s->launch[k], s->T, s->T, Dl, v, s->Pw, s->fac32, s->X, st);
+    else
+      launch_local_tangent(g, s->launch[k], s->T, Dl, v, s->Pw, s->fac, s->X, st);
     s->launches += s->launch[k].n_ents ? 1 : 0;
   }
   for (int k = 1; k <= d && s->src_nslots; ++k) {
@@ -1821,6 +1868,10 @@ extern "C" int msfv_autotune(msfv_session_t* s, const double* m_dev, int* varian
     LocalLaunch& L = s->launch[k];
     if (variants_out) variants_out[k] = L.variant;
     if (L.n_ents == 0) continue;
+    if (k == g.d && s->mixed_top) {   // mixed-precision class: one kernel shape
+      if (variants_out) variants_out[k] = -1;
+      continue;
+    }
     int best = L.variant;
     float best_ms = 1e30f;
     for (int v = 0; v < kLocalVariants; ++v) {

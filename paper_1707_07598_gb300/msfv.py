@@ -261,6 +261,9 @@ class Session:
         self._check(self._lib.msfv_autotune(self._h, _ptr(m) if m is not None else None, var, ms))
         out = {}
         for k in range(1, self.dim + 1):
+            if var[k] < 0:      # the mixed-precision top class has a single kernel shape
+                out[k] = ("mixed", {})
+                continue
             times = {self.VARIANTS[v]: ms[4 * (k - 1) + v] for v in range(4) if ms[4 * (k - 1) + v] >= 0}
             out[k] = (self.VARIANTS[var[k]], times)
         return out

@@ -331,6 +331,8 @@ def test_autotune_picks_a_shape_and_stays_exact(dev):
     res = s.autotune(torch.from_numpy(m).to(dev))
     assert set(res) == {1, 2, 3}
     for k, (choice, times) in res.items():
+        if choice == "mixed":       # mixed-precision interiors: nothing to choose
+            continue
         assert choice in times and times[choice] == min(times.values())
     orc = Oracle(prob)
     st = orc.forward(m)
@@ -437,4 +439,43 @@ def test_multigrid_solver_variants_match_oracle(dev, monkeypatch, variant, n, c,
     assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
     info = s.info()
     assert 0 < info["coarse_iters"] < 100 and 0 < info["coarse_iters_T"] < 100
+    s.close()
+
+
+@pytest.mark.parametrize("n,c,ns,nr", [((16, 16, 16), 8, 3, 20), ((24, 16, 16), 8, 4, 30),
+                                       ((9, 9, 6), 3, 2, 7), ((32, 32), 8, 2, 16),
+                                       ((64, 64, 64), 8, 8, 64)])
+def test_mixed_precision_interiors_match_oracle(dev, monkeypatch, n, c, ns, nr):
+    """MSFV_LOCAL_PRECISION=mixed: the top-dimensional local problems factored in FP32 and
+    solved with two FP64 refinement steps reach the same 1e-9 bar on d, u, the gradient,
+    J v and J^T w."""
+    monkeypatch.setenv("MSFV_LOCAL_PRECISION", "mixed")
+    from paper_1707_07598_gb300.msfv import Session
+    prob = W.make_problem(n, c, ns, nr, seed=211, top_layer=len(n) == 3)
+    m = W.gaussian_random_field(n, 0.2, 212)
+    orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
+    assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
+    v = W.noise_like(prob.N, 1.0, 213)
+    w = W.noise_like((prob.n_src, prob.n_rec), 1.0, 214)
+    assert rel(s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy(), orc.jvec(st, v)) < TOL
+    assert rel(s.jtvec(torch.from_numpy(w).to(dev)).cpu().numpy(), orc.jtvec(st, w)) < TOL
+    s.close()
+
+
+def test_mixed_precision_nodal_variant(dev, monkeypatch):
+    monkeypatch.setenv("MSFV_LOCAL_PRECISION", "mixed")
+    from oracle.galerkin_oracle import NodalOracle
+    from paper_1707_07598_gb300.msfv import Session
+    prob = W.make_problem((16, 16, 16), 4, 3, 20, seed=221, top_layer=False, nodal=True)
+    m = W.gaussian_random_field(prob.n, 0.2, 222)
+    orc = NodalOracle(prob)
+    st = orc.forward(m)
+    d_obs = st['d'] * 1.02
+    _, g_ref = orc.misfit_gradient(st, d_obs)
+    s = Session(prob)
+    d = s.forward(torch.from_numpy(m).to(dev)).cpu().numpy()
+    _, g = s.adjoint(torch.from_numpy(d_obs).to(dev))
+    v = W.noise_like(prob.N, 1.0, 223)
+    assert rel(d, st['d']) < TOL and rel(g.cpu().numpy(), g_ref) < TOL
+    assert rel(s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy(), orc.jvec(st, v)) < TOL
     s.close()
