@@ -146,23 +146,56 @@ __device__ __forceinline__ double apply_row(const DevGeom& g, const MEnt& E,
 }
 
 // FP32 solve of one column (n values at D) with the factor F (column j at j*B1), both in
-// shared memory; one warp
+// shared memory; one warp.  Both sweeps go by blocks of 8 rows: the block's triangle is
+// solved through shuffles, the rest of the band by all lanes at once.
 __device__ void msolve(const float* F, float* D, int n, int b, int lane) {
+  const unsigned full = 0xffffffffu;
   const int B1 = b + 1;
-  for (int j = 0; j < n; ++j) {               // L y = r, column sweep
-    const float vj = D[j];
-    const float* col = F + j * B1;
-    for (int q = lane + 1; q <= b && j + q < n; q += 32) D[j + q] = fmaf(-col[q], vj, D[j + q]);
+  for (int j0 = 0; j0 < n; j0 += 8) {          // L y = r
+    const int m = min(8, n - j0);
+    float y = (lane < m) ? D[j0 + lane] : 0.0f;
+    for (int k = 0; k + 1 < m; ++k) {
+      const float yk = __shfl_sync(full, y, k);
+      if (lane > k && lane < m && lane - k <= b) y = fmaf(-F[(j0 + k) * B1 + (lane - k)], yk, y);
+    }
+    if (lane < m) D[j0 + lane] = y;
+    float yb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) yb[k] = __shfl_sync(full, y, k);
+    const int r_end = min(n, j0 + m + b);
+    for (int r = j0 + m + lane; r < r_end; r += 32) {
+      float acc = D[r];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int off = r - (j0 + k);
+        if (k < m && off <= b) acc = fmaf(-F[(j0 + k) * B1 + off], yb[k], acc);
+      }
+      D[r] = acc;
+    }
     __syncwarp();
   }
   for (int p = lane; p < n; p += 32) D[p] *= F[p * B1];   // D^{-1}
   __syncwarp();
-  for (int j = n - 1; j >= 0; --j) {          // L^T x = w, row dot products
-    const float* col = F + j * B1;
+  const int nblk = (n + 7) / 8;
+  for (int blk = nblk - 1; blk >= 0; --blk) {  // L^T x = w
+    const int j0 = blk * 8, m = min(8, n - j0);
+    // the part of each block row's sum that reaches beyond the block: 4 lanes per row
+    const int rr = lane >> 2, part = lane & 3;
     float acc = 0.0f;
-    for (int q = lane + 1; q <= b && j + q < n; q += 32) acc = fmaf(col[q], D[j + q], acc);
-    acc = mwarp_sumf(acc);
-    if (lane == 0) D[j] -= acc;
+    if (rr < m) {
+      const int r = j0 + rr;
+      for (int k = j0 + m - r + part; k <= b && r + k < n; k += 4)
+        acc = fmaf(F[r * B1 + k], D[r + k], acc);
+    }
+    acc += __shfl_xor_sync(full, acc, 1);
+    acc += __shfl_xor_sync(full, acc, 2);
+    const float outside = __shfl_sync(full, acc, (lane & 7) * 4);
+    float x = (lane < m) ? D[j0 + lane] - outside : 0.0f;
+    for (int k = m - 1; k >= 1; --k) {
+      const float xk = __shfl_sync(full, x, k);
+      if (lane < k && k - lane <= b) x = fmaf(-F[(j0 + lane) * B1 + (k - lane)], xk, x);
+    }
+    if (lane < m) D[j0 + lane] = x;
     __syncwarp();
   }
 }
@@ -211,10 +244,22 @@ k_mix_fwd(DevGeom g, LocalLaunch L, const double* __restrict__ T, double* __rest
   const int nslot = 1 << g.d;
   const int nmax = L.nmax, B1max = L.bmax + 1;
   // layout: [ R : nmax*8 doubles ][ Lf : nmax*B1max floats ][ D : nmax*8 floats ]
+  //         [ pair table : bmax(bmax+1)/2 ushorts ]
   double* R = smem;
   float* Lf = reinterpret_cast<float*>(smem + (long long)nmax * 8);
   float* D = Lf + (long long)nmax * B1max;
+  unsigned short* tab = reinterpret_cast<unsigned short*>(D + (long long)nmax * 8);
   const int tid = threadIdx.x;
+  {
+    // pair q of the update triangle, ordered by r then k: (r << 8) | k, 0 <= k <= r < bmax
+    const int np = L.bmax * (L.bmax + 1) / 2;
+    for (int q = tid; q < np; q += kMixThreads) {
+      int r = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
+      while (r * (r + 1) / 2 > q) --r;
+      while ((r + 1) * (r + 2) / 2 <= q) ++r;
+      tab[q] = (unsigned short)((r << 8) | (q - r * (r + 1) / 2));
+    }
+  }
   for (;;) {
     const int eid = mnext(L.counter + 0, &s_next);
     if (eid >= L.n_ents) break;
@@ -275,12 +320,8 @@ k_mix_fwd(DevGeom g, LocalLaunch L, const double* __restrict__ T, double* __rest
         const int bj = min(b, n - 1 - j);
         const int npairs = bj * (bj + 1) / 2;
         for (int q = tid; q < npairs; q += kMixThreads) {
-          // pair q -> (r, k), 1 <= k <= r <= bj, ordered by r then k
-          int r = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
-          while (r * (r + 1) / 2 > q) --r;
-          while ((r + 1) * (r + 2) / 2 <= q) ++r;
-          const int k = q - r * (r + 1) / 2;
-          const int rr = r + 1, kk = k + 1;
+          const int e = tab[q];                    // (r, k), 1 <= k <= r <= bj
+          const int rr = (e >> 8) + 1, kk = (e & 255) + 1;
           const float lr = Lf[j * B1 + rr], lk = Lf[j * B1 + kk];
           Lf[(j + kk) * B1 + (rr - kk)] = fmaf(-lr * rd, lk, Lf[(j + kk) * B1 + (rr - kk)]);
         }
@@ -390,6 +431,15 @@ k_mix_adj(DevGeom g, LocalLaunch L, const double* __restrict__ T, const double* 
       double* o = MU + x * nslot + mnth_slot(slots, i);
       *o = first ? dx : *o + dx;
     });
+    // mu of the entity into shared memory (the residual buffer is free now) for the
+    // face terms
+    for (int k = tid; k < n * E.nvs; k += kMixThreads) {
+      const int i = k / n, p = k - (k / n) * n;
+      int xc[3];
+      mcoords(E, p, xc);
+      R[i * nmax + p] = MU[mcell(g, xc) * nslot + mnth_slot(slots, i)];
+    }
+    __syncthreads();
     // transmissibility gradient of the owned faces
     for (int p = tid; p < n; p += kMixThreads) {
       int xc[3];
@@ -404,10 +454,10 @@ k_mix_adj(DevGeom g, LocalLaunch L, const double* __restrict__ T, const double* 
           double acc = 0.0;
           for (int i = 0; i < E.nvs; ++i) {
             const int s = mnth_slot(E.slots, i);
-            const double mx = MU[x * nslot + s];
+            const double mx = R[i * nmax + p];
             double my = 0.0, py = 0.0;
             if (in) {
-              my = MU[y * nslot + s];
+              my = R[i * nmax + p + E.str[a]];
               py = Pw[y * nslot + s];
             } else {
               const int sp = mmapped_slot(s, a, +1);
@@ -422,7 +472,7 @@ k_mix_adj(DevGeom g, LocalLaunch L, const double* __restrict__ T, const double* 
           double acc = 0.0;
           for (int i = 0; i < E.nvs; ++i) {
             const int s = mnth_slot(E.slots, i);
-            const double mx = MU[x * nslot + s];
+            const double mx = R[i * nmax + p];
             const int sp = mmapped_slot(s, a, -1);
             const double py = (sp >= 0) ? Pw[y * nslot + sp] : 0.0;
             acc = fma(mx, Pw[x * nslot + s] - py, acc);
@@ -528,7 +578,7 @@ k_mix_tan(DevGeom g, LocalLaunch L, const double* __restrict__ Top, const double
 namespace {
 size_t fwd_smem(const LocalLaunch& L) {
   return sizeof(double) * (size_t)L.nmax * 8 + sizeof(float) * (size_t)L.nmax * (L.bmax + 1) +
-         sizeof(float) * (size_t)L.nmax * 8;
+         sizeof(float) * (size_t)L.nmax * 8 + sizeof(unsigned short) * (size_t)(L.bmax * (L.bmax + 1) / 2 + 8);
 }
 size_t der_smem(const LocalLaunch& L) { return fwd_smem(L); }
 int mix_grid(const void* fn, size_t sm, int n_ents) {
