@@ -78,7 +78,14 @@ typedef struct msfv_desc {
                                hbm_budget_bytes, then recompute; 1 store them (the
                                derivative calls reuse them); 2 recompute them in every
                                derivative call (adjoint / jvec / jtvec refactor each
-                               local problem; only per-thread-group scratch is kept) */
+                               local problem; only per-thread-group scratch is kept).
+                               With the environment variable MSFV_LOCAL_PRECISION=mixed
+                               at msfv_setup, stored factors of the top-dimensional
+                               local problems are kept in FP32 and every solve with
+                               them is refined twice in FP64 (results to FP64
+                               rounding); that needs stored factors, no source bases,
+                               and a band that fits in shared memory (c <= 8 in 3D),
+                               otherwise the FP64 kernels run                          */
   size_t hbm_budget_bytes;  /* 0 = no limit; else setup fails with MSFV_ERR_OOM when
                                the session workspace would exceed it                   */
   int source_bases;         /* 0: vertex bases only.  1: add one source basis per source
