@@ -103,12 +103,6 @@ __device__ __forceinline__ int mmapped_slot(int s, int a, int dir) {
   return bit ? -1 : s;
 }
 
-__device__ __forceinline__ double mwarp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 __device__ __forceinline__ float mwarp_sumf(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -37,12 +37,6 @@ __device__ __forceinline__ long long stride_of(const long long* st, int a) {
   return a == 0 ? st[0] : (a == 1 ? st[1] : st[2]);
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // sum of f(cell) over the cells sharing edge (x, x + e_a), restricted to the box
 // [lo, hi) of cell coordinates
 template <typename F>
