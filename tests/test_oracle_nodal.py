@@ -161,3 +161,47 @@ def test_identity_receivers_adaptive_matches_fixed_does_not():
     fd = np.sum(w * ref)
     assert abs(g_ad @ v - fd) <= 1e-10 * abs(fd)
     assert abs(g_fx @ v - fd) > 1e-4 * abs(fd)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_nodal_operator_converges_at_second_order(d):
+    """The nodal operator (reading R13: arithmetic edge averages of sigma, area/length
+    weights, no flux through the outer boundary) against -div(sigma grad u) = f for the
+    manufactured u = prod cos(pi x_a) and a smooth sigma, with f integrated over each
+    node's dual volume: the nodal error falls at second order.  This pins the geometric
+    factors and the averaging independently of the brute force, which shares the reading."""
+    import scipy.sparse.linalg as spla
+    errs = []
+    sizes = (8, 16, 32) if d == 2 else (4, 8, 16)
+    for n in sizes:
+        nn = (n,) * d
+        prob = W.Problem(n=nn, coarsen=1, src_pos=np.array([0]), src_neg=np.array([1]),
+                         src_amp=np.array([1.0]), rec_cell=np.array([0]), nodal=True)
+        o = NodalOracle(prob)
+        h = 1.0 / n
+        Xc = (o.Xc + 0.5) * h                       # cell centres
+        m = 0.5 * np.sin(2 * np.pi * Xc[:, 0]) * np.cos(np.pi * Xc[:, -1])
+        A = o.operator(o.E @ np.exp(m))
+        Xn = o.Xn * h                               # node positions
+        # sigma and its gradient at the nodes from the same analytic model
+        s_m = 0.5 * np.sin(2 * np.pi * Xn[:, 0]) * np.cos(np.pi * Xn[:, -1])
+        sig = np.exp(s_m)
+        dm = np.zeros_like(Xn)
+        dm[:, 0] += np.pi * np.cos(2 * np.pi * Xn[:, 0]) * np.cos(np.pi * Xn[:, -1])
+        dm[:, -1] += -0.5 * np.pi * np.sin(2 * np.pi * Xn[:, 0]) * np.sin(np.pi * Xn[:, -1])
+        u = np.prod(np.cos(np.pi * Xn), axis=1)
+        grad_u = np.stack([-np.pi * np.sin(np.pi * Xn[:, a]) *
+                           np.prod(np.cos(np.pi * np.delete(Xn, a, axis=1)), axis=1)
+                           for a in range(d)], axis=1)
+        lap_u = -d * np.pi ** 2 * u
+        f = -(sig * lap_u + sig * np.sum(dm * grad_u, axis=1))   # -div(sigma grad u)
+        vol = np.prod(np.where((o.Xn == 0) | (o.Xn == n), 0.5, 1.0), axis=1) * h ** d
+        q = f * vol
+        q -= (q.sum() / vol.sum()) * vol            # compatible with the Neumann problem
+        keep = np.arange(1, o.Nn)
+        uh = np.zeros(o.Nn)
+        uh[keep] = spla.spsolve(A[keep][:, keep].tocsc(), q[keep])
+        e = (uh - uh.mean()) - (u - u.mean())
+        errs.append(np.abs(e).max())
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(rates) >= 1.8, (errs, rates)
