@@ -157,7 +157,20 @@ __device__ void msolve(const float* F, float* D, int n, int b, int lane) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) yb[k] = __shfl_sync(full, y, k);
     const int r_end = min(n, j0 + m + b);
-    for (int r = j0 + m + lane; r < r_end; r += 32) {
+    // rows j0+8 .. j0+b take all 8 block columns: entry (r, j0+k) of L sits at
+    // F[j0*B1 + (r-j0) + k*b], no bounds tests
+    const int fast_end = (m == 8) ? min(r_end, j0 + b + 1) : j0 + m;
+    {
+      const float* f0 = F + j0 * B1 - j0;
+      for (int r = j0 + m + lane; r < fast_end; r += 32) {
+        const float* f = f0 + r;
+        float acc = D[r];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = fmaf(-f[k * b], yb[k], acc);
+        D[r] = acc;
+      }
+    }
+    for (int r = max(fast_end, j0 + m) + lane; r < r_end; r += 32) {
       float acc = D[r];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
