@@ -31,7 +31,12 @@
  *    msfv_last_error(session) (or msfv_last_error(NULL) when no session exists)
  *    gives a one-line message.  No call throws and there is no CPU fallback:
  *    without a usable GPU the calls fail with MSFV_ERR_CUDA.
- *  - All arithmetic is IEEE FP64.
+ *  - All arithmetic is IEEE FP64, except with MSFV_LOCAL_PRECISION=mixed (opt-in), where
+ *    the top-dimensional local factors are FP32 and every solve with them is refined
+ *    to FP64 accuracy.
+ *  - Two additions beside the cell-centred MSFV path, chosen in the descriptor:
+ *    source bases (Sec. 3.2, source_bases = 1) and the paper's own nodal Galerkin
+ *    discretisation (discretization = 1).
  *  - Numerical failures (a non-positive local pivot, e.g. from a NaN model value; a
  *    singular or unconverged coarse solve) are recorded on the device and reported as
  *    MSFV_ERR_NUMERIC by the next call that reads the status (msfv_adjoint with phi_host,
@@ -126,7 +131,10 @@ int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t** out);
  * and the predicted data d_pred[j*Nr+i] = u_j(rec_cell[i]).
  *   m_dev       N doubles, log-conductivity per cell (read only)
  *   d_pred_dev  Ns*Nr doubles (written)
- *   u_dev       NULL, or Ns*N doubles receiving the fields u_j = P t_j
+ *   u_dev       NULL, or Ns*N doubles receiving the fields u_j = P t_j (+ C_j with
+ *               source bases); in the nodal variant Ns*(n0+1)(n1+1)(n2+1) node values
+ *               u_j = S t_j
+ * N is the number of cells in both discretisations (m and every gradient live on cells).
  * The session keeps P, the local factors and t for later derivative calls. */
 int msfv_forward(msfv_session_t* s, const double* m_dev, double* d_pred_dev, double* u_dev);
 
