@@ -139,71 +139,99 @@ __device__ __forceinline__ double apply_row(const DevGeom& g, const MEnt& E,
   return acc;
 }
 
-// FP32 solve of one column (n values at D) with the factor F (column j at j*B1), both in
-// shared memory; one warp.  Both sweeps go by blocks of 8 rows: the block's triangle is
-// solved through shuffles, the rest of the band by all lanes at once.
-__device__ void msolve(const float* F, float* D, int n, int b, int lane) {
+// FP32 solve of all right-hand sides at once, D[p*8 + i] (8 columns, unused ones zero),
+// with the factor F (column j at j*B1), both in shared memory; all threads of the CTA.
+// Both sweeps go by blocks of 8 rows.  Forward: warp 0 solves the block's unit triangle
+// for the 8 columns (lane: row l>>2, columns 2(l&3), 2(l&3)+1; the solved row k reaches
+// the others through shuffles), then every thread updates one (row, column pair) of the
+// band below the block.  Backward: the part of each block row's dot products that
+// reaches beyond the block is split over 4 lanes per (row, column) and reduced by
+// shuffles into S (64 floats); then warp 0 solves the block's transposed triangle.
+// Each factor entry is loaded once per block for all columns.
+__device__ void msolve_all(const float* F, float* D, float* S, int n, int b) {
   const unsigned full = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int B1 = b + 1;
-  for (int j0 = 0; j0 < n; j0 += 8) {          // L y = r
+  const int t = lane >> 2, c2 = 2 * (lane & 3);
+  for (int j0 = 0; j0 < n; j0 += 8) {                 // L y = r
     const int m = min(8, n - j0);
-    float y = (lane < m) ? D[j0 + lane] : 0.0f;
-    for (int k = 0; k + 1 < m; ++k) {
-      const float yk = __shfl_sync(full, y, k);
-      if (lane > k && lane < m && lane - k <= b) y = fmaf(-F[(j0 + k) * B1 + (lane - k)], yk, y);
-    }
-    if (lane < m) D[j0 + lane] = y;
-    float yb[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) yb[k] = __shfl_sync(full, y, k);
-    const int r_end = min(n, j0 + m + b);
-    // rows j0+8 .. j0+b take all 8 block columns: entry (r, j0+k) of L sits at
-    // F[j0*B1 + (r-j0) + k*b], no bounds tests
-    const int fast_end = (m == 8) ? min(r_end, j0 + b + 1) : j0 + m;
-    {
-      const float* f0 = F + j0 * B1 - j0;
-      for (int r = j0 + m + lane; r < fast_end; r += 32) {
-        const float* f = f0 + r;
-        float acc = D[r];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc = fmaf(-f[k * b], yb[k], acc);
-        D[r] = acc;
+    if (warp == 0) {
+      float y0 = 0.0f, y1 = 0.0f;
+      if (t < m) {
+        y0 = D[(j0 + t) * 8 + c2];
+        y1 = D[(j0 + t) * 8 + c2 + 1];
+      }
+      for (int k = 0; k + 1 < m; ++k) {
+        const float a0 = __shfl_sync(full, y0, 4 * k + (lane & 3));
+        const float a1 = __shfl_sync(full, y1, 4 * k + (lane & 3));
+        if (t > k && t < m && t - k <= b) {
+          const float f = F[(j0 + k) * B1 + (t - k)];
+          y0 = fmaf(-f, a0, y0);
+          y1 = fmaf(-f, a1, y1);
+        }
+      }
+      if (t < m) {
+        D[(j0 + t) * 8 + c2] = y0;
+        D[(j0 + t) * 8 + c2 + 1] = y1;
       }
     }
-    for (int r = max(fast_end, j0 + m) + lane; r < r_end; r += 32) {
-      float acc = D[r];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int off = r - (j0 + k);
-        if (k < m && off <= b) acc = fmaf(-F[(j0 + k) * B1 + off], yb[k], acc);
+    __syncthreads();
+    const int nrows = min(n, j0 + m + b) - (j0 + m);
+    for (int it = tid; it < nrows * 4; it += kMixThreads) {
+      const int r = j0 + m + (it >> 2), cc = 2 * (it & 3);
+      float acc0 = D[r * 8 + cc], acc1 = D[r * 8 + cc + 1];
+      for (int k = 0; k < m; ++k) {
+        const int off = r - j0 - k;
+        if (off <= b) {
+          const float f = F[(j0 + k) * B1 + off];
+          acc0 = fmaf(-f, D[(j0 + k) * 8 + cc], acc0);
+          acc1 = fmaf(-f, D[(j0 + k) * 8 + cc + 1], acc1);
+        }
       }
-      D[r] = acc;
+      D[r * 8 + cc] = acc0;
+      D[r * 8 + cc + 1] = acc1;
     }
-    __syncwarp();
+    __syncthreads();
   }
-  for (int p = lane; p < n; p += 32) D[p] *= F[p * B1];   // D^{-1}
-  __syncwarp();
-  const int nblk = (n + 7) / 8;
-  for (int blk = nblk - 1; blk >= 0; --blk) {  // L^T x = w
+  for (int k = tid; k < n * 8; k += kMixThreads) D[k] *= F[(k >> 3) * B1];   // D^{-1}
+  __syncthreads();
+  for (int blk = (n + 7) / 8 - 1; blk >= 0; --blk) {   // L^T x = w
     const int j0 = blk * 8, m = min(8, n - j0);
-    // the part of each block row's sum that reaches beyond the block: 4 lanes per row
-    const int rr = lane >> 2, part = lane & 3;
-    float acc = 0.0f;
-    if (rr < m) {
-      const int r = j0 + rr;
-      for (int k = j0 + m - r + part; k <= b && r + k < n; k += 4)
-        acc = fmaf(F[r * B1 + k], D[r + k], acc);
+    {
+      const int pair = tid >> 2, part = tid & 3;       // 64 (row, column) pairs x 4 parts
+      const int row = pair >> 3, col = pair & 7;
+      float acc = 0.0f;
+      if (row < m) {
+        const int r = j0 + row;
+        for (int k = j0 + m - r + part; k <= b && r + k < n; k += 4)
+          acc = fmaf(F[r * B1 + k], D[(r + k) * 8 + col], acc);
+      }
+      acc += __shfl_xor_sync(full, acc, 1);
+      acc += __shfl_xor_sync(full, acc, 2);
+      if (part == 0) S[pair] = acc;
     }
-    acc += __shfl_xor_sync(full, acc, 1);
-    acc += __shfl_xor_sync(full, acc, 2);
-    const float outside = __shfl_sync(full, acc, (lane & 7) * 4);
-    float x = (lane < m) ? D[j0 + lane] - outside : 0.0f;
-    for (int k = m - 1; k >= 1; --k) {
-      const float xk = __shfl_sync(full, x, k);
-      if (lane < k && k - lane <= b) x = fmaf(-F[(j0 + lane) * B1 + (k - lane)], xk, x);
+    __syncthreads();
+    if (warp == 0) {
+      float x0 = 0.0f, x1 = 0.0f;
+      if (t < m) {
+        x0 = D[(j0 + t) * 8 + c2] - S[t * 8 + c2];
+        x1 = D[(j0 + t) * 8 + c2 + 1] - S[t * 8 + c2 + 1];
+      }
+      for (int k = m - 1; k >= 1; --k) {
+        const float a0 = __shfl_sync(full, x0, 4 * k + (lane & 3));
+        const float a1 = __shfl_sync(full, x1, 4 * k + (lane & 3));
+        if (t < k && k - t <= b) {
+          const float f = F[(j0 + t) * B1 + (k - t)];
+          x0 = fmaf(-f, a0, x0);
+          x1 = fmaf(-f, a1, x1);
+        }
+      }
+      if (t < m) {
+        D[(j0 + t) * 8 + c2] = x0;
+        D[(j0 + t) * 8 + c2 + 1] = x1;
+      }
     }
-    if (lane < m) D[j0 + lane] = x;
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -212,28 +240,25 @@ __device__ void msolve(const float* F, float* D, int n, int b, int lane) {
 // into the caller's FP64 store through put(i, p, dx, first)
 template <typename Put>
 __device__ void mixed_solve(const DevGeom& g, const MEnt& E, const double* __restrict__ T,
-                            const float* F, double* R, float* D, int nmax, Put put) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+                            const float* F, double* R, float* D, float* S, int nmax, Put put) {
+  const int tid = threadIdx.x;
   const int n = E.n, nv = E.nvs;
   for (int it = 0; it < 3; ++it) {
-    for (int k = tid; k < n * nv; k += kMixThreads) {
-      const int i = k / n, p = k - (k / n) * n;
-      D[i * nmax + p] = (float)R[i * nmax + p];
+    for (int k = tid; k < n * 8; k += kMixThreads) {
+      const int p = k >> 3, i = k & 7;
+      D[k] = i < nv ? (float)R[i * nmax + p] : 0.0f;
     }
     __syncthreads();
-    if (warp < nv) msolve(F, D + warp * nmax, n, E.b, lane);
-    __syncthreads();
+    msolve_all(F, D, S, n, E.b);
     for (int k = tid; k < n * nv; k += kMixThreads) {
       const int i = k / n, p = k - (k / n) * n;
-      const double dx = (double)D[i * nmax + p];
+      const double dx = (double)D[p * 8 + i];
       int xc[3];
       mcoords(E, p, xc);
       const long long x = mcell(g, xc);
       put(i, x, dx, it == 0);
-      if (it < 2) {
-        const float* Di = D + i * nmax;
-        R[i * nmax + p] -= apply_row(g, E, T, p, xc, x, [&](int q) { return (double)Di[q]; });
-      }
+      if (it < 2)
+        R[i * nmax + p] -= apply_row(g, E, T, p, xc, x, [&](int q) { return (double)D[q * 8 + i]; });
     }
     __syncthreads();
   }
@@ -255,7 +280,8 @@ k_mix_fwd(DevGeom g, LocalLaunch L, const double* __restrict__ T, double* __rest
   double* R = smem;
   float* Lf = reinterpret_cast<float*>(smem + (long long)nmax * 8);
   float* D = Lf + (long long)nmax * B1max;
-  unsigned short* tab = reinterpret_cast<unsigned short*>(D + (long long)nmax * 8);
+  float* S = D + (long long)nmax * 8;
+  unsigned short* tab = reinterpret_cast<unsigned short*>(S + 64);
   const int tid = threadIdx.x;
   {
     // pair q of the update triangle, ordered by r then k: (r << 8) | k, 0 <= k <= r < bmax
@@ -359,7 +385,7 @@ k_mix_fwd(DevGeom g, LocalLaunch L, const double* __restrict__ T, double* __rest
     }
     __syncthreads();
     const unsigned slots = E.slots;
-    mixed_solve(g, E, T, Lf, R, D, nmax, [&](int i, long long x, double dx, bool first) {
+    mixed_solve(g, E, T, Lf, R, D, S, nmax, [&](int i, long long x, double dx, bool first) {
       double* o = Pw + x * nslot + mnth_slot(slots, i);
       *o = first ? dx : *o + dx;
     });
@@ -379,6 +405,7 @@ k_mix_adj(DevGeom g, LocalLaunch L, const double* __restrict__ T, const double* 
   double* R = smem;
   float* Lf = reinterpret_cast<float*>(smem + (long long)nmax * 8);
   float* D = Lf + (long long)nmax * B1max;
+  float* S = D + (long long)nmax * 8;
   const int tid = threadIdx.x;
   const int S3 = (g.d == 3) ? 27 : 9;
   for (;;) {
@@ -434,7 +461,7 @@ k_mix_adj(DevGeom g, LocalLaunch L, const double* __restrict__ T, const double* 
     // mu of every slot goes straight to MU (the entity's own cells), where the lower
     // entities read it as seeds
     const unsigned slots = E.slots;
-    mixed_solve(g, E, T, Lf, R, D, nmax, [&](int i, long long x, double dx, bool first) {
+    mixed_solve(g, E, T, Lf, R, D, S, nmax, [&](int i, long long x, double dx, bool first) {
       double* o = MU + x * nslot + mnth_slot(slots, i);
       *o = first ? dx : *o + dx;
     });
@@ -506,6 +533,7 @@ k_mix_tan(DevGeom g, LocalLaunch L, const double* __restrict__ Top, const double
   double* R = smem;
   float* Lf = reinterpret_cast<float*>(smem + (long long)nmax * 8);
   float* D = Lf + (long long)nmax * B1max;
+  float* S = D + (long long)nmax * 8;
   const int tid = threadIdx.x;
   for (;;) {
     const int eid = mnext(L.counter + 2, &s_next);
@@ -574,7 +602,7 @@ k_mix_tan(DevGeom g, LocalLaunch L, const double* __restrict__ Top, const double
       }
     }
     const unsigned slots = E.slots;
-    mixed_solve(g, E, Top, Lf, R, D, nmax, [&](int i, long long x, double dx, bool first) {
+    mixed_solve(g, E, Top, Lf, R, D, S, nmax, [&](int i, long long x, double dx, bool first) {
       double* o = dPw + x * nslot + mnth_slot(slots, i);
       *o = first ? dx : *o + dx;
     });
@@ -585,7 +613,8 @@ k_mix_tan(DevGeom g, LocalLaunch L, const double* __restrict__ Top, const double
 namespace {
 size_t fwd_smem(const LocalLaunch& L) {
   return sizeof(double) * (size_t)L.nmax * 8 + sizeof(float) * (size_t)L.nmax * (L.bmax + 1) +
-         sizeof(float) * (size_t)L.nmax * 8 + sizeof(unsigned short) * (size_t)(L.bmax * (L.bmax + 1) / 2 + 8);
+         sizeof(float) * (size_t)(L.nmax * 8 + 64) +
+         sizeof(unsigned short) * (size_t)(L.bmax * (L.bmax + 1) / 2 + 8);
 }
 size_t der_smem(const LocalLaunch& L) { return fwd_smem(L); }
 int mix_grid(const void* fn, size_t sm, int n_ents) {
