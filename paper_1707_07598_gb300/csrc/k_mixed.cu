@@ -91,22 +91,12 @@ __device__ __forceinline__ int mnth_slot(unsigned slots, int i) {
   return __ffs(slots) - 1;
 }
 
-__device__ __forceinline__ int mslot_index(unsigned slots, int s) {
-  return __popc(slots & ((1u << s) - 1u));
-}
-
 // slot of a Dirichlet neighbour across tangential axis a (it sits on a vertex
 // coordinate of a): the entity's hi vertex for dir +1, its lo vertex for dir -1
 __device__ __forceinline__ int mmapped_slot(int s, int a, int dir) {
   const int bit = (s >> a) & 1;
   if (dir > 0) return bit ? (s & ~(1 << a)) : -1;
   return bit ? -1 : s;
-}
-
-__device__ __forceinline__ float mwarp_sumf(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
 }
 
 __device__ __forceinline__ int mnext(int* counter, int* s_next) {
@@ -116,25 +106,43 @@ __device__ __forceinline__ int mnext(int* counter, int* s_next) {
   return *s_next;
 }
 
-// (A x)_p for the entity operator (FP64), x given per local index by xv(q)
+// Per local cell: its global index and, per axis a (4 bits at 4a), whether the face to
+// the + side exists (bit 0), its neighbour is in the entity (bit 1), the face to the
+// - side exists (bit 2), its neighbour is in the entity (bit 3).  Filled once per entity.
+__device__ __forceinline__ void cell_table(const DevGeom& g, const MEnt& E, int* cellx,
+                                           unsigned short* cmask) {
+  for (int p = threadIdx.x; p < E.n; p += kMixThreads) {
+    int xc[3];
+    mcoords(E, p, xc);
+    cellx[p] = (int)mcell(g, xc);
+    unsigned msk = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (E.lk[a] < 0) continue;
+      const int la = xc[a] - E.org[a];
+      unsigned bits = 0;
+      if (xc[a] + 1 < g.n[a]) bits |= 1u | ((la + 1 < E.len[a]) ? 2u : 0u);
+      if (xc[a] > 0) bits |= 4u | ((la > 0) ? 8u : 0u);
+      msk |= bits << (4 * a);
+    }
+    cmask[p] = (unsigned short)msk;
+  }
+}
+
+// (A x)_p from the cell table (FP64)
 template <typename F>
-__device__ __forceinline__ double apply_row(const DevGeom& g, const MEnt& E,
-                                            const double* __restrict__ T, int p, const int* xc,
-                                            long long x, F xv) {
+__device__ __forceinline__ double apply_row_t(const DevGeom& g, const MEnt& E,
+                                              const double* __restrict__ T, int p, long long x,
+                                              unsigned msk, F xv) {
   const double xp = xv(p);
   double acc = 0.0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (E.lk[a] < 0) continue;
-    const int la = xc[a] - E.org[a];
-    if (xc[a] + 1 < g.n[a]) {
-      const double t = tface(T, g, a, x);
-      acc = fma(t, xp - (la + 1 < E.len[a] ? xv(p + E.str[a]) : 0.0), acc);
-    }
-    if (xc[a] > 0) {
-      const double t = tface(T, g, a, x - gstride(g, a));
-      acc = fma(t, xp - (la > 0 ? xv(p - E.str[a]) : 0.0), acc);
-    }
+    const unsigned bits = (msk >> (4 * a)) & 15u;
+    if (bits & 1u) acc = fma(tface(T, g, a, x), xp - ((bits & 2u) ? xv(p + E.str[a]) : 0.0), acc);
+    if (bits & 4u)
+      acc = fma(tface(T, g, a, x - gstride(g, a)), xp - ((bits & 8u) ? xv(p - E.str[a]) : 0.0), acc);
   }
   return acc;
 }
@@ -240,7 +248,8 @@ __device__ void msolve_all(const float* F, float* D, float* S, int n, int b) {
 // into the caller's FP64 store through put(i, p, dx, first)
 template <typename Put>
 __device__ void mixed_solve(const DevGeom& g, const MEnt& E, const double* __restrict__ T,
-                            const float* F, double* R, float* D, float* S, int nmax, Put put) {
+                            const float* F, double* R, float* D, float* S, const int* cellx,
+                            const unsigned short* cmask, int nmax, Put put) {
   const int tid = threadIdx.x;
   const int n = E.n, nv = E.nvs;
   for (int it = 0; it < 3; ++it) {
@@ -250,15 +259,14 @@ __device__ void mixed_solve(const DevGeom& g, const MEnt& E, const double* __res
     }
     __syncthreads();
     msolve_all(F, D, S, n, E.b);
-    for (int k = tid; k < n * nv; k += kMixThreads) {
-      const int i = k / n, p = k - (k / n) * n;
-      const double dx = (double)D[p * 8 + i];
-      int xc[3];
-      mcoords(E, p, xc);
-      const long long x = mcell(g, xc);
+    for (int k = tid; k < n * 8; k += kMixThreads) {
+      const int p = k >> 3, i = k & 7;
+      if (i >= nv) continue;
+      const double dx = (double)D[k];
+      const long long x = cellx[p];
       put(i, x, dx, it == 0);
       if (it < 2)
-        R[i * nmax + p] -= apply_row(g, E, T, p, xc, x, [&](int q) { return (double)D[q * 8 + i]; });
+        R[i * nmax + p] -= apply_row_t(g, E, T, p, x, cmask[p], [&](int q) { return (double)D[q * 8 + i]; });
     }
     __syncthreads();
   }
@@ -281,7 +289,9 @@ k_mix_fwd(DevGeom g, LocalLaunch L, const double* __restrict__ T, double* __rest
   float* Lf = reinterpret_cast<float*>(smem + (long long)nmax * 8);
   float* D = Lf + (long long)nmax * B1max;
   float* S = D + (long long)nmax * 8;
-  unsigned short* tab = reinterpret_cast<unsigned short*>(S + 64);
+  int* cellx = reinterpret_cast<int*>(S + 64);
+  unsigned short* cmask = reinterpret_cast<unsigned short*>(cellx + nmax);
+  unsigned short* tab = cmask + ((nmax + 1) & ~1);
   const int tid = threadIdx.x;
   {
     // pair q of the update triangle, ordered by r then k: (r << 8) | k, 0 <= k <= r < bmax
@@ -385,7 +395,10 @@ k_mix_fwd(DevGeom g, LocalLaunch L, const double* __restrict__ T, double* __rest
     }
     __syncthreads();
     const unsigned slots = E.slots;
-    mixed_solve(g, E, T, Lf, R, D, S, nmax, [&](int i, long long x, double dx, bool first) {
+    cell_table(g, E, cellx, cmask);
+    __syncthreads();
+    mixed_solve(g, E, T, Lf, R, D, S, cellx, cmask, nmax,
+                [&](int i, long long x, double dx, bool first) {
       double* o = Pw + x * nslot + mnth_slot(slots, i);
       *o = first ? dx : *o + dx;
     });
@@ -406,6 +419,8 @@ k_mix_adj(DevGeom g, LocalLaunch L, const double* __restrict__ T, const double* 
   float* Lf = reinterpret_cast<float*>(smem + (long long)nmax * 8);
   float* D = Lf + (long long)nmax * B1max;
   float* S = D + (long long)nmax * 8;
+  int* cellx = reinterpret_cast<int*>(S + 64);
+  unsigned short* cmask = reinterpret_cast<unsigned short*>(cellx + nmax);
   const int tid = threadIdx.x;
   const int S3 = (g.d == 3) ? 27 : 9;
   for (;;) {
@@ -461,7 +476,10 @@ k_mix_adj(DevGeom g, LocalLaunch L, const double* __restrict__ T, const double* 
     // mu of every slot goes straight to MU (the entity's own cells), where the lower
     // entities read it as seeds
     const unsigned slots = E.slots;
-    mixed_solve(g, E, T, Lf, R, D, S, nmax, [&](int i, long long x, double dx, bool first) {
+    cell_table(g, E, cellx, cmask);
+    __syncthreads();
+    mixed_solve(g, E, T, Lf, R, D, S, cellx, cmask, nmax,
+                [&](int i, long long x, double dx, bool first) {
       double* o = MU + x * nslot + mnth_slot(slots, i);
       *o = first ? dx : *o + dx;
     });
@@ -534,6 +552,8 @@ k_mix_tan(DevGeom g, LocalLaunch L, const double* __restrict__ Top, const double
   float* Lf = reinterpret_cast<float*>(smem + (long long)nmax * 8);
   float* D = Lf + (long long)nmax * B1max;
   float* S = D + (long long)nmax * 8;
+  int* cellx = reinterpret_cast<int*>(S + 64);
+  unsigned short* cmask = reinterpret_cast<unsigned short*>(cellx + nmax);
   const int tid = threadIdx.x;
   for (;;) {
     const int eid = mnext(L.counter + 2, &s_next);
@@ -602,7 +622,10 @@ k_mix_tan(DevGeom g, LocalLaunch L, const double* __restrict__ Top, const double
       }
     }
     const unsigned slots = E.slots;
-    mixed_solve(g, E, Top, Lf, R, D, S, nmax, [&](int i, long long x, double dx, bool first) {
+    cell_table(g, E, cellx, cmask);
+    __syncthreads();
+    mixed_solve(g, E, Top, Lf, R, D, S, cellx, cmask, nmax,
+                [&](int i, long long x, double dx, bool first) {
       double* o = dPw + x * nslot + mnth_slot(slots, i);
       *o = first ? dx : *o + dx;
     });
@@ -613,8 +636,8 @@ k_mix_tan(DevGeom g, LocalLaunch L, const double* __restrict__ Top, const double
 namespace {
 size_t fwd_smem(const LocalLaunch& L) {
   return sizeof(double) * (size_t)L.nmax * 8 + sizeof(float) * (size_t)L.nmax * (L.bmax + 1) +
-         sizeof(float) * (size_t)(L.nmax * 8 + 64) +
-         sizeof(unsigned short) * (size_t)(L.bmax * (L.bmax + 1) / 2 + 8);
+         sizeof(float) * (size_t)(L.nmax * 8 + 64) + sizeof(int) * (size_t)L.nmax +
+         sizeof(unsigned short) * (size_t)(((L.nmax + 1) & ~1) + L.bmax * (L.bmax + 1) / 2 + 8);
 }
 size_t der_smem(const LocalLaunch& L) { return fwd_smem(L); }
 int mix_grid(const void* fn, size_t sm, int n_ents) {
