@@ -985,13 +985,14 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     if (ce == cudaSuccess) ce = upload(s->src_neg, sn, st);
     if (ce == cudaSuccess) ce = upload(s->src_amp, sa, st);
   }
+  std::vector<double> ones_h;   // lives until the stream synchronisation below
   if (nodal && ce == cudaSuccess) {
     ce = upload(s->qpt, qpt, st);
-    if (ce == cudaSuccess) ce = upload(s->ones, std::vector<double>((size_t)N, 1.0), st);
+    ones_h.assign((size_t)N, 1.0);
+    if (ce == cudaSuccess) ce = upload(s->ones, ones_h, st);
     // the coarse-stencil collapse of the cell-centred adjoint is not used: its array
     // stays zero so the shared local adjoint kernel adds nothing from it
     if (ce == cudaSuccess) ce = cudaMemsetAsync(s->Lam, 0, sizeof(double) * (size_t)Nc * S3, st);
-    if (ce == cudaSuccess) cudaStreamSynchronize(st);
   }
   if (s->src_nslots && ce == cudaSuccess) {
     ce = upload(s->src_slots, slots, st);
