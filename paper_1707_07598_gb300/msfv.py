@@ -134,7 +134,10 @@ class Session:
     """One MSFV problem (mesh, coarsening, sources, receivers) on the current GPU.
 
     Mirrors the C ABI: ``forward`` (steps a-e), ``adjoint`` (misfit and gradient),
-    ``jvec`` / ``jtvec`` (Sec. 4.3 sensitivities), ``solve_host``.
+    ``jvec`` / ``jtvec`` (Sec. 4.3 sensitivities), ``solve_host``.  ``prob.source_bases``
+    adds the source bases of Sec. 3.2; ``prob.nodal`` selects the nodal Galerkin
+    discretisation (fields of ``Nf`` node values per source; m and gradients stay on the
+    ``N`` cells).
     """
 
     def __init__(self, prob, stream=None, factor_mode: int = 0, hbm_budget_bytes: int = 0):
