@@ -93,3 +93,56 @@ def test_null_arguments(lib):
     assert lib.msfv_forward(None, None, None, None) == 1
     assert lib.msfv_destroy(None) == 0
     assert lib.msfv_phase_name(4).decode() == "basis_interiors"
+
+
+def _desc3(n, c, pos, neg, rec, **kw):
+    d = M._Desc()
+    d.dim = 3
+    for a in range(3):
+        d.n[a] = n[a]
+    d.coarsen = c
+    pos = np.asarray(pos, dtype=np.int64)
+    neg = np.asarray(neg, dtype=np.int64)
+    rec = np.asarray(rec, dtype=np.int64)
+    d.n_src = len(pos)
+    d.src_pos = pos.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.src_neg = neg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.src_amp = None
+    d.n_rec = len(rec)
+    d.rec_cell = rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.factor_mode = 0
+    d.hbm_budget_bytes = kw.get("budget", 1000)
+    d.source_bases = kw.get("sb", 0)
+    d.discretization = kw.get("disc", 0)
+    d._keep = (pos, neg, rec)
+    return d
+
+
+def test_host_tables_of_source_bases_and_nodal_variant_build_on_the_host(lib):
+    """Setup builds every host-side table (source-basis support, slots, side links to
+    the neighbouring entities, flux rows, receiver map; the nodal seed points and
+    block-interior subset) before it checks the budget.  With a tiny budget the call
+    runs that logic on the CPU and stops with MSFV_ERR_OOM: a broken side link would
+    surface as MSFV_ERR_ARG ("inconsistent dual-grid sides")."""
+    n, c = (16, 16, 16), 4                 # vertex coordinates 2, 6, 10, 14
+
+    def idx(x, y, z):
+        return x + 16 * (y + 16 * z)
+    # source ends on a vertex, dual edges, faces, interiors and partial boundary cells
+    pos = [idx(2, 6, 10), idx(4, 2, 6), idx(3, 6, 5), idx(4, 4, 4), idx(0, 15, 1)]
+    neg = [idx(6, 0, 2), idx(5, 5, 5), idx(4, 2, 7), idx(14, 14, 13), idx(15, 15, 15)]
+    rec = [idx(1, 2, 3), idx(4, 2, 6), idx(15, 15, 15)]
+    for kw, frag in [(dict(sb=1), "source bases need the stored local factors"),
+                     (dict(disc=1), "nodal variant needs the stored local factors")]:
+        d = _desc3(n, c, pos, neg, rec, **kw)
+        h = ctypes.c_void_p()
+        rc = lib.msfv_setup(ctypes.byref(d), None, ctypes.byref(h))
+        assert rc == 2 and not h.value, lib.msfv_last_error(None).decode()
+        assert frag in lib.msfv_last_error(None).decode()
+    # the nodal lattice has 17^3 nodes: a node index beyond the cell count is valid there
+    d = _desc3(n, c, [4500], [0], [17 ** 3 - 1], disc=1)
+    h = ctypes.c_void_p()
+    assert lib.msfv_setup(ctypes.byref(d), None, ctypes.byref(h)) == 2
+    d = _desc3(n, c, [17 ** 3], [0], [1], disc=1)
+    assert lib.msfv_setup(ctypes.byref(d), None, ctypes.byref(h)) == 1
+    assert "out of range" in lib.msfv_last_error(None).decode()
