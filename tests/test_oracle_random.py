@@ -73,3 +73,30 @@ def test_cell_centred_adjoint_identity(pm):
     w = rng.normal(size=(prob.n_src, prob.n_rec))
     lhs, rhs = np.sum(w * o.jvec(s_, v)), o.jtvec(s_, w) @ v
     assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + np.linalg.norm(w) * np.linalg.norm(v))
+
+
+@settings(max_examples=25, deadline=None, derandomize=True)
+@given(problems(nodal=True))
+def test_nodal_adjoint_identity(pm):
+    prob, m = pm
+    o = NodalOracle(prob)
+    s_ = o.forward(m)
+    rng = np.random.default_rng(2)
+    v = rng.normal(size=prob.N)
+    w = rng.normal(size=(prob.n_src, prob.n_rec))
+    lhs, rhs = np.sum(w * o.jvec(s_, v)), o.jtvec(s_, w) @ v
+    assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + np.linalg.norm(w) * np.linalg.norm(v))
+
+
+@settings(max_examples=20, deadline=None, derandomize=True)
+@given(problems())
+def test_cell_centred_jvec_complex_step(pm):
+    """J v (with or without source bases) against complex step of the brute force."""
+    prob, m = pm
+    if prob.N > 200:
+        return                                    # keep the dense complex step cheap
+    o = Oracle(prob)
+    s_ = o.forward(m)
+    v = np.random.default_rng(3).normal(size=prob.N)
+    ref = BF.jvec_complex_step(m, prob, v)
+    assert np.linalg.norm(o.jvec(s_, v) - ref) <= 1e-10 * max(np.linalg.norm(ref), 1e-300)
