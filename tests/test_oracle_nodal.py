@@ -205,3 +205,33 @@ def test_nodal_operator_converges_at_second_order(d):
         errs.append(np.abs(e).max())
     rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert min(rates) >= 1.8, (errs, rates)
+
+
+def test_constant_direction_leaves_the_lagrange_basis_unchanged():
+    """Sec. 4.4 uses a constant perturbation dm = -0.001 * 1.  The Lagrange-data basis is
+    invariant under a uniform scaling of sigma (the block problems are homogeneous in
+    sigma and their boundary data are fixed), so dS = 0 along it and the adaptive and
+    fixed-basis J v coincide; along a non-constant direction they differ."""
+    n, c = (12, 12, 6), 3
+    nn = tuple(v + 1 for v in n)
+    Nn = int(np.prod(nn))
+    prob = W.Problem(n=n, coarsen=c, src_pos=np.array([_node(nn, 2, 6, 6)]),
+                     src_neg=np.array([_node(nn, 10, 6, 6)]), src_amp=np.array([1.0]),
+                     rec_cell=np.arange(Nn, dtype=np.int64), nodal=True)
+    m = W.gaussian_random_field(n, 0.3, 17)
+    o = NodalOracle(prob)
+    st_ = o.forward(m)
+
+    def fixed_jv(v):
+        dA = o.operator(o.dweights(st_, v))
+        S = st_['S']
+        dt = o.coarse_solve(st_, -(S.T @ (dA @ st_['U'][0])))
+        return (S @ dt)[prob.rec_cell]
+
+    v0 = -0.001 * np.ones(prob.N)
+    ja = o.jvec(st_, v0)[0]
+    assert np.linalg.norm(ja - fixed_jv(v0)) <= 1e-12 * np.linalg.norm(ja)
+    X = np.stack(np.unravel_index(np.arange(prob.N), n[::-1])[::-1], axis=1)
+    v1 = 0.001 * np.sin(np.pi * (X[:, 0] + 0.5) / n[0])
+    j1 = o.jvec(st_, v1)[0]
+    assert np.linalg.norm(j1 - fixed_jv(v1)) > 1e-4 * np.linalg.norm(j1)
