@@ -362,11 +362,14 @@ def test_golden_oracle_outputs_are_reproduced():
     import json
     with open(os.path.join(GOLDEN, "oracle_tiny.json")) as f:
         gold = json.load(f)
+    from oracle.galerkin_oracle import NodalOracle
+    assert len(gold) >= 6 and any(c.get('sb') for c in gold) and any(c.get('nodal') for c in gold)
     for case in gold:
         prob = W.make_problem(tuple(case['n']), case['c'], case['ns'], case['nr'],
-                              seed=case['seed'], top_layer=False)
+                              seed=case['seed'], top_layer=False,
+                              source_bases=case.get('sb', False), nodal=case.get('nodal', False))
         m = W.gaussian_random_field(prob.n, case['corr'], case['seed'] + 2)
-        o = Oracle(prob)
+        o = NodalOracle(prob) if case.get('nodal') else Oracle(prob)
         st = o.forward(m)
         phi, g = o.misfit_gradient(st, np.array(case['d_obs']))
         assert np.allclose(st['d'], np.array(case['d']), rtol=1e-12, atol=1e-14)
