@@ -40,7 +40,9 @@
  *  - Numerical failures (a non-positive local pivot, e.g. from a NaN model value; a
  *    singular or unconverged coarse solve) are recorded on the device and reported as
  *    MSFV_ERR_NUMERIC by the next call that reads the status (msfv_adjoint with phi_host,
- *    msfv_solve_host, msfv_batch_check, msfv_gn_step); msfv_forward clears the record.
+ *    msfv_solve_host, msfv_batch_check, msfv_gn_step); an expired device-side wait
+ *    (msfv_set_wait_limit) is reported the same way as MSFV_ERR_TIMEOUT; msfv_forward
+ *    clears the record.
  */
 #ifndef MSFV_H
 #define MSFV_H
@@ -171,10 +173,10 @@ int msfv_solve_host(msfv_session_t* s, const double* m_host, const double* d_obs
                     double* d_pred_host, double* grad_host, double* phi_host);
 
 /* ---- allocation-free misfit (no counterpart in the paper) --------------------------
- * For callers that cannot allocate GPU memory where they need the data misfit: code
- * running inside a CUDA graph capture, a serving loop whose allocator must not grow, or
- * a host application that only lends its own buffers.  Such callers cannot create a
- * session (msfv_setup allocates), so this entry point needs none: it takes the data and
+ * For callers that cannot allocate GPU memory where they need the data misfit: a
+ * serving loop whose allocator must not grow, or a host application that only lends its
+ * own buffers.  Such callers cannot create a session (msfv_setup allocates), so this
+ * entry point needs none: it takes the data and
  * the outputs from the caller and computes, on the given stream,
  *   r_dev[i] = d_pred_dev[i] - d_obs_dev[i]   (skipped when r_dev is NULL)
  *   *phi_dev = 1/2 sum_i r_i^2                 (device double, written)
@@ -184,7 +186,8 @@ int msfv_solve_host(msfv_session_t* s, const double* m_host, const double* d_obs
  *   count   number of data values, 0 .. MSFV_MISFIT_STATIC_MAX; larger counts return
  *           MSFV_ERR_ARG and enqueue nothing
  * The first call on a device looks up the scratch address on that device (a CUDA
- * runtime query); make that first call outside any stream capture.  All calls share the
+ * runtime query; again after the device's context changed, e.g. after cudaDeviceReset);
+ * make that first call before any stream capture.  All calls share the
  * one scratch array: calls that overlap on the GPU (e.g. on two streams at once) race
  * and must be ordered by the caller.  Nothing needs to start at zero: each call
  * rewrites every partial it reads.  Calls no cudaMalloc / cudaFree and no allocating
@@ -267,6 +270,13 @@ const char* msfv_batch_last_error(const msfv_batch_t* b);
  * available for the nodal variant (MSFV_ERR_ARG). */
 int msfv_autotune(msfv_session_t* s, const double* m_dev, int* variants_out, double* ms_out);
 
+/* Numerical status of the last msfv_forward and the derivative calls after it:
+ * synchronises the session's stream and returns MSFV_OK, MSFV_ERR_NUMERIC (a non-
+ * positive local pivot, a singular or unconverged coarse solve) or MSFV_ERR_TIMEOUT (an
+ * expired device-side wait, see msfv_set_wait_limit), with the message in
+ * msfv_last_error(s).  Reads the status only; the record stays until the next forward. */
+int msfv_status(msfv_session_t* s);
+
 /* Free the session and its device workspace (synchronises its stream). NULL is ok. */
 int msfv_destroy(msfv_session_t* s);
 
@@ -278,6 +288,17 @@ const char* msfv_last_error(const msfv_session_t* s);
 
 /* Change the stream later calls enqueue on. */
 int msfv_set_stream(msfv_session_t* s, void* stream);
+
+/* Bound on the one device-side wait of the library: the software grid barrier of the
+ * all-SM coarse solver (the cooperative multigrid GMRES used for coarse meshes of 65536
+ * nodes and more, or with MSFV_MG_SOLVER=all at setup).  A CTA that has waited ns
+ * nanoseconds (GPU global timer) at one barrier gives up; every CTA then leaves the
+ * solve, the solution is not valid, and the next status read (see the conventions
+ * above) reports MSFV_ERR_TIMEOUT.  The next msfv_forward clears the record.
+ *   ns   > 0: the bound in nanoseconds; 0: the default (250 ms; a phase between two
+ *        barriers takes microseconds).  MSFV_ERR_ARG for ns < 0.
+ * Applies to solves enqueued after the call. */
+int msfv_set_wait_limit(msfv_session_t* s, int64_t ns);
 
 /* Sizes of the session: out[0]=N, out[1]=Nc, out[2]=Ns, out[3]=Nr, out[4]=number of
  * local problems (edges + faces + dual-cell interiors), out[5]=workspace bytes,
@@ -312,13 +333,29 @@ int msfv_profile(msfv_session_t* s, int enable);
 int msfv_phase_times(msfv_session_t* s, double* ms, int64_t* calls, int n, int reset);
 const char* msfv_phase_name(int k);
 
-/* Algorithmic FP64 FLOPs of one launch of the dual-cell interior basis kernel
- * (banded LDL^T factor + 2^d forward/backward solves, counted per Sec. 3.2 local
- * problem as n*b^2 + 2^d * 4*n*b summed over interiors). */
+/* Algorithmic FP64 FLOPs of one launch of the dual-cell interior basis kernel: the
+ * banded LDL^T factor and the forward and backward solves of the 2^d corner right-hand
+ * sides of every dual-cell interior (Sec. 3.2 local problems), counted exactly for the
+ * banded algorithm the kernel runs.  Column j of an interior with n unknowns, half
+ * bandwidth b and nvs right-hand sides has bj = min(b, n-1-j) entries below the
+ * diagonal and contributes bj(bj+1) + bj flops to the factor and 2 nvs (bj + min(b, j))
+ * + nvs to the solves; asymptotically n*b^2 + 2^d * 4*n*b per interior.  The bands are
+ * those of the axis order the kernel uses (shortest tangential axis fastest). */
 double msfv_interior_flops(const msfv_session_t* s);
 
 /* Number of kernel launches this session has enqueued since setup. */
 int64_t msfv_launch_count(const msfv_session_t* s);
+
+/* FP64 fused multiply-add throughput of the current device (no counterpart in the paper:
+ * it is the denominator of the FP64 rooflines the local and coarse solves are measured
+ * against).  One warm-up and five timed launches of a kernel that keeps every SM's FP64
+ * pipe busy with independent FMA chains (8 per thread, 2^14 steps each, one wave of
+ * 256-thread blocks); the fastest launch counts.
+ *   stream      cudaStream_t (NULL = legacy default); the call synchronises it
+ *   tflops_out  host double receiving the rate in TFLOP/s (2 flops per FMA)
+ *   ms_out      NULL or a host double receiving that launch's duration
+ * Allocates nothing on the device; MSFV_ERR_CUDA when a launch or an event fails. */
+int msfv_fp64_probe(void* stream, double* tflops_out, double* ms_out);
 
 #ifdef __cplusplus
 }

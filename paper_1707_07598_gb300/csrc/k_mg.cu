@@ -981,16 +981,19 @@ struct GA {
   long long stage_cap;
   unsigned* bar;                       // grid barrier: [0] arrivals, [1] generation
   int* err;                            // set when a barrier wait expired
+  unsigned long long limit_ns;         // longest wait of one CTA at one barrier
 };
 
 // Software grid barrier of the cooperative launch (all CTAs co-resident).  Returns false
-// once a wait has expired anywhere.
+// once a wait has expired anywhere.  A wait is bounded in time (GPU global timer): after
+// a.limit_ns, or as soon as another CTA has flagged an expiry, the CTA stops waiting, the
+// flag is set and every CTA leaves the solve at its next barrier, so a launch always ends.
 __device__ __noinline__ bool gbar(const GA& a) {
   __syncthreads();
   if (a.tid == 0) {
     // arrival with acquire-release semantics at GPU scope (after the block barrier, so the
     // block's writes are released); the last arrival resets the count and releases the
-    // generation; the others poll it with acquire loads, up to a bounded number of times
+    // generation; the others poll it with acquire loads until it moves or time runs out
     unsigned g, arrived;
     asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(g) : "l"(a.bar + 1) : "memory");
     asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(a.bar) : "memory");
@@ -998,15 +1001,17 @@ __device__ __noinline__ bool gbar(const GA& a) {
       asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(a.bar) : "memory");
       asm volatile("red.release.gpu.add.u32 [%0], 1;" ::"l"(a.bar + 1) : "memory");
     } else {
-      long long spins = 0;
+      const unsigned long long t0 = gtimer();
       unsigned cur;
-      do {
+      while (true) {
         asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(a.bar + 1) : "memory");
-        if (++spins > (1LL << 28)) {
+        if (cur != g) break;
+        if (*(volatile int*)a.err != 0) break;          // expired elsewhere: stop too
+        if (gtimer() - t0 >= a.limit_ns) {
           atomicExch(a.err, 1);
           break;
         }
-      } while (cur == g);
+      }
     }
   }
   __syncthreads();
@@ -1229,6 +1234,7 @@ __global__ void __launch_bounds__(NTA, 1) k_mg_gmres_all(MGParamsDev P, unsigned
   a.lt = a.tid - a.j * a.tpr;
   a.bar = aux;
   a.err = reinterpret_cast<int*>(aux + 2);
+  a.limit_ns = P.wait_limit_ns;
   const int m = min(P.m, MAXM);
   const int ns = P.Ns;
   // shared memory: per-RHS GMRES scalars, the reduction scratch, then staging
@@ -1442,9 +1448,10 @@ __global__ void __launch_bounds__(NTA, 1) k_mg_gmres_all(MGParamsDev P, unsigned
       for (long long i = b + a.lt; act && i < e; i += a.tpr) x[i] -= nbv[a.j];
   }
   if (a.cta == 0 && a.tid == 0) {
-    const bool failed = !ok || *(volatile int*)a.err != 0;
+    // 3: a barrier wait expired (the solve stopped early); 2: did not converge
+    const bool expired = !ok || *(volatile int*)a.err != 0;
     for (int jj = 0; jj < ns; ++jj) {
-      const int stv = failed ? 2 : st[jj];
+      const int stv = expired ? 3 : st[jj];
       if (stv && P.status) P.status[jj] = stv;
       if (P.iters) P.iters[jj] = its[jj];
     }
@@ -1593,6 +1600,7 @@ cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose,
   P.trace_cap = H.trace_cap;
   P.cws = H.cws;
   P.cws_stride = H.cws_stride;
+  P.wait_limit_ns = H.wait_limit_ns;
   const size_t dyn = mg_dyn_smem();
   if (H.all && H.ncta > 0 && Ns <= 64) {
     // all-SM variant: one cooperative grid, one CTA per SM

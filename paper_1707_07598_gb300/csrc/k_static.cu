@@ -2,16 +2,18 @@
 // r = d_pred - d_obs, computed without any device allocation.
 //
 // Why it exists: some callers cannot allocate GPU memory at the point where they need
-// the misfit -- code running while a CUDA graph is being captured, a host loop with a
-// fixed memory budget whose allocator must not grow, or an embedding application that
-// hands out only the buffers it owns.  msfv_setup allocates the session workspace up
-// front, so those callers cannot create a session there.  This entry point takes the
-// two data arrays and the two outputs from the caller and keeps its only scratch (one
-// partial sum per thread block) in a fixed array that is part of the library image.
+// the misfit -- a serving loop with a fixed memory budget whose allocator must not grow,
+// or an embedding application that hands out only the buffers it owns.  msfv_setup
+// allocates the session workspace up front, so those callers cannot create a session
+// there.  This entry point takes the two data arrays and the two outputs from the caller
+// and keeps its only scratch (one partial sum per thread block) in a fixed array that is
+// part of the library image.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/msfv.h"
 
@@ -26,6 +28,9 @@ static __device__ __align__(256) double g_misfit_partials[kStaticBlocks];
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 double* g_partials_addr[kMaxDevices] = {nullptr};
+// Driver id of the context each cached address belongs to: a cudaDeviceReset gives the
+// device a new primary context, in which the array may sit at another address.
+unsigned long long g_partials_ctx[kMaxDevices] = {0};
 
 // pass 1: each block owns a contiguous chunk, writes r and its partial sum of r^2
 __global__ void __launch_bounds__(kStaticThreads) k_misfit_pass1(const double* __restrict__ dp,
@@ -66,16 +71,40 @@ __global__ void __launch_bounds__(kStaticThreads) k_misfit_pass2(const double* _
   if (threadIdx.x == 0) phi[0] = 0.5 * red[0];
 }
 
-// Device address of the scratch array for the current device, looked up once per device.
+// Id of the current context (driver cuCtxGetId, reached through the runtime), or 0.
+unsigned long long current_context_id() {
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetId fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<GetId>(p);
+  }();
+  unsigned long long id = 0;
+  if (!fn || fn(nullptr, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array for the current device, looked up once per device
+// and context (again after the context changed, e.g. after a cudaDeviceReset).
 int partials_for_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MSFV_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_partials_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_partials_addr[dev] || ctx == 0 || ctx != g_partials_ctx[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_misfit_partials);
-    if (e != cudaSuccess || !p) return MSFV_ERR_CUDA;
+    if (e != cudaSuccess || !p) {
+      if (e != cudaSuccess) cudaGetLastError();   // this call's own error
+      return MSFV_ERR_CUDA;
+    }
     g_partials_addr[dev] = static_cast<double*>(p);
+    // the lookup made the device's context current if it was not yet
+    g_partials_ctx[dev] = current_context_id();
   }
   *out = g_partials_addr[dev];
   return MSFV_OK;
@@ -97,8 +126,21 @@ extern "C" int msfv_misfit_static(const double* d_pred_dev, const double* d_obs_
   if (nb < 1) nb = 1;
   if (nb > kStaticBlocks) nb = kStaticBlocks;
   const long long chunk = (count + nb - 1) / nb;
-  k_misfit_pass1<<<(int)nb, kStaticThreads, 0, st>>>(d_pred_dev, d_obs_dev, count,
-                                                      chunk > 0 ? chunk : 1, r_dev, partials);
-  k_misfit_pass2<<<1, kStaticThreads, 0, st>>>(partials, (int)nb, phi_dev);
-  return cudaGetLastError() == cudaSuccess ? MSFV_OK : MSFV_ERR_CUDA;
+  // cudaLaunchKernel reports the error of its own launch, so an error left behind by
+  // unrelated earlier work is neither cleared nor reported as this call's failure
+  long long cnt = count, ck = chunk > 0 ? chunk : 1;
+  int nbi = (int)nb;
+  void* a1[] = {(void*)&d_pred_dev, (void*)&d_obs_dev, (void*)&cnt, (void*)&ck, (void*)&r_dev,
+                (void*)&partials};
+  cudaError_t e = cudaLaunchKernel((const void*)k_misfit_pass1, dim3(nbi), dim3(kStaticThreads),
+                                   a1, 0, st);
+  if (e == cudaSuccess) {
+    void* a2[] = {(void*)&partials, (void*)&nbi, (void*)&phi_dev};
+    e = cudaLaunchKernel((const void*)k_misfit_pass2, dim3(1), dim3(kStaticThreads), a2, 0, st);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // the failed launch's own error, reported through the status
+    return MSFV_ERR_CUDA;
+  }
+  return MSFV_OK;
 }

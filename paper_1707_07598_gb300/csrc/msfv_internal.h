@@ -270,6 +270,9 @@ void launch_band_solve(const BandLU& B, double* rhs, int Ns, long long Nc, int t
 
 // ---- multigrid-preconditioned GMRES coarse solver (k_mg.cu) -----------------------
 constexpr int kMaxLevels = 12;
+// Longest time one CTA waits at one software grid barrier before the solve gives up and
+// reports MSFV_ERR_TIMEOUT (a phase between barriers takes microseconds).
+constexpr unsigned long long kDefaultWaitLimitNs = 250ull * 1000 * 1000;
 struct MGLevelDev {
   int g[3];
   int coarsened[3];     // 1 if this axis is coarsened to the next level
@@ -304,6 +307,7 @@ struct MGHost {
   double* tot = nullptr;      // Ns * 32 reduced sums
   double* hcol = nullptr;     // Ns * 24 * 24 rotated Hessenberg columns
   double* ybuf = nullptr;     // Ns * 24 least-squares solutions
+  unsigned long long wait_limit_ns = kDefaultWaitLimitNs;  // grid-barrier wait bound
 };
 struct MGParamsDev {
   int d, nlev, ld;
@@ -324,6 +328,7 @@ struct MGParamsDev {
   int trace_cap;
   double* cws;          // global coarse-level vectors per cluster group (null: on chip)
   long long cws_stride;
+  unsigned long long wait_limit_ns;   // all-SM variant: grid-barrier wait bound
 };
 void mg_setup_levels(MGHost& H, const DevGeom& g);
 // true when the vectors of levels >= 1 fit in one CTA's shared memory
@@ -337,7 +342,8 @@ int mg_all_grid(int d);
 int mg_pick_cluster(int d, int Ns, int* max_clusters);
 void launch_mg_setup(const MGHost& H, int* status, cudaStream_t s);
 // rhs: Ns x Nc, solved in place (pinned: entry 0 of each solution is zero);
-// status[j] = 2 when right-hand side j did not converge.
+// status[j] = 2 when right-hand side j did not converge, 3 when a grid-barrier wait of the
+// all-SM variant expired.
 cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose, int* status,
                             cudaStream_t s);
 

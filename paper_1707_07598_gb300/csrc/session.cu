@@ -1055,6 +1055,13 @@ extern "C" const char* msfv_last_error(const msfv_session_t* s) {
   return s ? s->err.c_str() : g_setup_error.c_str();
 }
 
+extern "C" int msfv_set_wait_limit(msfv_session_t* s, int64_t ns) {
+  if (!s) return MSFV_ERR_ARG;
+  if (ns < 0) return fail(s, MSFV_ERR_ARG, "msfv_set_wait_limit: negative limit");
+  s->mg.wait_limit_ns = ns ? (unsigned long long)ns : kDefaultWaitLimitNs;
+  return MSFV_OK;
+}
+
 extern "C" int msfv_set_stream(msfv_session_t* s, void* stream) {
   if (!s) return MSFV_ERR_ARG;
   s->stream = static_cast<cudaStream_t>(stream);
@@ -1382,6 +1389,9 @@ int read_status(msfv_session* s) {
   if (h[0]) return fail(s, MSFV_ERR_NUMERIC, "non-positive pivot in a local problem");
   if (h[1]) return fail(s, MSFV_ERR_NUMERIC, "zero pivot in the coarse solver (singular A_c)");
   for (int j = 0; j < s->Ns; ++j)
+    if (h[2 + j] == 3)
+      return fail(s, MSFV_ERR_TIMEOUT, "a grid-barrier wait of the coarse solver expired");
+  for (int j = 0; j < s->Ns; ++j)
     if (h[2 + j]) return fail(s, MSFV_ERR_NUMERIC, "coarse GMRES did not converge");
   return MSFV_OK;
 }
@@ -1414,6 +1424,11 @@ extern "C" int msfv_adjoint(msfv_session_t* s, const double* d_obs_dev, double* 
     return read_status(s);
   }
   return MSFV_OK;
+}
+
+extern "C" int msfv_status(msfv_session_t* s) {
+  if (!s) return MSFV_ERR_ARG;
+  return read_status(s);
 }
 
 extern "C" int msfv_jvec(msfv_session_t* s, const double* v_dev, double* jv_dev) {

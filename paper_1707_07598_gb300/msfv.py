@@ -104,6 +104,12 @@ def load(path: Optional[str] = None):
     L.msfv_gn_step.restype = ctypes.c_int
     L.msfv_autotune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     L.msfv_autotune.restype = ctypes.c_int
+    L.msfv_fp64_probe.argtypes = [vp, dp, dp]
+    L.msfv_set_wait_limit.argtypes = [vp, ctypes.c_int64]
+    L.msfv_status.argtypes = [vp]
+    L.msfv_status.restype = ctypes.c_int
+    L.msfv_set_wait_limit.restype = ctypes.c_int
+    L.msfv_fp64_probe.restype = ctypes.c_int
     for f in ("msfv_setup", "msfv_forward", "msfv_adjoint", "msfv_jvec", "msfv_jtvec",
               "msfv_solve_host", "msfv_destroy", "msfv_set_stream", "msfv_info", "msfv_profile",
               "msfv_phase_times", "msfv_phase_name", "msfv_coarse_trace"):
@@ -291,6 +297,16 @@ class Session:
                 "recompute", "global_window_mask", "source_slots", "source_values"]
         return dict(zip(keys, list(out)))
 
+    def check(self):
+        """Wait for the session's stream and raise MSFVError when the last forward or a
+        derivative call after it failed numerically or timed out (msfv_status)."""
+        self._check(self._lib.msfv_status(self._h))
+
+    def set_wait_limit(self, ns: int = 0):
+        """Bound (ns; 0 = the default) on a grid-barrier wait of the all-SM coarse solver;
+        an expired wait is reported as MSFV_ERR_TIMEOUT (msfv_set_wait_limit)."""
+        self._check(self._lib.msfv_set_wait_limit(self._h, int(ns)))
+
     def profile(self, enable: bool = True):
         self._check(self._lib.msfv_profile(self._h, int(enable)))
 
@@ -330,6 +346,17 @@ def misfit_static(d_pred, d_obs, r=None, phi=None, stream=None):
     if rc != MSFV_OK:
         raise MSFVError(rc, L.msfv_last_error(None).decode())
     return phi
+
+
+def fp64_probe(stream=None):
+    """(TFLOP/s, ms) of the device's FP64 FMA pipe, measured by msfv_fp64_probe."""
+    L = load()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    rc = L.msfv_fp64_probe(ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(tf),
+                           ctypes.byref(ms))
+    if rc != MSFV_OK:
+        raise MSFVError(rc, "msfv_fp64_probe failed")
+    return tf.value, ms.value
 
 
 class Batch:

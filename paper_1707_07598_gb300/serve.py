@@ -46,7 +46,7 @@ class Record:
     arrival: float
     start: float = float("nan")
     finish: float = float("nan")
-    status: str = "queued"      # queued / running / done / rejected
+    status: str = "queued"      # queued / running / done / failed / rejected
     result: object = None
 
     @property
@@ -63,7 +63,12 @@ class Stats:
     peak_bytes: int
 
     def done(self) -> List[Record]:
+        """Requests that finished with a valid result (the throughput and latencies)."""
         return [r for r in self.records if r.status == "done"]
+
+    def failed(self) -> List[Record]:
+        """Requests whose solve finished with a numerical or device-wait error."""
+        return [r for r in self.records if r.status == "failed"]
 
     @property
     def throughput(self) -> float:
@@ -164,8 +169,10 @@ class Server:
                 if self.backend.done(tok):
                     r = recs[req.rid]
                     r.finish = self.clock() - t0
-                    r.status = "done"
-                    if self.keep_results:
+                    # a solve whose local pivots or coarse solve failed is not a result
+                    ok = self.backend.ok(tok) if hasattr(self.backend, "ok") else True
+                    r.status = "done" if ok else "failed"
+                    if self.keep_results and ok:
                         r.result = self.backend.result(tok)
                     last_finish = max(last_finish, r.finish)
                     s.busy = False
@@ -311,6 +318,21 @@ class GpuBackend:
 
     def done(self, tok) -> bool:
         return tok[0].query()
+
+    def ok(self, tok) -> bool:
+        """Numerical status of a finished request (its event has completed, so reading the
+        status waits for nothing but a few bytes): False when the session's local pivots
+        or coarse solve failed or a device-side wait expired."""
+        from .msfv import MSFVError
+        h = tok[2]
+        try:
+            if h["batch"] is not None:
+                h["batch"].check()
+            else:
+                h["sess"].check()
+        except MSFVError:
+            return False
+        return True
 
     def result(self, tok):
         if tok[1] is None:

@@ -15,9 +15,13 @@ TOL = 1e-9
 
 
 def rel(a, b):
+    """Relative error in the 2-norm and in the max-norm, whichever is larger: a bound on
+    rel() holds for the whole array and for its largest entries alike."""
     a = np.asarray(a)
     b = np.asarray(b)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    r2 = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    rinf = np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300) if b.size else 0.0
+    return max(r2, rinf)
 
 
 @pytest.fixture(scope="module")

@@ -235,3 +235,25 @@ def test_constant_direction_leaves_the_lagrange_basis_unchanged():
     v1 = 0.001 * np.sin(np.pi * (X[:, 0] + 0.5) / n[0])
     j1 = o.jvec(st_, v1)[0]
     assert np.linalg.norm(j1 - fixed_jv(v1)) > 1e-4 * np.linalg.norm(j1)
+
+
+# The sizes the paper prints for its two test meshes (Sec. 5.1, Tab. 1; Sec. 5.2, Tab. 2):
+# the fine nodal systems have k = 17,797 (36 x 36 x 12 cells) and 139,425 (64 x 64 x 32)
+# unknowns, and each multiscale k is the number of Lagrange coarse nodes plus the
+# augmented bases the text lists (25 global-skeleton + 93 / 400 local bases for the block
+# model's 12^3 / 6^3 blocks; 72 + 862 / 3938 for the SEG model's 16^3 / 8^3 blocks).
+PAPER_SIZES = [
+    ((36, 36, 12), 12, 17797, 150, 25 + 93),
+    ((36, 36, 12), 6, 17797, 572, 25 + 400),
+    ((64, 64, 32), 16, 139425, 1009, 72 + 862),
+    ((64, 64, 32), 8, 139425, 4415, 72 + 3938),
+]
+
+
+@pytest.mark.parametrize("n,c,k_fine,k_ms,augmented", PAPER_SIZES)
+def test_node_and_basis_counts_match_the_paper(n, c, k_fine, k_ms, augmented):
+    prob = W.make_problem(n, c, 2, 4, seed=1, nodal=True)
+    orc = NodalOracle(prob)
+    assert orc.Nn == k_fine
+    assert orc.Ncn + augmented == k_ms
+    assert orc.Hat.shape == (k_fine, k_ms - augmented)

@@ -144,3 +144,36 @@ def test_smallest_work_first_cuts_the_median_latency_under_overload():
         qs.sort(key=lambda q: q.iteration)
         for a, b in zip(qs, qs[1:]):
             assert rec[b.rid].start >= rec[a.rid].finish
+
+
+class FailingBackend(FakeBackend):
+    """FakeBackend whose solves for the listed request ids finish with a bad status."""
+
+    def __init__(self, clock, bad):
+        super().__init__(clock)
+        self.bad = set(bad)
+
+    def ok(self, tok):
+        return tok[1] not in self.bad
+
+
+def test_a_failed_solve_is_not_counted_and_the_loop_goes_on():
+    clock = FakeClock()
+    rs = reqs(seed=8)
+    bad = {rs[1].rid, rs[4].rid}
+    be = FailingBackend(clock, bad)
+    st = Server(be, budget_bytes=10 ** 9, max_inflight=4, clock=clock, sleep=clock.sleep,
+                keep_results=True).run(rs)
+    failed = {r.rid for r in st.failed()}
+    assert failed == bad
+    done = st.done()
+    assert len(done) == len(rs) - len(bad)
+    assert all(r.rid not in bad for r in done) and all(r.result == r.rid for r in done)
+    assert all(r.result is None for r in st.failed())
+    # throughput and latencies count the good results only
+    assert st.throughput == pytest.approx(len(done) / st.makespan)
+    lat = sorted(r.latency for r in done)
+    assert st.percentile(100) == pytest.approx(lat[-1])
+    # every request was launched once, in order per client, and every session closed
+    assert sorted(be.launched) == sorted(r.rid for r in rs)
+    assert not be.open_now

@@ -1,8 +1,8 @@
 """The allocation-free misfit entry point against msfv_adjoint's misfit.
 
 msfv_misfit_static serves callers that cannot allocate device memory where they need
-the misfit (inside a CUDA graph capture, under a fixed allocator budget, or in a host
-application that only lends its own buffers).  This file is collected last so that a
+the misfit (a serving loop under a fixed allocator budget, or a host application that
+only lends its own buffers).  This file is collected last so that a
 run stopping at the first failure has already run every other test; it also passes
 on its own in a fresh process.
 """
@@ -57,6 +57,13 @@ def test_static_misfit_matches_adjoint_twice_in_a_row(lib):
         torch.cuda.synchronize()
         assert abs(phi.item() - phi_ref) <= TOL * abs(phi_ref)
         assert torch.equal(r, d_pred - d_obs)
+    # after the first call (which may load the kernels), a call takes no device memory
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert _static(lib, d_pred, d_obs, r, phi) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert abs(phi.item() - phi_ref) <= TOL * abs(phi_ref)
     # a different, larger input right after: no stale partials leak in
     big_p = torch.from_numpy(W.noise_like(300000, 1.0, 64)).to(dev)
     big_o = torch.from_numpy(W.noise_like(300000, 1.0, 65)).to(dev)
