@@ -1,14 +1,20 @@
 #!/usr/bin/env python3
-"""Benchmark: MSFV forward + misfit-gradient solves per second on GB300.
+"""Benchmark: batched MSFV forward + misfit-gradient solves per second on GB300, against
+the plain one-instance path on the same instances.
 
-Workload: 3D, 128^3 cells, coarsening 8 (16^3 coarse cells, 7^3 interior dual-cell
-problems with 8 right-hand sides), sigma = exp(m) with m a Gaussian random field
-(std 1, correlation length 0.15) plus two +/-2 boxes, 16 dipoles and 512
-receivers on the top layer.  One step = one forward solve (basis, coarse operator,
-reduced solve, predicted data) plus the misfit gradient through dP/dm, all FP64,
-inputs resident in HBM.  L2 is flushed (a 512 MiB write) before every timed step.
+Default workload (the batching configuration): 64 independent 3D instances, fine size
+drawn uniformly from {64, 96, 128, 192}^3, coarsening from {4, 8, 16} (uneven dual-cell
+sizes), lognormal conductivity with correlation length U[0.05, 0.2], 8-32 dipoles and
+256 receivers on the top layer, all FP64.  One step = one forward solve (basis, coarse
+operator, reduced solve, predicted data) plus the misfit gradient through dP/dm of every
+instance, replayed as one captured CUDA graph; inputs resident in HBM (the working set
+of a step is tens of GB, far larger than L2).  Beside it, in the same run: the same
+instances one at a time without a graph (the plain path), bit-for-bit equality of the
+two, oracle parity on one instance, the end-to-end rate through host buffers, the plain
+128^3 single-instance line with its roofline, and the CPU oracle on a sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batched|plain|served|diff|gn|sources|nodal]
 
 Under torchrun (N > 1) every rank runs an independent replica (the path has no
 exchange step); value = solves of all ranks / max-over-ranks time.
@@ -16,16 +22,23 @@ exchange step); value = solves of all ranks / max-over-ranks time.
 """
 from __future__ import annotations
 
-import argparse
-import json
 import os
-import statistics
-import subprocess
-import sys
-import tempfile
-import time
 
-import numpy as np
+if os.environ.get("MSFV_ORACLE_WORKER") == "1":
+    # oracle worker processes: one thread each, so the core count is the worker count
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import platform  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -35,13 +48,14 @@ from paper_1707_07598_gb300 import replicas as R  # noqa: E402
 
 METRIC = "batched/served MSFV fwd+grad solves/s vs plain at 1e-9 rel err; p50/p99 ms"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk x 2 flop x max SM clock
+FP64_PEAK_SOURCE = ("FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (unit counts and "
+                    "maximum SM clock of the profiling recipe); measured_tflops is the "
+                    "library's DFMA probe (msfv_fp64_probe) in this run")
 WORKLOAD = "3d_128^3_c8_16dipoles_512rec_fwd+grad"
-# DRAM bytes (read + write) of one k_local_fwd<256,1> launch per fine cell, from the ncu
-# capture of the current kernel at 64^3, c=8 (12.32 MB read + 13.16 MB write over 262144
-# cells; profiles/k_local_fwd_interiors_3d_64cube_c8.md).  The kernel's traffic (factor and
-# basis writes, conductivity reads) grows with the number of cells, so a launch on another
-# mesh is scaled by its cell count.  Set to None whenever the kernel changes.
-INTERIOR_DRAM_BYTES_PER_CELL = (12.322816e6 + 13.156096e6) / 64 ** 3
+# DRAM bytes (read + write) of one k_local_fwd<256,1> launch on the 128^3, c = 8 workload,
+# from an ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum).  Set
+# to None whenever the kernel changes, until it is captured again.
+INTERIOR_DRAM_BYTES_128 = 116805120.0 + 549029632.0
 
 
 def parse():
@@ -50,18 +64,24 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=128, help="mesh size per axis (default 128)")
+    p.add_argument("--n", type=int, default=128, help="plain: mesh size per axis (default 128)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", default="plain",
-                   choices=["plain", "batched", "served", "diff", "gn", "sources", "nodal"],
-                   help="plain: the one-instance 128^3 step (default); batched: independent "
-                        "instances in one CUDA graph vs one at a time; served: the Poisson "
-                        "request stream; diff: 256^3, c=16 gradient, J v, J^T w; gn: 5 "
-                        "Gauss-Newton-CG iterations on the 128^3 two-block model; sources: "
+    p.add_argument("--workload", default="batched",
+                   choices=["batched", "plain", "served", "diff", "gn", "sources", "nodal"],
+                   help="batched: 64 uneven instances in one CUDA graph per step vs one at a "
+                        "time (default); plain: the one-instance 128^3 step; served: the "
+                        "Poisson request stream; diff: 256^3, c=16 gradient, J v, J^T w; gn: "
+                        "5 Gauss-Newton-CG iterations on the 128^3 two-block model; sources: "
                         "the 128^3 step with source bases beside the plain one; nodal: "
                         "the paper's nodal Galerkin variant on the same survey shape")
     p.add_argument("--instances", type=int, default=64, help="batched: number of instances")
+    p.add_argument("--instance-budget-gb", type=float, default=0.0,
+                   help="batched: per-instance HBM budget (0 = store every local factor)")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="batched: skip the autotuner (default: tune each instance class once)")
+    p.add_argument("--plain-reps", type=int, default=2,
+                   help="batched: timed passes of the one-at-a-time comparison")
     p.add_argument("--rate", type=float, default=50.0, help="served: requests per second")
     p.add_argument("--duration", type=float, default=10.0,
                    help="served: seconds of the arrival stream that are replayed")
@@ -79,27 +99,6 @@ def dist_env():
     return e.rank, e.world, e.local
 
 
-# ---------------------------------------------------------------------------------
-# CPU oracle timing (the reference arm and the cpu_baseline object)
-# ---------------------------------------------------------------------------------
-SAMPLE_N = 64
-
-
-def oracle_sample_time():
-    """One oracle forward + gradient on the 64^3 sub-problem of the workload (same
-    c = 8, 16 dipoles, 512 top receivers).  Returns (seconds, scale) where scale =
-    cells(128^3) / cells(64^3) extrapolates the time to the full workload."""
-    from oracle.msfv_oracle import Oracle
-    prob, m = W.config_3d_128(n=SAMPLE_N)
-    orc = Oracle(prob)
-    t0 = time.perf_counter()
-    st = orc.forward(m)
-    d_obs = st['d'] * 1.01
-    orc.misfit_gradient(st, d_obs)
-    t1 = time.perf_counter()
-    return t1 - t0, (128 / SAMPLE_N) ** 3
-
-
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -107,32 +106,203 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            low = line.lower()
+            if low.startswith("model name") or low.startswith("cpu part"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+# ---------------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline object)
+# ---------------------------------------------------------------------------------
+def _oracle_worker(conn, spec, send_arrays):
+    """One oracle instance in its own process: build it once (the set-up, untimed), then
+    one forward + misfit gradient per request, timed; d_obs = 0.97 x the oracle's own
+    prediction, as the GPU arm does with its prediction."""
+    try:
+        from oracle.msfv_oracle import Oracle
+        prob = spec.problem()
+        m = W.gaussian_random_field(prob.n, spec.corr_len, spec.seed)
+        t0 = time.perf_counter()
+        orc = Oracle(prob)
+        conn.send(("ready", time.perf_counter() - t0))
+        while True:
+            msg = conn.recv()
+            if msg != "step":
+                break
+            t0 = time.perf_counter()
+            st = orc.forward(m)
+            phi, g = orc.misfit_gradient(st, 0.97 * st['d'])
+            dt = time.perf_counter() - t0
+            conn.send(("done", dt, (st['d'], g, phi) if send_arrays else None))
+    except Exception as exc:   # report and stop; the parent raises
+        conn.send(("error", repr(exc)))
+
+
+class OraclePool:
+    """One spawned single-threaded process per sampled instance.  Processes start before
+    any CUDA call of the parent; a step runs one oracle forward + gradient on every
+    instance at once and returns the wall time."""
+
+    def __init__(self, specs, arrays_for=()):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.specs = list(specs)
+        self.conns, self.procs = [], []
+        os.environ["MSFV_ORACLE_WORKER"] = "1"
+        try:
+            for i, sp in enumerate(self.specs):
+                a, b = ctx.Pipe()
+                pr = ctx.Process(target=_oracle_worker, args=(b, sp, i in arrays_for),
+                                 daemon=True)
+                pr.start()
+                self.conns.append(a)
+                self.procs.append(pr)
+        finally:
+            del os.environ["MSFV_ORACLE_WORKER"]
+        self.ready = False
+        self.pending = False
+        self.t_start = 0.0
+
+    def _recv(self, c):
+        msg = c.recv()
+        if msg[0] == "error":
+            raise RuntimeError("oracle worker failed: " + msg[1])
+        return msg
+
+    def wait_ready(self):
+        if not self.ready:
+            self.setup_s = [self._recv(c)[1] for c in self.conns]
+            self.ready = True
+
+    def start_step(self):
+        self.wait_ready()
+        self.t_start = time.perf_counter()
+        for c in self.conns:
+            c.send("step")
+        self.pending = True
+
+    def finish_step(self):
+        out = [self._recv(c) for c in self.conns]
+        wall = time.perf_counter() - self.t_start
+        self.pending = False
+        return wall, [o[1] for o in out], [o[2] for o in out]
+
+    def step(self):
+        self.start_step()
+        return self.finish_step()
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send("stop")
+            except Exception:
+                pass
+        for pr in self.procs:
+            pr.join(timeout=10)
+
+
+def oracle_sample(specs):
+    """The batch's instances the oracle solves in about 10-15 s each on one core: the
+    64^3 ones with c = 8 or 16 (those with c = 4 take about three times longer, the larger
+    meshes minutes)."""
+    return [i for i, sp in enumerate(specs) if sp.n[0] == 64 and sp.coarsen in (8, 16)]
+
+
+def sample_text(specs, idx, cores):
+    kinds = {}
+    for i in idx:
+        key = f"{specs[i].n[0]}^3 c={specs[i].coarsen}"
+        kinds[key] = kinds.get(key, 0) + 1
+    mix = ", ".join(f"{v} x {k}" for k, v in sorted(kinds.items()))
+    return (f"per step, one oracle forward + misfit gradient of each of the {len(idx)} "
+            f"instances of the batch that the oracle finishes in seconds ({mix}; the larger "
+            f"instances take minutes to hours each, so the rate on the whole mix is lower), "
+            f"one single-threaded process per instance on {cores} host cores; value = "
+            f"instances / wall time; oracle set-up (geometry) outside the timing")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    if args.workload == "plain":
+        return run_reference_plain(args)
+    specs = W.batch_instances(args.instances)
+    idx = oracle_sample(specs)
+    pool = OraclePool([specs[i] for i in idx])
+    pool.wait_ready()
     for _ in range(args.warmup):
-        oracle_sample_time()
-    times = []
+        pool.step()
+    walls = []
     for _ in range(args.steps):
-        t, scale = oracle_sample_time()
-        times.append(t * scale)
-    ms = 1000.0 * statistics.mean(times)
-    val = 1000.0 / ms
-    sample = (f"oracle fwd+grad on the {SAMPLE_N}^3 sub-problem of the workload (c=8, 16 dipoles, "
-              f"512 top receivers) per step, time x{(128 // SAMPLE_N) ** 3} (cell ratio) for 128^3")
+        walls.append(pool.step()[0])
+    pool.close()
+    ms = 1000.0 * statistics.mean(walls)
+    val = len(idx) * len(walls) / sum(walls)
+    cores = len(idx)
+    cfg = batched_config(specs, args)
     out = {"metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "n": [128] * 3, "coarsen": 8, "n_src": 16,
-                      "n_rec": 512},
-           "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                            "sample": sample},
+           "data": "synthetic", "impl": "reference", "config": cfg,
+           "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                            "sample": sample_text(specs, idx, cores),
+                            "host_cores": host_cores(), "cpu_model": cpu_model()},
            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def run_reference_plain(args):
+    """The oracle on the full 128^3 plain workload, one forward + gradient per step."""
+    from oracle.msfv_oracle import Oracle
+    prob, m = W.config_3d_128(n=args.n)
+    orc = Oracle(prob)
+
+    def one():
+        t0 = time.perf_counter()
+        st = orc.forward(m)
+        orc.misfit_gradient(st, st['d'] * 1.01)
+        return time.perf_counter() - t0
+    for _ in range(args.warmup):
+        one()
+    times = [one() for _ in range(args.steps)]
+    ms = 1000.0 * statistics.mean(times)
+    val = 1000.0 / ms
+    out = {"metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "n": [args.n] * 3, "coarsen": 8, "n_src": 16,
+                      "n_rec": 512},
+           "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                            "sample": f"one oracle forward + gradient of the whole {args.n}^3 "
+                                      "workload per step, one process, one thread",
+                            "cpu_model": cpu_model()},
+           "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def batched_config(specs, args):
+    mix = {}
+    for sp in specs:
+        key = f"{sp.n[0]}^3_c{sp.coarsen}"
+        mix[key] = mix.get(key, 0) + 1
+    return {"workload": f"batched_{len(specs)}_instances_3d_sizes64-192_c4-16_8-32dipoles_256rec",
+            "instances": len(specs), "mix": mix, "sizes": [64, 96, 128, 192],
+            "coarsenings": [4, 8, 16], "dipoles": "8-32", "receivers": 256,
+            "corr_len": "U[0.05, 0.2]", "parallelism": "replicas x1",
+            "l2": "inputs and working set of a step (tens of GB) far larger than L2",
+            "graph": "one CUDA graph per step, one branch per instance"}
 
 
 # ---------------------------------------------------------------------------------
@@ -194,29 +364,12 @@ class ClockSampler:
         return out
 
 
-def run_ours(args):
+def plain_measure(args, dev, sess, prob, m, d_obs, world=1):
+    """Time the plain one-instance step (msfv_forward + msfv_adjoint) of an open session:
+    CUDA events on the session stream, L2 flushed before each step, phase timers for the
+    roofline of the interior basis kernel, and the end-to-end rate through host buffers."""
     import torch
-    from paper_1707_07598_gb300 import build as B
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
-    torch.cuda.set_device(dev)
-    B.build()
-    from paper_1707_07598_gb300.msfv import Session
-
-    seeds = R.replica_seeds(rank)
-    prob, m_np = W.config_3d_128(seed=seeds.model, n=args.n)
     stream = torch.cuda.current_stream(dev)
-    sess = Session(prob, stream=stream)
-    m = torch.from_numpy(m_np).to(dev)
-    # observed data: forward at an independent model plus 1% noise (outside the timing)
-    m_true = torch.from_numpy(W.config_3d_128(seed=seeds.truth, n=args.n)[1]).to(dev)
-    d_true = sess.forward(m_true).clone()
-    noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, seeds.noise)).to(dev)
-    d_obs = d_true + 0.01 * d_true.abs() * noise
     grad = torch.empty(prob.N, dtype=torch.float64, device=dev)
     d_pred = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -225,16 +378,13 @@ def run_ours(args):
         sess.forward(m, d_pred)
         sess.adjoint(d_obs, grad, want_phi=False)
 
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup, 1)):
         step()
     torch.cuda.synchronize(dev)
     sess.profile(True)
     sess.phase_times(reset=True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    clocks = ClockSampler(dev.index if dev.index is not None else 0)
-    clocks.start()
-    time.sleep(0.3)
     R.barrier()
     torch.cuda.synchronize(dev)
     launches0 = sess.launch_count()
@@ -246,38 +396,29 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     launches = sess.launch_count() - launches0
     R.barrier()
-    clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     phases = sess.phase_times(reset=True)
     sess.profile(False)
     info = sess.info()
     total_ms = R.max_over_ranks(sum(step_ms), dev)
-    ms_per_step = total_ms / args.steps
-    value = R.whole_job_rate(world, args.steps, total_ms / 1000.0)
-
-    # roofline of the dominant kernel: the dual-cell interior basis solve
+    # roofline of the dominant kernel of this step: the dual-cell interior basis solve
     int_ms, int_calls = phases.get("basis_interiors", (0.0, 0))
     int_avg_s = (int_ms / max(int_calls, 1)) / 1000.0
     flops = sess.interior_flops()
     achieved = flops / int_avg_s / 1e12 if int_avg_s > 0 else 0.0
     roof = {"bound": "alu", "kernel": "k_local_fwd<256,1> (3D dual-cell interiors)",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (recipe unit "
-                           "counts and max clock); a DFMA probe measured 1.20 TFLOP/s at 1987 MHz",
+            "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_SOURCE,
             "flops_per_launch": flops, "avg_launch_ms": int_avg_s * 1000.0,
-            "traffic": (INTERIOR_DRAM_BYTES_PER_CELL * prob.N
-                        if INTERIOR_DRAM_BYTES_PER_CELL is not None else None),
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel at "
-                              "64^3, scaled by the number of fine cells"}
+            "traffic": INTERIOR_DRAM_BYTES_128 if (args.n == 128 and args.precision == "fp64")
+            else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
+                              "this kernel on the 128^3 workload"}
     if args.precision == "mixed":
         roof.update(kernel="k_mix_fwd (3D dual-cell interiors: FP32 band factor, two FP64 "
                            "refinement steps)",
-                    traffic=None,
                     note="the method's FP64 flop count (the same numerator as the FP64 kernel) "
                          "over the FP64 peak; most of the arithmetic runs in FP32")
-    phase_ms = {k: v[0] / max(args.steps, 1) for k, v in phases.items() if v[1]}
-
     e2e = None
     if not args.no_e2e:
         m_h = torch.empty(prob.N, dtype=torch.float64).pin_memory()
@@ -302,31 +443,65 @@ def run_ours(args):
         e2e = {"value": R.whole_job_rate(world, args.steps, tot), "unit": "solves/s",
                "h2d_bytes_per_step": 8 * prob.N + 8 * prob.n_src * prob.n_rec,
                "d2h_bytes_per_step": 8 * prob.N + 8 * prob.n_src * prob.n_rec + 8}
+    return {"value": R.whole_job_rate(world, args.steps, total_ms / 1000.0), "unit": "solves/s",
+            "ms_per_step": total_ms / args.steps,
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+            "phases_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in phases.items() if v[1]},
+            "coarse": {"solver": "mg-gmres" if info["coarse_solver"] else "banded-lu",
+                       "iters_fwd": info["coarse_iters"], "iters_adj": info["coarse_iters_T"]}}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, scale = oracle_sample_time()
-        cpu = {"value": 1.0 / (t * scale), "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle fwd+grad on the {SAMPLE_N}^3 sub-problem of the workload "
-                         f"(c=8, 16 dipoles, 512 top receivers): {t:.2f} s, scaled x{scale:.0f} "
-                         f"(cell ratio) to 128^3; numpy/scipy, single thread"}
 
+def open_plain(args, dev, seed_model=2, seed_truth=3, seed_noise=4):
+    """The 128^3 plain workload: session, model and observed data (forward at an
+    independent model plus 1% noise, outside any timing)."""
+    import torch
+    from paper_1707_07598_gb300.msfv import Session
+    prob, m_np = W.config_3d_128(seed=seed_model, n=args.n)
+    sess = Session(prob, stream=torch.cuda.current_stream(dev))
+    m = torch.from_numpy(m_np).to(dev)
+    m_true = torch.from_numpy(W.config_3d_128(seed=seed_truth, n=args.n)[1]).to(dev)
+    d_true = sess.forward(m_true).clone()
+    noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, seed_noise)).to(dev)
+    d_obs = d_true + 0.01 * d_true.abs() * noise
+    return sess, prob, m, d_obs
+
+
+def run_plain(args):
+    """The plain one-instance line: 128^3, c = 8, 16 dipoles, 512 receivers."""
+    import torch
+    from paper_1707_07598_gb300 import build as B
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    B.build()
+    seeds = R.replica_seeds(rank)
+    sess, prob, m, d_obs = open_plain(args, dev, seeds.model, seeds.truth, seeds.noise)
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    time.sleep(0.3)
+    res = plain_measure(args, dev, sess, prob, m, d_obs, world)
+    clk = clocks.stop()
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-               "p50_ms": float(np.percentile(step_ms, 50)),
-               "p99_ms": float(np.percentile(step_ms, 99)),
+        out = {"metric": METRIC, "value": res["value"], "unit": "solves/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+               "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"],
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64", "data": "synthetic",
                "config": {"workload": WORKLOAD if args.n == 128 else f"3d_{args.n}^3_c8",
                           "n": [args.n] * 3, "coarsen": 8, "n_src": prob.n_src,
                           "n_rec": prob.n_rec, "parallelism": f"replicas x{world}",
                           "l2": "flushed before every timed step (512 MiB write)",
-                          "factor_mode": "store", "precision": args.precision},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk, "phases_ms_per_step": phase_ms,
-               "coarse": {"solver": "mg-gmres" if info["coarse_solver"] else "banded-lu",
-                          "iters_fwd": info["coarse_iters"], "iters_adj": info["coarse_iters_T"]}}
+                          "factor_mode": "store", "precision": args.precision,
+                          "order": "first order in h at even c (coarse vertex half a cell off "
+                                   "the coarse-cell centre)"},
+               "roofline": res["roofline"], "cpu_baseline": None, "e2e": res["e2e"],
+               "gpu_launches": res["gpu_launches"], "clocks": clk,
+               "phases_ms_per_step": res["phases_ms_per_step"], "coarse": res["coarse"]}
         print(json.dumps(out))
     sess.close()
     if world > 1:
@@ -334,11 +509,6 @@ def run_ours(args):
     return 0
 
 
-
-# ---------------------------------------------------------------------------------
-# Extra workloads (not the default line): batched instances, served requests, and the
-# 256^3 differentiation case.  Each prints its own JSON line.
-# ---------------------------------------------------------------------------------
 def _gpu_setup():
     import torch
     from paper_1707_07598_gb300 import build as B
@@ -348,92 +518,247 @@ def _gpu_setup():
     return torch, dev
 
 
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    r2 = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    ri = np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+    return float(max(r2, ri))
+
+
 def run_batched(args):
-    """Independent 3D instances (sizes 64..192^3, c in {4, 8, 16}, 8-32 dipoles) as one
-    CUDA graph per step, against the same instances run one at a time."""
-    torch, dev = _gpu_setup()
-    from paper_1707_07598_gb300.msfv import Batch, Session
-    specs = W.batch_instances(args.instances)
+    """The default line: independent 3D instances (sizes 64..192^3, c in {4, 8, 16}, 8-32
+    dipoles) as one CUDA graph per step, against the same instances one at a time."""
+    import torch
+    from paper_1707_07598_gb300 import build as B
+    rank, world, local = dist_env()
+    specs = W.batch_instances(args.instances, seed=3 + 1000 * rank)
+    sample = oracle_sample(specs)
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and sample:
+        # before any CUDA call: the oracle processes start now and run one timed step on
+        # the sample while the GPU sessions are set up
+        pool = OraclePool([specs[i] for i in sample], arrays_for=(0,))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    B.build()
+    from paper_1707_07598_gb300.msfv import Batch, Session, fp64_probe
+    if pool is not None:
+        pool.start_step()
+    stream = torch.cuda.current_stream(dev)
+    t_setup = time.perf_counter()
+    budget = int(args.instance_budget_gb * (1 << 30))
     sessions, ms, dobs = [], [], []
-    per_instance_budget = 6 << 30     # larger stored factors switch to recompute
-    for sp in specs:
+    tuned = {}
+    for k, sp in enumerate(specs):
         prob = sp.problem()
-        st = torch.cuda.Stream(dev)
-        sessions.append(Session(prob, stream=st, factor_mode=0,
-                                hbm_budget_bytes=per_instance_budget))
-        ms.append(W.gaussian_random_field_device(prob.n, sp.corr_len, sp.seed, dev))
+        sessions.append(Session(prob, stream=torch.cuda.Stream(dev), factor_mode=0,
+                                hbm_budget_bytes=budget))
+        if k in sample:    # the host generator: the oracle draws the same field
+            ms.append(torch.from_numpy(W.gaussian_random_field(prob.n, sp.corr_len,
+                                                               sp.seed)).to(dev))
+        else:
+            ms.append(W.gaussian_random_field_device(prob.n, sp.corr_len, sp.seed, dev))
         dobs.append(torch.zeros((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev))
+        key = (sp.n[0], sp.coarsen)
+        if not args.no_autotune and key not in tuned:
+            tuned[key] = sessions[-1].autotune(ms[-1])
     torch.cuda.synchronize()
-    batch = Batch(sessions, ms, dobs)
+    batch = Batch(sessions, ms, dobs, stream=stream)
     batch.run()
     batch.check()
     for k in range(len(specs)):                       # observed data: 97% of the prediction
         dobs[k].copy_(0.97 * batch.d_pred[k])
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    cpu = None
+    parity = None
+    if pool is not None:
+        wall, times, arrays = pool.finish_step()
+        pool.close()
+        cpu = {"value": len(sample) / wall, "unit": "solves/s", "cores": len(sample),
+               "kind": "oracle", "sample": sample_text(specs, sample, len(sample)),
+               "wall_s": wall, "host_cores": host_cores(), "cpu_model": cpu_model(),
+               "per_instance_s": times}
     for _ in range(max(args.warmup - 1, 0)):
         batch.run()
     batch.check()
-    stream = torch.cuda.current_stream(dev)
-    clocks = ClockSampler(0)
+    fp64_tf, _ = fp64_probe(stream)
+    # ---- timed: the batched step ----------------------------------------------------
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
     clocks.start()
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    R.barrier()
+    torch.cuda.synchronize(dev)
     for k in range(args.steps):
         ev[k][0].record(stream)
         batch.run()
         ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    torch.cuda.synchronize(dev)
+    R.barrier()
     batch.check()
-    bt = [a.elapsed_time(b) for a, b in ev]
     clk = clocks.stop()
-    # the plain one-instance path: the same instances one after another, no graph
-    plain_ms = []
-    d_plain, g_plain = [], []
-    for rep in range(max(1, min(args.steps, 2))):
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
+    bt = [a.elapsed_time(b) for a, b in ev]
+    K = len(specs)
+    total_ms = R.max_over_ranks(sum(bt), dev)
+    value = R.whole_job_rate(world, K * args.steps, total_ms / 1000.0)
+    d_b = [t.clone() for t in batch.d_pred]
+    g_b = [t.clone() for t in batch.grad]
+    # ---- the plain path: the same instances one at a time, no graph -------------------
+    plain_ms, inst_ms = [], np.zeros(K)
+    phase_tot = {}
+    roof_cls = {}
+    launches_step = 0
+    same = True
+    for s in sessions:
+        s.set_stream(stream)
+    for rep in range(max(1, args.plain_reps)):
+        prof = rep == 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ie = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
         for k, s in enumerate(sessions):
-            s.set_stream(stream)
+            if prof:
+                s.profile(True)
+                s.phase_times(reset=True)
+                l0 = s.launch_count()
+            ie[k][0].record(stream)
             d = s.forward(ms[k])
             _, g = s.adjoint(dobs[k], want_phi=False)
+            ie[k][1].record(stream)
+            if prof:
+                launches_step += s.launch_count() - l0
             if rep == 0:
-                d_plain.append(d)
-                g_plain.append(g)
-        t1.record(stream)
-        torch.cuda.synchronize()
-        plain_ms.append(t0.elapsed_time(t1))
-    same = all(torch.equal(d_plain[k], batch.d_pred[k]) and torch.equal(g_plain[k], batch.grad[k])
-               for k in range(len(specs)))
-    K = len(specs)
-    ms_step = float(np.mean(bt))
-    value = K / (ms_step / 1000.0)
-    plain_val = K / (float(np.mean(plain_ms)) / 1000.0)
+                same = same and torch.equal(d, d_b[k]) and torch.equal(g, g_b[k])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms.append(e0.elapsed_time(e1))
+        for k in range(K):
+            inst_ms[k] += ie[k][0].elapsed_time(ie[k][1]) / max(1, args.plain_reps)
+        if prof:
+            for k, s in enumerate(sessions):
+                ph = s.phase_times(reset=True)
+                s.profile(False)
+                for name, (t, c) in ph.items():
+                    phase_tot[name] = phase_tot.get(name, 0.0) + t
+                tms, tc = ph.get("basis_interiors", (0.0, 0))
+                cls = f"c{specs[k].coarsen}"
+                r = roof_cls.setdefault(cls, {"flops": 0.0, "ms": 0.0, "launches": 0})
+                r["flops"] += s.interior_flops() * tc
+                r["ms"] += tms
+                r["launches"] += tc
+    plain_val = R.whole_job_rate(world, K, R.max_over_ranks(float(np.mean(plain_ms)), dev) / 1000.0)
+    # roofline: the interior basis kernel, whose launches take the largest share of the
+    # step, over every instance of the batch, timed per launch with CUDA events on the
+    # stream it runs on (the one-at-a-time pass); per coarsening class beside it
+    fl = sum(r["flops"] for r in roof_cls.values())
+    tm = sum(r["ms"] for r in roof_cls.values())
+    achieved = fl / (tm / 1000.0) / 1e12 if tm > 0 else 0.0
+    top = max(phase_tot.items(), key=lambda kv: kv[1])[0] if phase_tot else None
+    roof = {"bound": "alu",
+            "kernel": "k_local_fwd (3D dual-cell interior basis solves) over all instances",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_SOURCE,
+            "measured_tflops": fp64_tf, "frac_of_measured": achieved / fp64_tf if fp64_tf else None,
+            "flops_per_step": fl, "kernel_ms_per_step": tm, "traffic": None,
+            "by_class": {c: {"achieved": r["flops"] / (r["ms"] / 1000.0) / 1e12 if r["ms"] else 0.0,
+                             "ms_per_step": r["ms"], "launches": r["launches"]}
+                         for c, r in sorted(roof_cls.items())},
+            "largest_phase": top,
+            "phase_share": {k2: v / max(sum(phase_tot.values()), 1e-12)
+                            for k2, v in sorted(phase_tot.items(), key=lambda kv: -kv[1])[:6]}}
+    # ---- oracle parity on the first sampled instance (same field, same survey) ---------
+    if pool is not None and arrays[0] is not None:
+        i0 = sample[0]
+        d_o, g_o, phi_o = arrays[0]
+        parity = {"instance": f"{specs[i0].n[0]}^3 c={specs[i0].coarsen} "
+                              f"({specs[i0].n_src} dipoles)",
+                  "rel_err_d": rel_err(d_b[i0].cpu().numpy(), d_o),
+                  "rel_err_grad": rel_err(g_b[i0].cpu().numpy(), g_o),
+                  "tol": 1e-9, "norm": "max of relative 2-norm and max-norm"}
+        parity["ok"] = parity["rel_err_d"] < 1e-9 and parity["rel_err_grad"] < 1e-9
+        gpu_same = sum(inst_ms[i] for i in sample) / 1000.0
+        cpu["gpu_plain_same_sample"] = {"value": len(sample) / gpu_same, "unit": "solves/s",
+                                        "note": "the same sampled instances on the GPU, one "
+                                                "at a time"}
+    # ---- end to end: host buffers through msfv_batch_run_host -------------------------
+    e2e = None
+    if not args.no_e2e:
+        mh = [torch.empty(t.numel(), dtype=torch.float64).pin_memory() for t in ms]
+        dh = [torch.empty(tuple(t.shape), dtype=torch.float64).pin_memory() for t in dobs]
+        for k in range(K):
+            mh[k].copy_(ms[k].cpu())
+            dh[k].copy_(dobs[k].cpu())
+        ph_ = [torch.empty(tuple(t.shape), dtype=torch.float64).pin_memory() for t in dobs]
+        gh = [torch.empty(t.numel(), dtype=torch.float64).pin_memory() for t in ms]
+        args_h = ([x.numpy() for x in mh], [x.numpy().reshape(-1) for x in dh],
+                  [x.numpy().reshape(-1) for x in ph_], [x.numpy() for x in gh])
+        batch.run_host(*args_h)
+        n_e2e = max(1, min(args.steps, 3))
+        R.barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            batch.run_host(*args_h)
+        tot = R.max_over_ranks(time.perf_counter() - t0, dev)
+        same = same and all(np.array_equal(args_h[3][k], g_b[k].cpu().numpy()) for k in range(K))
+        hb = sum(8 * t.numel() for t in ms) + sum(8 * t.numel() for t in dobs)
+        db = sum(8 * t.numel() for t in ms) + sum(8 * t.numel() for t in dobs)
+        e2e = {"value": R.whole_job_rate(world, K * n_e2e, tot), "unit": "solves/s",
+               "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db, "steps": n_e2e,
+               "api": "msfv_batch_run_host (pinned host buffers, copies inside the timing)"}
+    # ---- the plain 128^3 single-instance line ---------------------------------------
+    plain128 = None
+    if world == 1:
+        psess, pprob, pm, pdobs = open_plain(args, dev)
+        pres = plain_measure(args, dev, psess, pprob, pm, pdobs, 1)
+        psess.close()
+        plain128 = dict(pres, workload=WORKLOAD,
+                        note="configuration 2 of the task: one instance, 128^3, c = 8, 16 "
+                             "dipoles, 512 receivers; L2 flushed before each step; first "
+                             "order in h at even c (coarse vertex half a cell off the "
+                             "coarse-cell centre)")
     recompute = sum(int(s.info()["recompute"]) for s in sessions)
-    mix = {}
-    for sp in specs:
-        key = f"{sp.n[0]}^3_c{sp.coarsen}"
-        mix[key] = mix.get(key, 0) + 1
-    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-           "p50_ms": float(np.percentile(bt, 50)), "p99_ms": float(np.percentile(bt, 99)),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
-           "config": {"workload": f"batched_{K}_instances_3d", "instances": K, "mix": mix,
-                      "graph": "one CUDA graph per step, one branch per instance",
-                      "recompute_instances": recompute,
-                      "l2": "working set of every step far larger than L2"},
-           "plain": {"value": plain_val, "unit": "solves/s",
-                     "ms_per_step": float(np.mean(plain_ms)),
-                     "path": "same sessions, forward + adjoint one instance at a time"},
-           "speedup_vs_plain": value / plain_val,
-           "parity": "batched == plain bit for bit on every instance" if same else "MISMATCH",
-           "clocks": clk}
-    print(json.dumps(out))
+    ws_gb = sum(int(s.info()["workspace_bytes"]) for s in sessions) / 1e9
+    if rank == 0:
+        cfg = batched_config(specs, args)
+        cfg.update(recompute_instances=recompute, workspace_gb=ws_gb,
+                   parallelism=f"replicas x{world}", autotuned_classes=len(tuned),
+                   setup_s=setup_s)
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": total_ms / args.steps,
+               "p50_ms": float(np.percentile(bt, 50)), "p99_ms": float(np.percentile(bt, 99)),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64", "data": "synthetic", "config": cfg,
+               "plain": {"value": plain_val, "unit": "solves/s",
+                         "ms_per_step": float(np.mean(plain_ms)),
+                         "path": "same sessions and inputs, msfv_forward + msfv_adjoint one "
+                                 "instance at a time on one stream, no graph",
+                         "per_instance_ms_p50": float(np.percentile(inst_ms, 50)),
+                         "per_instance_ms_p99": float(np.percentile(inst_ms, 99))},
+               "speedup_vs_plain": value / plain_val if plain_val else None,
+               "bitwise_equal_to_plain": bool(same), "oracle_parity": parity,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches_step * args.steps, "clocks": clk,
+               "plain_128": plain128}
+        print(json.dumps(out))
     batch.close()
     for s in sessions:
         s.close()
-    return 0 if same else 1
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    ok = same and (parity is None or parity["ok"])
+    return 0 if ok else 1
 
 
 def run_served(args):
@@ -728,19 +1053,9 @@ def main():
         os.environ["MSFV_LOCAL_PRECISION"] = "mixed"
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batched":
-        return run_batched(args)
-    if args.workload == "served":
-        return run_served(args)
-    if args.workload == "diff":
-        return run_diff(args)
-    if args.workload == "gn":
-        return run_gn(args)
-    if args.workload == "sources":
-        return run_sources(args)
-    if args.workload == "nodal":
-        return run_nodal(args)
-    return run_ours(args)
+    runners = {"batched": run_batched, "plain": run_plain, "served": run_served,
+               "diff": run_diff, "gn": run_gn, "sources": run_sources, "nodal": run_nodal}
+    return runners[args.workload](args)
 
 
 if __name__ == "__main__":

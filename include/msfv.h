@@ -252,6 +252,15 @@ int msfv_batch_create(msfv_session_t* const* sessions, int K, const double* cons
                       double* const* grad_dev, void* stream, msfv_batch_t** out);
 int msfv_batch_run(msfv_batch_t* b);
 int msfv_batch_check(msfv_batch_t* b);
+/* One step through HOST buffers: copies m_host[k] (N_k doubles) and d_obs_host[k]
+ * (Ns_k*Nr_k) into the instances' captured device inputs, runs the graph, copies the
+ * captured outputs back to d_pred_host[k] (Ns_k*Nr_k) and grad_host[k] (N_k), all on the
+ * batch's stream (one cudaMemcpyAsync per buffer), then does what msfv_batch_check does:
+ * synchronises and reports the first instance whose solve failed.  Pinned host buffers
+ * give the fastest copies.  MSFV_ERR_ARG (nothing enqueued) for a NULL array or entry. */
+int msfv_batch_run_host(msfv_batch_t* b, const double* const* m_host,
+                        const double* const* d_obs_host, double* const* d_pred_host,
+                        double* const* grad_host);
 int msfv_batch_destroy(msfv_batch_t* b);
 /* Last error of the batch (or of the last failed msfv_batch_create when b is NULL). */
 const char* msfv_batch_last_error(const msfv_batch_t* b);

@@ -1564,6 +1564,9 @@ extern "C" int64_t msfv_launch_count(const msfv_session_t* s) { return s ? s->la
 // =============================================================================
 struct msfv_batch {
   std::vector<msfv_session*> ss;
+  // the captured device buffers of every instance (the graph reads and writes these)
+  std::vector<const double*> m, dobs;
+  std::vector<double*> dpred, grad;
   std::vector<cudaStream_t> branch;  // one stream per instance, owned by the batch
   std::vector<cudaEvent_t> join;
   cudaEvent_t fork = nullptr;
@@ -1621,6 +1624,10 @@ extern "C" int msfv_batch_create(msfv_session_t* const* sessions, int K,
   msfv_batch* b = new msfv_batch();
   b->stream = static_cast<cudaStream_t>(stream);
   b->ss.assign(sessions, sessions + K);
+  b->m.assign(m_dev, m_dev + K);
+  b->dobs.assign(d_obs_dev, d_obs_dev + K);
+  b->dpred.assign(d_pred_dev, d_pred_dev + K);
+  b->grad.assign(grad_dev, grad_dev + K);
   cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
@@ -1701,6 +1708,52 @@ extern "C" int msfv_batch_check(msfv_batch_t* b) {
     }
   }
   return MSFV_OK;
+}
+
+extern "C" int msfv_batch_run_host(msfv_batch_t* b, const double* const* m_host,
+                                   const double* const* d_obs_host, double* const* d_pred_host,
+                                   double* const* grad_host) {
+  if (!b) return MSFV_ERR_ARG;
+  const size_t K = b->ss.size();
+  if (!m_host || !d_obs_host || !d_pred_host || !grad_host) {
+    b->err = "msfv_batch_run_host: NULL array";
+    return MSFV_ERR_ARG;
+  }
+  for (size_t k = 0; k < K; ++k)
+    if (!m_host[k] || !d_obs_host[k] || !d_pred_host[k] || !grad_host[k]) {
+      b->err = "msfv_batch_run_host: NULL entry";
+      return MSFV_ERR_ARG;
+    }
+  // one copy per buffer, all on the caller's stream the graph is ordered after / before
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < K && e == cudaSuccess; ++k) {
+    const msfv_session* s = b->ss[k];
+    const size_t nd = sizeof(double) * (size_t)s->Ns * s->Nr;
+    e = cudaMemcpyAsync(const_cast<double*>(b->m[k]), m_host[k], sizeof(double) * (size_t)s->Nm,
+                        cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(const_cast<double*>(b->dobs[k]), d_obs_host[k], nd,
+                          cudaMemcpyHostToDevice, b->stream);
+  }
+  if (e != cudaSuccess) {
+    b->err = std::string("batch upload: ") + cudaGetErrorString(e);
+    return MSFV_ERR_CUDA;
+  }
+  const int rc = msfv_batch_run(b);
+  if (rc != MSFV_OK) return rc;
+  for (size_t k = 0; k < K && e == cudaSuccess; ++k) {
+    const msfv_session* s = b->ss[k];
+    e = cudaMemcpyAsync(d_pred_host[k], b->dpred[k], sizeof(double) * (size_t)s->Ns * s->Nr,
+                        cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(grad_host[k], b->grad[k], sizeof(double) * (size_t)s->Nm,
+                          cudaMemcpyDeviceToHost, b->stream);
+  }
+  if (e != cudaSuccess) {
+    b->err = std::string("batch download: ") + cudaGetErrorString(e);
+    return MSFV_ERR_CUDA;
+  }
+  return msfv_batch_check(b);   // synchronises the stream, then the numerical status
 }
 
 extern "C" int msfv_batch_destroy(msfv_batch_t* b) {

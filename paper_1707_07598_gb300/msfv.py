@@ -95,6 +95,9 @@ def load(path: Optional[str] = None):
                                     ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                     vp, ctypes.POINTER(vp)]
     L.msfv_batch_create.restype = ctypes.c_int
+    L.msfv_batch_run_host.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                      ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.msfv_batch_run_host.restype = ctypes.c_int
     for f in ("msfv_batch_run", "msfv_batch_check", "msfv_batch_destroy"):
         getattr(L, f).argtypes = [vp]
         getattr(L, f).restype = ctypes.c_int
@@ -400,6 +403,30 @@ class Batch:
             raise MSFVError(rc, self._lib.msfv_batch_last_error(self._h).decode())
         for s in self.sessions:
             s.version += 1
+
+    def run_host(self, m_host, d_obs_host, d_pred_host, grad_host):
+        """One step through host buffers (msfv_batch_run_host): lists of C-contiguous
+        float64 numpy arrays (pinned memory gives the fastest copies), one per instance;
+        the outputs are written in place.  Synchronises the batch's stream."""
+        K = len(self.sessions)
+        arrs = []
+        for xs, n_of, writable in ((m_host, lambda s: s.N, False),
+                                   (d_obs_host, lambda s: s.Ns * s.Nr, False),
+                                   (d_pred_host, lambda s: s.Ns * s.Nr, True),
+                                   (grad_host, lambda s: s.N, True)):
+            if len(xs) != K:
+                raise ValueError("one host array per instance")
+            for s, x in zip(self.sessions, xs):
+                if (x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"] or x.size != n_of(s)
+                        or (writable and not x.flags["WRITEABLE"])):
+                    raise ValueError("host arrays must be C-contiguous float64 of the "
+                                     "instance's size")
+            arrs.append((ctypes.c_void_p * K)(*[ctypes.c_void_p(x.ctypes.data) for x in xs]))
+        rc = self._lib.msfv_batch_run_host(self._h, *arrs)
+        for s in self.sessions:
+            s.version += 1
+        if rc != MSFV_OK:
+            raise MSFVError(rc, self._lib.msfv_batch_last_error(self._h).decode())
 
     def check(self):
         rc = self._lib.msfv_batch_check(self._h)
