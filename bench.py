@@ -302,7 +302,7 @@ def batched_config(specs, args):
             "coarsenings": [4, 8, 16], "dipoles": "8-32", "receivers": 256,
             "corr_len": "U[0.05, 0.2]", "parallelism": "replicas x1",
             "l2": "inputs and working set of a step (tens of GB) far larger than L2",
-            "graph": "one CUDA graph per step, one branch per instance"}
+            "graph": "one CUDA graph per step: per-instance branches for the edges, faces, coarse problems and gradients, fused persistent launches for the dual-cell interiors of instances of one kernel shape"}
 
 
 # ---------------------------------------------------------------------------------
@@ -606,6 +606,31 @@ def run_batched(args):
     clk = clocks.stop()
     bt = [a.elapsed_time(b) for a, b in ev]
     K = len(specs)
+    # the same graph without fused interior launches (each instance its own branch)
+    unfused = None
+    if args.plain_reps > 0:
+        os.environ["MSFV_BATCH_FUSE"] = "0"
+        try:
+            ub = Batch(sessions, ms, dobs, stream=stream)
+        finally:
+            del os.environ["MSFV_BATCH_FUSE"]
+        ub.run()
+        ub.check()
+        ut = []
+        for _ in range(max(1, args.plain_reps)):
+            a = torch.cuda.Event(enable_timing=True)
+            b2 = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ub.run()
+            b2.record(stream)
+            torch.cuda.synchronize(dev)
+            ut.append(a.elapsed_time(b2))
+        ub.check()
+        ub.close()
+        unfused = {"value": K / (float(np.mean(ut)) / 1000.0), "unit": "solves/s",
+                   "ms_per_step": float(np.mean(ut)),
+                   "path": "the same graph with every instance in its own branch (no fused "
+                           "interior launches)"}
     total_ms = R.max_over_ranks(sum(bt), dev)
     value = R.whole_job_rate(world, K * args.steps, total_ms / 1000.0)
     d_b = [t.clone() for t in batch.d_pred]
@@ -731,7 +756,7 @@ def run_batched(args):
     ws_gb = sum(int(s.info()["workspace_bytes"]) for s in sessions) / 1e9
     if rank == 0:
         cfg = batched_config(specs, args)
-        cfg.update(recompute_instances=recompute, workspace_gb=ws_gb,
+        cfg.update(recompute_instances=recompute, workspace_gb=ws_gb, fusion=batch.info(),
                    parallelism=f"replicas x{world}", autotuned_classes=len(tuned),
                    setup_s=setup_s)
         out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -747,6 +772,7 @@ def run_batched(args):
                          "per_instance_ms_p50": float(np.percentile(inst_ms, 50)),
                          "per_instance_ms_p99": float(np.percentile(inst_ms, 99))},
                "speedup_vs_plain": value / plain_val if plain_val else None,
+               "graph_without_fusion": unfused,
                "bitwise_equal_to_plain": bool(same), "oracle_parity": parity,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches_step * args.steps, "clocks": clk,

@@ -232,7 +232,9 @@ int msfv_gn_step(msfv_session_t* s, double* m_dev, const double* d_obs_dev,
  * Captures one forward + gradient step (msfv_forward then msfv_adjoint without phi) of K
  * independent sessions as one CUDA graph: the K instances run as parallel branches, so
  * the device overlaps one instance's latency-bound phases (the coarse solve) with
- * another's local solves, and the whole step is one graph launch.  The pointers are
+ * another's local solves, the dual-cell interiors of instances of one kernel shape run
+ * in fused persistent launches (msfv_batch_info), and the whole step is one graph
+ * launch.  The pointers are
  * captured: msfv_batch_run replays the step on the same buffers, so callers refresh
  * m_dev[k] / d_obs_dev[k] in place between runs.
  *   sessions   K distinct sessions (any meshes, coarsening factors and sources)
@@ -262,6 +264,17 @@ int msfv_batch_run_host(msfv_batch_t* b, const double* const* m_host,
                         const double* const* d_obs_host, double* const* d_pred_host,
                         double* const* grad_host);
 int msfv_batch_destroy(msfv_batch_t* b);
+/* Fused interior launches of a batch.  Instances of the plain cell-centred path (no
+ * source bases, not the nodal variant, FP64 local factors) whose dual-cell interiors use
+ * the same kernel shape, window kind and factor mode form a group: the graph runs the
+ * interiors of all of a group's instances -- forward and adjoint -- in one persistent
+ * launch over one work list sorted by cost, between each instance's own lower-
+ * dimensional problems and coarse solve (the local problems are independent, Sec. 4.5;
+ * results are bit for bit those of the instances run alone).  MSFV_BATCH_FUSE=0 at
+ * msfv_batch_create keeps every instance in its own branch.
+ *   out[0] instances, out[1] fused groups, out[2] instances in them, out[3] their
+ *   interiors (one entry per fused launch's work item); n_out may be smaller than 4. */
+int msfv_batch_info(const msfv_batch_t* b, int64_t* out, int n_out);
 /* Last error of the batch (or of the last failed msfv_batch_create when b is NULL). */
 const char* msfv_batch_last_error(const msfv_batch_t* b);
 

@@ -645,14 +645,17 @@ constexpr int min_blocks(int nt, int g) { return nt * g == 128 ? 4 : (nt == 256 
 // -----------------------------------------------------------------------------
 // Basis (forward) kernel
 // -----------------------------------------------------------------------------
-template <int NT, int G>
-__global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom g, LocalLaunch L,
-                                                     const double* __restrict__ T,
-                                                     double* __restrict__ Pw, double* fac,
-                                                     int* status) {
+// MULTI: a fused launch over several instances; every array (and the geometry) is the
+// one of the entity's instance (L.inst[ents[e].inst]), the kernel arguments are unused
+// apart from the dimension.
+template <int NT, int G, bool MULTI = false>
+__global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom g0, LocalLaunch L,
+                                                     const double* __restrict__ T0,
+                                                     double* __restrict__ Pw0, double* fac0,
+                                                     int* status0) {
   extern __shared__ double smem[];
   __shared__ int s_next;
-  const int nslot = 1 << g.d;
+  const int nslot = 1 << g0.d;
   const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
   unsigned short* tab = reinterpret_cast<unsigned short*>(smem + G * gd);
   build_pair_table(tab, L.npairs);
@@ -665,6 +668,12 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom 
     if (eid >= L.n_ents) break;
     Loc E;
     load_loc(L.ents[eid], E);
+    const InstPtrs* ip = MULTI ? L.inst + L.ents[eid].inst : nullptr;
+    const DevGeom& g = MULTI ? ip->g : g0;
+    const double* __restrict__ T = MULTI ? ip->T : T0;
+    double* __restrict__ Pw = MULTI ? ip->Pw : Pw0;
+    double* fac = MULTI ? ip->fac : fac0;
+    int* status = MULTI ? ip->status : status0;
     double* fac_e = set_window(sm, E, fac);
     build_coef<NT>(g, E, T, sm, L.nmax, tid);
     // right-hand sides: T * phi_v at Dirichlet neighbours across the box boundary
@@ -708,19 +717,19 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom 
 // -----------------------------------------------------------------------------
 // Adjoint kernel
 // -----------------------------------------------------------------------------
-template <int NT, int G>
-__global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_adj(DevGeom g, LocalLaunch L,
-                                                     const double* __restrict__ T,
-                                                     const double* __restrict__ Pw, double* fac,
-                                                     const double* __restrict__ Lam,
-                                                     const int* __restrict__ rec_p,
-                                                     const int* __restrict__ rec_u,
-                                                     const double* __restrict__ ZT,
-                                                     double* __restrict__ MU,
-                                                     double* __restrict__ gTloc) {
+template <int NT, int G, bool MULTI = false>
+__global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_adj(DevGeom g0, LocalLaunch L,
+                                                     const double* __restrict__ T0,
+                                                     const double* __restrict__ Pw0, double* fac0,
+                                                     const double* __restrict__ Lam0,
+                                                     const int* __restrict__ rec_p0,
+                                                     const int* __restrict__ rec_u0,
+                                                     const double* __restrict__ ZT0,
+                                                     double* __restrict__ MU0,
+                                                     double* __restrict__ gTloc0) {
   extern __shared__ double smem[];
   __shared__ int s_next;
-  const int nslot = 1 << g.d;
+  const int nslot = 1 << g0.d;
   const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
   unsigned short* tab = reinterpret_cast<unsigned short*>(smem + G * gd);
   if (L.recompute) {
@@ -730,13 +739,24 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_adj(DevGeom 
   const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
   double* gs = L.scratch ? L.scratch + (long long)(blockIdx.x * G + grp) * L.scratch_group : nullptr;
   Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute);
-  const int S3 = (g.d == 3) ? 27 : 9;
+  const int S3 = (g0.d == 3) ? 27 : 9;
   for (;;) {
     const int eid = next_entity<NT>(L.counter + 1, &s_next, tid);
     if (eid >= L.n_ents) break;
     Loc E;
     load_loc(L.ents[eid], E);
     if (E.nvs < 2) continue;  // constant basis on this entity: no derivative
+    const InstPtrs* ip = MULTI ? L.inst + L.ents[eid].inst : nullptr;
+    const DevGeom& g = MULTI ? ip->g : g0;
+    const double* __restrict__ T = MULTI ? ip->T : T0;
+    const double* __restrict__ Pw = MULTI ? ip->Pw : Pw0;
+    double* fac = MULTI ? ip->fac : fac0;
+    const double* __restrict__ Lam = MULTI ? ip->Lam : Lam0;
+    const int* __restrict__ rec_p = MULTI ? ip->rec_p : rec_p0;
+    const int* __restrict__ rec_u = MULTI ? ip->rec_u : rec_u0;
+    const double* __restrict__ ZT = MULTI ? ip->ZT : ZT0;
+    double* __restrict__ MU = MULTI ? ip->MU : MU0;
+    double* __restrict__ gTloc = MULTI ? ip->gTloc : gTloc0;
     double* fac_e = set_window(sm, E, fac);
     if (L.recompute) {
       build_coef<NT>(g, E, T, sm, L.nmax, tid);
@@ -1036,6 +1056,40 @@ void launch_local_adjoint(const DevGeom& g, const LocalLaunch& L, const double* 
   double* f = const_cast<double*>(fac);  // written only in recompute mode (then it is scratch)
 #define MSFV_ADJ(NT, G) \
   launch_k<NT, G>(k_local_adj<NT, G>, 1, g, L, s, T, Pw, f, Lam, rec_p, rec_u, ZT, MU, gTloc)
+  MSFV_VARIANT_SWITCH(L.variant, MSFV_ADJ)
+#undef MSFV_ADJ
+}
+
+bool local_plan_fused(const DevGeom& g, LocalLaunch& L) {
+  if (local_smem_bytes(g, L) > kSmemLimit) return false;
+  const int nslot = 1 << g.d;
+  L.scratch_group = scratch_group_doubles(L.nmax, L.bmax, nslot, L.gw, L.recompute);
+#define MSFV_GRIDS(NT, G)                                             \
+  L.grid[0] = wave_ctas<NT, G>(k_local_fwd<NT, G, true>, g, L);       \
+  L.grid[1] = wave_ctas<NT, G>(k_local_adj<NT, G, true>, g, L);       \
+  L.grid[2] = 1
+  MSFV_VARIANT_SWITCH(L.variant, MSFV_GRIDS)
+#undef MSFV_GRIDS
+  return L.grid[0] > 0 && L.grid[1] > 0;
+}
+
+void launch_local_forward_fused(const DevGeom& g, const LocalLaunch& L, cudaStream_t s) {
+  if (L.n_ents == 0) return;
+  double* np = nullptr;
+  int* ni = nullptr;
+#define MSFV_FWD(NT, G) \
+  launch_k<NT, G>(k_local_fwd<NT, G, true>, 0, g, L, s, (const double*)np, np, np, ni)
+  MSFV_VARIANT_SWITCH(L.variant, MSFV_FWD)
+#undef MSFV_FWD
+}
+
+void launch_local_adjoint_fused(const DevGeom& g, const LocalLaunch& L, cudaStream_t s) {
+  if (L.n_ents == 0) return;
+  double* np = nullptr;
+  const int* ni = nullptr;
+#define MSFV_ADJ(NT, G)                                                                    \
+  launch_k<NT, G>(k_local_adj<NT, G, true>, 1, g, L, s, (const double*)np, (const double*)np, \
+                  np, (const double*)np, ni, ni, (const double*)np, np, np)
   MSFV_VARIANT_SWITCH(L.variant, MSFV_ADJ)
 #undef MSFV_ADJ
 }

@@ -49,7 +49,15 @@ struct EntDesc {
   long long fac;      // offset of the stored factor (doubles), n*(b+1) of them
   int rec_off;        // receivers inside: [rec_off, rec_off + rec_cnt) in the rec lists
   int rec_cnt;
+  int inst;           // fused launches over several instances: the entity's instance
+  int pad_;
 };
+
+struct DevGeom;
+// Per-instance arrays of a fused launch: the local kernels of a batch run the entities of
+// several instances (sessions) in one persistent launch; each entity names its instance
+// (EntDesc::inst) and the kernel takes that instance's geometry and arrays from here.
+struct InstPtrs;
 
 // Launch-wide parameters of the local-problem kernels.  The kernels are persistent: a
 // grid of at most one wave of thread groups takes entities from a work counter (largest
@@ -69,6 +77,7 @@ struct LocalLaunch {
   int* counter;       // 3 work counters (forward / adjoint / tangent), zeroed per launch
   double* scratch;    // per-group scratch in global memory (null when not needed)
   long long scratch_group;  // doubles of scratch per thread group
+  const InstPtrs* inst;     // fused launch: per-instance arrays (null: one instance)
 };
 
 struct DevGeom {
@@ -77,6 +86,20 @@ struct DevGeom {
   long long N, Nc;
   long long st[3], cst[3];
   double geo[3];      // area / distance of a face normal to axis a (unit box)
+};
+
+struct InstPtrs {
+  DevGeom g;
+  const double* T;     // face transmissibilities (then Dl)
+  double* Pw;          // basis weights
+  double* fac;         // stored local factors
+  int* status;         // numerical status
+  const double* Lam;   // adjoint: coarse-stencil collapse of lambda
+  const int* rec_p;    // adjoint: receivers inside entities
+  const int* rec_u;
+  const double* ZT;    // adjoint: receiver seeds
+  double* MU;          // adjoint: mu for the lower-dimensional entities
+  double* gTloc;       // adjoint: transmissibility gradient of the local problems
 };
 
 // Cells and primal blocks of the nodal Galerkin variant (the DevGeom of a nodal session
@@ -139,6 +162,12 @@ void launch_local_adjoint(const DevGeom& g, const LocalLaunch& L, const double* 
                           const double* Pw, const double* fac, const double* Lam,
                           const int* rec_p, const int* rec_u, const double* ZT, double* MU,
                           double* gTloc, cudaStream_t s);
+// Fused launches over several instances (L.inst set, L.ents naming each entity's
+// instance): the same kernels, every array taken from the entity's InstPtrs.  g gives
+// the dimension (equal for all instances of a fused launch).
+bool local_plan_fused(const DevGeom& g, LocalLaunch& L);
+void launch_local_forward_fused(const DevGeom& g, const LocalLaunch& L, cudaStream_t s);
+void launch_local_adjoint_fused(const DevGeom& g, const LocalLaunch& L, cudaStream_t s);
 // tangent: dPw from dT (computed from v) and lower entities' dPw
 void launch_local_tangent(const DevGeom& g, const LocalLaunch& L, const double* T,
                           const double* Dl, const double* v, const double* Pw,

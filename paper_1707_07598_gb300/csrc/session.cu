@@ -1221,11 +1221,16 @@ int run_jvec_nodal(msfv_session* s, const double* v, double* jv) {
   return check_launch(s, "msfv_jvec");
 }
 
-int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
+// part: 0 the whole forward; 1 up to (not including) the top-dimensional local problems;
+// 2 the rest (a batch runs the top-dimensional problems of several instances in one fused
+// launch between the two parts; only for sessions without source bases or the nodal
+// variant).
+int run_forward(msfv_session* s, const double* m, double* d_pred, double* u, int part = 0) {
   if (s->nodal) return run_forward_nodal(s, m, d_pred, u);
   const DevGeom& g = s->dg;
   cudaStream_t st = s->stream;
   const int d = g.d;
+  if (part != 2) {
   // numerical status (pivots, coarse convergence) refers to the latest forward and the
   // derivative calls after it
   cudaMemsetAsync(s->status, 0, sizeof(int) * (2 + (size_t)s->Ns), st);
@@ -1239,14 +1244,17 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
     launch_vertices(g, s->Pw, st);
     s->launches += 1;
   }
+  }
   for (int k = 1; k <= d; ++k) {
+    if ((part == 1 && k == d) || (part == 2 && k < d)) continue;
     PhaseScope ps(s, k == d ? PH_INTERIOR : (k == 1 ? PH_EDGE : PH_FACE));
     if (k == d && s->mixed_top)
       launch_mixed_forward(g, s->launch[k], s->T, s->Pw, s->fac32, s->status, st);
-    else
+    else if (!(part == 2 && k == d))
       launch_local_forward(g, s->launch[k], s->T, s->Pw, s->fac, s->status, st);
-    s->launches += s->launch[k].n_ents ? 1 : 0;
+    s->launches += (s->launch[k].n_ents && part == 0) ? 1 : 0;
   }
+  if (part == 1) return check_launch(s, "msfv_forward");
   if (s->src_nslots) {
     // source bases C_j on their support (edges, faces, interiors), with the factors the
     // vertex-basis kernels just stored
@@ -1298,13 +1306,16 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u) {
 
 // J^T w for w (Ns x Nr, device) at the last forward; out: N doubles.  fixed_basis: leave
 // out the derivative of the basis (the local adjoint solves), as in Sec. 4.2.
-int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = false) {
+// part: 0 all; 1 up to (not including) the top-dimensional local adjoints; 2 the rest
+// (as run_forward's parts, for fused batch launches).
+int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = false,
+              int part = 0) {
   if (s->nodal) return run_jtvec_nodal(s, w, out, fixed_basis);
   const DevGeom& g = s->dg;
   cudaStream_t st = s->stream;
   const int d = g.d;
   const double* Dl = s->T + (size_t)d * g.N;
-  {
+  if (part != 2) {
     PhaseScope ps(s, PH_ADJ_SETUP);
     launch_receiver_gather(w, s->Ns, s->Nr, s->ru_off, s->ru_idx, s->Nru, s->zc, st);
     launch_coarse_adjoint_rhs(g, s->Pw, s->zc, s->Ns, s->Nru, s->cj_off, s->cj_u, s->cj_s,
@@ -1316,7 +1327,9 @@ int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = 
     cudaMemsetAsync(s->gT, 0, sizeof(double) * (size_t)d * g.N, st);
     s->launches += 2;
   }
+  if (part == 1) return check_launch(s, "msfv_jtvec");
   for (int k = d; k >= 1 && !fixed_basis; --k) {
+    if (part == 2 && k == d) continue;
     PhaseScope ps(s, k == d ? PH_ADJ_INTERIOR : (k == 1 ? PH_ADJ_EDGE : PH_ADJ_FACE));
     if (k == d && s->mixed_top)
       launch_mixed_adjoint(g, s->launch[k], s->T, s->Pw, s->fac32, s->Lam, s->rec_p, s->rec_u,
@@ -1562,8 +1575,27 @@ extern "C" int64_t msfv_launch_count(const msfv_session_t* s) { return s ? s->la
 // =============================================================================
 // batches: one forward + gradient step of several sessions captured as one CUDA graph
 // =============================================================================
+// A group of batch instances whose top-dimensional local problems (the dual-cell
+// interiors) run in one fused persistent launch: the same kernel shape, window kind and
+// factor mode, so one kernel takes every instance's entities from one list sorted by
+// cost (uneven dual-cell sizes and instances in one persistent kernel).
+struct FusedGroup {
+  LocalLaunch L{};
+  DevGeom g{};                        // dimension and geometry of the first member
+  EntDesc* d_ents = nullptr;          // every member's interiors, largest first
+  InstPtrs* d_inst = nullptr;         // per member: its arrays
+  int* counter = nullptr;             // work counters of the fused launches
+  double* scratch = nullptr;          // per-thread-group scratch of the fused launches
+  std::vector<int> members;           // batch indices of the member instances
+  cudaStream_t st = nullptr;          // the group's branch of the graph
+  cudaEvent_t ev_fwd = nullptr, ev_adj = nullptr, ev_end = nullptr;
+};
+
 struct msfv_batch {
   std::vector<msfv_session*> ss;
+  std::vector<FusedGroup> groups;     // fused interior launches (empty: none)
+  std::vector<int> group_of;          // per instance: its group, -1 when not fused
+  std::vector<cudaEvent_t> ev_pre, ev_mid;
   // the captured device buffers of every instance (the graph reads and writes these)
   std::vector<const double*> m, dobs;
   std::vector<double*> dpred, grad;
@@ -1582,6 +1614,20 @@ namespace {
 std::string g_batch_error;
 
 void batch_release(msfv_batch* b) {
+  for (auto& G : b->groups) {
+    if (G.d_ents) cudaFree(G.d_ents);
+    if (G.d_inst) cudaFree(G.d_inst);
+    if (G.counter) cudaFree(G.counter);
+    if (G.scratch) cudaFree(G.scratch);
+    if (G.st) cudaStreamDestroy(G.st);
+    for (cudaEvent_t e : {G.ev_fwd, G.ev_adj, G.ev_end})
+      if (e) cudaEventDestroy(e);
+  }
+  b->groups.clear();
+  for (auto e : b->ev_pre) cudaEventDestroy(e);
+  for (auto e : b->ev_mid) cudaEventDestroy(e);
+  b->ev_pre.clear();
+  b->ev_mid.clear();
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto e : b->join) cudaEventDestroy(e);
@@ -1593,6 +1639,107 @@ void batch_release(msfv_batch* b) {
   b->origin = nullptr;
   b->join.clear();
   b->branch.clear();
+}
+
+// Instances whose interiors can join a fused launch: the plain cell-centred path (no
+// source bases, no nodal variant, FP64 factors) with interiors to solve.
+bool batch_fusable(const msfv_session* s) {
+  const int d = s->dg.d;
+  return !s->nodal && !s->src_nslots && !s->mixed_top && s->launch[d].n_ents > 0;
+}
+
+// Group the fusable instances by (dimension, kernel shape, window kind, factor mode) and
+// build each group's fused entity list, instance table, counters and scratch.
+cudaError_t batch_plan_groups(msfv_batch* b) {
+  const int K = (int)b->ss.size();
+  b->group_of.assign(K, -1);
+  const char* env = getenv("MSFV_BATCH_FUSE");
+  if (env && atoi(env) == 0) return cudaSuccess;
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> by_key;
+  for (int k = 0; k < K; ++k) {
+    const msfv_session* s = b->ss[k];
+    if (!batch_fusable(s)) continue;
+    const LocalLaunch& L = s->launch[s->dg.d];
+    by_key[std::make_tuple(s->dg.d, L.variant, L.gw, L.recompute)].push_back(k);
+  }
+  for (auto& kv : by_key) {
+    FusedGroup G;
+    G.members = kv.second;
+    const msfv_session* s0 = b->ss[G.members[0]];
+    const int d = s0->dg.d;
+    G.g = s0->dg;
+    G.L = s0->launch[d];
+    std::vector<EntDesc> ents;
+    std::vector<double> cost;
+    std::vector<InstPtrs> inst;
+    for (size_t q = 0; q < G.members.size(); ++q) {
+      const msfv_session* s = b->ss[G.members[q]];
+      const LocalLaunch& L = s->launch[d];
+      G.L.nmax = std::max(G.L.nmax, L.nmax);
+      G.L.bmax = std::max(G.L.bmax, L.bmax);
+      for (EntDesc e : s->h_ents[d]) {
+        e.inst = (int)q;
+        ents.push_back(e);
+        cost.push_back(entity_flops(e, __builtin_popcount((unsigned)e.slots)));
+      }
+      InstPtrs ip{};
+      ip.g = s->dg;
+      ip.T = s->T;
+      ip.Pw = s->Pw;
+      ip.fac = s->fac;
+      ip.status = s->status;
+      ip.Lam = s->Lam;
+      ip.rec_p = s->rec_p;
+      ip.rec_u = s->rec_u;
+      ip.ZT = s->ZT;
+      ip.MU = s->X;
+      ip.gTloc = s->gT;
+      inst.push_back(ip);
+    }
+    // largest first, so the persistent launch ends with the small entities
+    std::vector<size_t> order(ents.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<EntDesc> sorted;
+    sorted.reserve(ents.size());
+    for (size_t i : order) sorted.push_back(ents[i]);
+    G.L.npairs = G.L.bmax * (G.L.bmax + 1) / 2;
+    G.L.n_ents = (int)sorted.size();
+    G.L.scratch = nullptr;
+    if (!local_plan_fused(G.g, G.L)) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaMalloc(&G.d_ents, sizeof(EntDesc) * sorted.size());
+    if (e == cudaSuccess) e = cudaMalloc(&G.d_inst, sizeof(InstPtrs) * inst.size());
+    if (e == cudaSuccess) e = cudaMalloc(&G.counter, sizeof(int) * 4);
+    const long long scr = local_scratch_doubles(G.L);
+    if (e == cudaSuccess && scr > 0) e = cudaMalloc(&G.scratch, sizeof(double) * (size_t)scr);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(G.d_ents, sorted.data(), sizeof(EntDesc) * sorted.size(),
+                     cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(G.d_inst, inst.data(), sizeof(InstPtrs) * inst.size(),
+                     cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&G.ev_fwd, &G.ev_adj, &G.ev_end})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    G.L.ents = G.d_ents;
+    G.L.inst = G.d_inst;
+    G.L.counter = G.counter;
+    G.L.scratch = G.scratch;
+    const int gi = (int)b->groups.size();
+    b->groups.push_back(G);   // released with the batch even when a later step failed
+    if (e != cudaSuccess) return e;
+    for (int k : G.members) b->group_of[k] = gi;
+  }
+  for (int k = 0; k < K; ++k) {
+    cudaEvent_t a = nullptr, c = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c, cudaEventDisableTiming);
+    if (a) b->ev_pre.push_back(a);
+    if (c) b->ev_mid.push_back(c);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int batch_fail(msfv_batch* b, int code, const std::string& msg) {
@@ -1644,26 +1791,90 @@ extern "C" int msfv_batch_create(msfv_session_t* const* sessions, int K,
     return batch_fail(b, MSFV_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e));
   // every session's previous work is complete before the capture starts
   for (auto s : b->ss) cudaStreamSynchronize(s->stream);
+  e = batch_plan_groups(b);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return batch_fail(b, MSFV_ERR_CUDA,
+                      std::string("batch fused launches: ") + cudaGetErrorString(e));
+  }
   e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess)
     return batch_fail(b, MSFV_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
   int rc = MSFV_OK;
   std::string msg;
   e = cudaEventRecord(b->fork, b->origin);
-  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
+  std::vector<cudaStream_t> old_st(K);
+  std::vector<bool> old_prof(K);
+  for (int k = 0; k < K; ++k) {
     msfv_session* s = b->ss[k];
-    const cudaStream_t old = s->stream;
-    const bool prof = s->prof;
+    old_st[k] = s->stream;
+    old_prof[k] = s->prof;
     s->prof = false;
     s->stream = b->branch[k];
+  }
+  auto fail_at = [&](int k) {
+    if (rc != MSFV_OK && msg.empty()) msg = b->ss[k]->err;
+  };
+  // stage 1: per instance, everything before its interiors (unfused instances: the
+  // whole step)
+  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
+    msfv_session* s = b->ss[k];
     e = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
-    if (e == cudaSuccess) rc = msfv_forward(s, m_dev[k], d_pred_dev[k], nullptr);
-    if (e == cudaSuccess && rc == MSFV_OK) rc = msfv_adjoint(s, d_obs_dev[k], grad_dev[k], nullptr);
-    if (rc != MSFV_OK) msg = s->err;
+    if (b->group_of[k] < 0) {
+      if (e == cudaSuccess) rc = msfv_forward(s, m_dev[k], d_pred_dev[k], nullptr);
+      if (e == cudaSuccess && rc == MSFV_OK) rc = msfv_adjoint(s, d_obs_dev[k], grad_dev[k], nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(b->join[k], b->branch[k]);
+    } else {
+      if (e == cudaSuccess) rc = run_forward(s, m_dev[k], d_pred_dev[k], nullptr, 1);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev_pre[k], b->branch[k]);
+    }
+    fail_at(k);
+  }
+  // stage 2: one fused launch of the interiors of each group
+  for (auto& G : b->groups) {
+    for (int k : G.members)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(G.st, b->ev_pre[k], 0);
+    if (e == cudaSuccess) launch_local_forward_fused(G.g, G.L, G.st);
+    if (e == cudaSuccess) e = cudaEventRecord(G.ev_fwd, G.st);
+  }
+  // stage 3: per fused instance, the coarse problem, predicted data, residual and the
+  // adjoint up to its interiors
+  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
+    if (b->group_of[k] < 0) continue;
+    msfv_session* s = b->ss[k];
+    e = cudaStreamWaitEvent(b->branch[k], b->groups[b->group_of[k]].ev_fwd, 0);
+    if (e == cudaSuccess) rc = run_forward(s, m_dev[k], d_pred_dev[k], nullptr, 2);
+    if (e == cudaSuccess && rc == MSFV_OK) {
+      launch_residual(s->dpred, d_obs_dev[k], s->Ns * s->Nr, s->r, s->phi, s->stream);
+      rc = run_jtvec(s, s->r, grad_dev[k], false, 1);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_mid[k], b->branch[k]);
+    fail_at(k);
+  }
+  // stage 4: one fused launch of the interior adjoints of each group
+  for (auto& G : b->groups) {
+    for (int k : G.members)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(G.st, b->ev_mid[k], 0);
+    if (e == cudaSuccess) launch_local_adjoint_fused(G.g, G.L, G.st);
+    if (e == cudaSuccess) e = cudaEventRecord(G.ev_adj, G.st);
+  }
+  // stage 5: per fused instance, the lower-dimensional adjoints and the gradient
+  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
+    if (b->group_of[k] < 0) continue;
+    msfv_session* s = b->ss[k];
+    e = cudaStreamWaitEvent(b->branch[k], b->groups[b->group_of[k]].ev_adj, 0);
+    if (e == cudaSuccess) rc = run_jtvec(s, s->r, grad_dev[k], false, 2);
     if (e == cudaSuccess) e = cudaEventRecord(b->join[k], b->branch[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join[k], 0);
-    s->stream = old;
-    s->prof = prof;
+    fail_at(k);
+  }
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+  for (auto& G : b->groups) {
+    if (e == cudaSuccess) e = cudaEventRecord(G.ev_end, G.st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, G.ev_end, 0);
+  }
+  for (int k = 0; k < K; ++k) {
+    b->ss[k]->stream = old_st[k];
+    b->ss[k]->prof = old_prof[k];
   }
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
@@ -1754,6 +1965,17 @@ extern "C" int msfv_batch_run_host(msfv_batch_t* b, const double* const* m_host,
     return MSFV_ERR_CUDA;
   }
   return msfv_batch_check(b);   // synchronises the stream, then the numerical status
+}
+
+extern "C" int msfv_batch_info(const msfv_batch_t* b, int64_t* out, int n_out) {
+  if (!b || !out) return MSFV_ERR_ARG;
+  int64_t v[4] = {(int64_t)b->ss.size(), (int64_t)b->groups.size(), 0, 0};
+  for (const auto& G : b->groups) {
+    v[2] += (int64_t)G.members.size();
+    v[3] += G.L.n_ents;
+  }
+  for (int i = 0; i < n_out && i < 4; ++i) out[i] = v[i];
+  return MSFV_OK;
 }
 
 extern "C" int msfv_batch_destroy(msfv_batch_t* b) {

@@ -98,6 +98,8 @@ def load(path: Optional[str] = None):
     L.msfv_batch_run_host.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                       ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.msfv_batch_run_host.restype = ctypes.c_int
+    L.msfv_batch_info.argtypes = [vp, i64p, ctypes.c_int]
+    L.msfv_batch_info.restype = ctypes.c_int
     for f in ("msfv_batch_run", "msfv_batch_check", "msfv_batch_destroy"):
         getattr(L, f).argtypes = [vp]
         getattr(L, f).restype = ctypes.c_int
@@ -427,6 +429,14 @@ class Batch:
             s.version += 1
         if rc != MSFV_OK:
             raise MSFVError(rc, self._lib.msfv_batch_last_error(self._h).decode())
+
+    def info(self) -> dict:
+        out = (ctypes.c_int64 * 4)()
+        rc = self._lib.msfv_batch_info(self._h, out, 4)
+        if rc != MSFV_OK:
+            raise MSFVError(rc, "msfv_batch_info failed")
+        return dict(zip(["instances", "fused_groups", "fused_instances", "fused_entities"],
+                        list(out)))
 
     def check(self):
         rc = self._lib.msfv_batch_check(self._h)

@@ -76,6 +76,50 @@ def test_batch_graph_matches_plain_sessions_and_oracle(dev):
         s.close()
 
 
+FUSE_MIX = [((16, 16, 16), 8, 3, 20, {}), ((24, 16, 16), 8, 2, 12, {}),
+            ((16, 16, 8), 8, 4, 10, {}), ((32, 32, 32), 16, 2, 16, {}),
+            ((32, 16, 16), 16, 3, 16, {}), ((16, 16, 16), 4, 2, 9, {}),
+            ((16, 16, 16), 8, 2, 12, {"source_bases": True}),
+            ((16, 16, 16), 8, 2, 12, {"nodal": True})]
+
+
+@pytest.mark.parametrize("fuse", ["1", "0"])
+def test_fused_interior_launches_match_sessions_alone(dev, monkeypatch, fuse):
+    """Instances that share a kernel shape have their dual-cell interiors (forward and
+    adjoint) in one fused persistent launch; source-basis and nodal instances stay
+    unfused in the same graph.  Every instance's data and gradient are the bits of the
+    same session run alone, with and without fusion, and match the oracle."""
+    from paper_1707_07598_gb300.msfv import Batch, Session
+    monkeypatch.setenv("MSFV_BATCH_FUSE", fuse)
+    probs, ms, dobs, sessions = [], [], [], []
+    for k, (n, c, ns, nr, kw) in enumerate(FUSE_MIX):
+        prob = W.make_problem(n, c, ns, nr, seed=170 + k, top_layer=True, **kw)
+        probs.append(prob)
+        ms.append(torch.from_numpy(W.gaussian_random_field(n, 0.2, 180 + k)).to(dev))
+        sessions.append(Session(prob, stream=torch.cuda.Stream(dev)))
+        dobs.append(torch.from_numpy(W.noise_like((ns, nr), 1e-3, 190 + k)).to(dev))
+    torch.cuda.synchronize()
+    b = Batch(sessions, ms, dobs)
+    for _ in range(2):
+        b.run()
+        b.check()
+    for k, prob in enumerate(probs):
+        s = Session(prob)
+        d = s.forward(ms[k])
+        _, g = s.adjoint(dobs[k], want_phi=False)
+        assert torch.equal(d, b.d_pred[k]) and torch.equal(g, b.grad[k]), k
+        s.close()
+    for k in (0, 3, 5):
+        orc = Oracle(probs[k])
+        st = orc.forward(ms[k].cpu().numpy())
+        _, g_ref = orc.misfit_gradient(st, W.noise_like(st['d'].shape, 1e-3, 190 + k))
+        assert rel(b.d_pred[k].cpu().numpy(), st['d']) < TOL
+        assert rel(b.grad[k].cpu().numpy(), g_ref) < TOL
+    b.close()
+    for s in sessions:
+        s.close()
+
+
 def test_served_results_are_the_same_alone_and_in_the_mix(dev):
     from paper_1707_07598_gb300.serve import GpuBackend, Server
     reqs = W.served_requests(rate=400.0, duration=0.08, seed=11, sizes=(16, 32),
