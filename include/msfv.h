@@ -275,6 +275,17 @@ int msfv_batch_destroy(msfv_batch_t* b);
  *   out[0] instances, out[1] fused groups, out[2] instances in them, out[3] their
  *   interiors (one entry per fused launch's work item); n_out may be smaller than 4. */
 int msfv_batch_info(const msfv_batch_t* b, int64_t* out, int n_out);
+/* One step like msfv_batch_run, enqueued eagerly on the same streams instead of as the
+ * graph, with CUDA events around every fused interior launch; synchronises and reports
+ * what msfv_batch_check reports.  For measurement: the launches inside a graph cannot be
+ * timed one by one.  Per fused group gi < n_groups (host arrays, each may be NULL):
+ *   fused_ms[2 gi], fused_ms[2 gi + 1]   the forward and adjoint launch times (ms)
+ *   fused_flops[gi]                       the algorithmic FP64 flops of the forward
+ *                                         launch, counted as msfv_interior_flops counts
+ *   fused_shape[3 gi .. 3 gi + 2]         the interiors in the group's work list, their
+ *                                         largest number of unknowns and half bandwidth */
+int msfv_batch_run_timed(msfv_batch_t* b, double* fused_ms, double* fused_flops,
+                         int64_t* fused_shape, int n_groups);
 /* Last error of the batch (or of the last failed msfv_batch_create when b is NULL). */
 const char* msfv_batch_last_error(const msfv_batch_t* b);
 

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
+
 #include "msfv_internal.h"
 
 namespace msfv {
@@ -476,8 +478,8 @@ __device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int n
 // c % RS), each holding rows c..c+b.  On return Z holds the solutions; the factor is
 // stored to fac_e: column j at j*(b+1) holds 1/d_j then l_{j+1..j+b, j} (zeros past n).
 template <int NT>
-__device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short* __restrict__ tab,
-                             int nmax, int bmax, double* fac_e, int* status, int tid) {
+__device__ void factor_solve(const Loc& E, const Smem& sm, int nmax, int bmax, double* fac_e,
+                             int* status, int tid) {
   constexpr int PA = (NT < 64) ? NT : 64;
   const int n = E.n, b = E.b, nvs = E.nvs;
   const int RS = sm.RS;
@@ -544,13 +546,26 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short*
       // (3) the rest of the trailing triangle: columns base+KP+1 .. base+bj
       const int m2 = bj - KP;
       const int np2 = (m2 > 0) ? m2 * (m2 + 1) / 2 : 0;
+      // pair it of the triangle 0 <= r <= c' < m2 (c' outer, r inner): c' and r of this
+      // thread's first pair, then advanced by N2 pairs per iteration (no table needed)
+      int cp = 0, rr = 0;
+      if (t2 < np2) {
+        cp = (int)((sqrtf(8.0f * (float)t2 + 1.0f) - 1.0f) * 0.5f);
+        while (cp * (cp + 1) / 2 > t2) --cp;
+        while ((cp + 1) * (cp + 2) / 2 <= t2) ++cp;
+        rr = t2 - cp * (cp + 1) / 2;
+      }
       for (int it = t2; it < np2; it += N2) {
-        // pair table entry (c'+1, r+1) of the triangle 0 <= r <= c' < m2, read column by
-        // column from the last: column k2 = m2 - c', row k1 = k2 + r (contiguous rows of a
-        // column for consecutive threads), both shifted past the next panel
-        const unsigned short pr = tab[it];
-        const int k2 = m2 - ((pr >> 8) - 1) + KP;  // column base+k2
-        const int k1 = k2 + (pr & 255) - 1;         // row base+k1
+        // read column by column from the last: column k2 = m2 - c', row k1 = k2 + r
+        // (contiguous rows of a column for consecutive threads), both shifted past the
+        // next panel
+        const int k2 = m2 - cp + KP;  // column base+k2
+        const int k1 = k2 + rr;       // row base+k1
+        rr += N2;
+        while (rr > cp) {
+          rr -= cp + 1;
+          ++cp;
+        }
         int slot = sb + k2 - 1;
         if (slot >= RS) slot -= RS;
         const int o = slot * B1s + (k1 - k2);
@@ -590,25 +605,13 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, const unsigned short*
 // Solve L_E x = Z (nvs right-hand sides in Z) with the factor: read the stored factor,
 // or (recompute mode) factor L_E again with the forward substitution fused in.
 template <int NT>
-__device__ void derivative_solve(const Loc& E, const Smem& sm, const unsigned short* tab, int nmax,
-                                 int bmax, double* fac_e, int tid) {
+__device__ void derivative_solve(const Loc& E, const Smem& sm, int nmax, int bmax, double* fac_e,
+                                 int tid) {
   if (sm.F) {
-    factor_solve<NT>(E, sm, tab, nmax, bmax, fac_e, nullptr, tid);
+    factor_solve<NT>(E, sm, nmax, bmax, fac_e, nullptr, tid);
   } else {
     forward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
     backward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
-  }
-}
-
-// Pair table of the blocked factorisation: entry i of the triangle 0 <= r <= c', in
-// order of c' then r, holds ((c'+1) << 8) | (r+1).
-__device__ void build_pair_table(unsigned short* tab, int npairs) {
-  for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
-    int k1 = (int)((sqrtf(8.0f * i + 1.0f) - 1.0f) * 0.5f);
-    while (k1 * (k1 + 1) / 2 > i) --k1;
-    while ((k1 + 1) * (k1 + 2) / 2 <= i) ++k1;
-    const int k2 = i - k1 * (k1 + 1) / 2;
-    tab[i] = (unsigned short)(((k1 + 1) << 8) | (k2 + 1));
   }
 }
 
@@ -657,9 +660,6 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom 
   __shared__ int s_next;
   const int nslot = 1 << g0.d;
   const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
-  unsigned short* tab = reinterpret_cast<unsigned short*>(smem + G * gd);
-  build_pair_table(tab, L.npairs);
-  __syncthreads();
   const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
   double* gs = L.scratch ? L.scratch + (long long)(blockIdx.x * G + grp) * L.scratch_group : nullptr;
   Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute);
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom 
       sm.Z[(long long)i * L.nmax + p] = r;
     }
     gsync<NT>();
-    factor_solve<NT>(E, sm, tab, L.nmax, L.bmax, fac_e, status, tid);
+    factor_solve<NT>(E, sm, L.nmax, L.bmax, fac_e, status, tid);
     // write the basis weights of every slot (zeros for slots the entity lacks)
     for (int it = tid; it < E.n * nslot; it += NT) {
       const int p = it / nslot, s = it - (it / nslot) * nslot;
@@ -731,11 +731,6 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_adj(DevGeom 
   __shared__ int s_next;
   const int nslot = 1 << g0.d;
   const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
-  unsigned short* tab = reinterpret_cast<unsigned short*>(smem + G * gd);
-  if (L.recompute) {
-    build_pair_table(tab, L.npairs);
-    __syncthreads();
-  }
   const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
   double* gs = L.scratch ? L.scratch + (long long)(blockIdx.x * G + grp) * L.scratch_group : nullptr;
   Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute);
@@ -810,7 +805,7 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_adj(DevGeom 
       sm.Z[(long long)i * L.nmax + p] = w;
     }
     gsync<NT>();
-    derivative_solve<NT>(E, sm, tab, L.nmax, L.bmax, fac_e, tid);
+    derivative_solve<NT>(E, sm, L.nmax, L.bmax, fac_e, tid);
     // transmissibility gradient of the owned faces and mu for lower entities
     for (int p = tid; p < E.n; p += NT) {
       int xc[3];
@@ -880,11 +875,6 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_tan(DevGeom 
   __shared__ int s_next;
   const int nslot = 1 << g.d;
   const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
-  unsigned short* tab = reinterpret_cast<unsigned short*>(smem + G * gd);
-  if (L.recompute) {
-    build_pair_table(tab, L.npairs);
-    __syncthreads();
-  }
   const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
   double* gs = L.scratch ? L.scratch + (long long)(blockIdx.x * G + grp) * L.scratch_group : nullptr;
   Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute);
@@ -944,7 +934,7 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_tan(DevGeom 
       sm.Z[(long long)i * L.nmax + p] = r;
     }
     gsync<NT>();
-    derivative_solve<NT>(E, sm, tab, L.nmax, L.bmax, fac_e, tid);
+    derivative_solve<NT>(E, sm, L.nmax, L.bmax, fac_e, tid);
     for (int it = tid; it < E.n * nslot; it += NT) {
       const int p = it / nslot, s = it - (it / nslot) * nslot;
       int xc[3];
@@ -964,8 +954,7 @@ namespace {
 template <int NT, int G>
 size_t smem_bytes(const DevGeom& g, const LocalLaunch& L) {
   const int nslot = 1 << g.d;
-  return (size_t)G * group_doubles(L.nmax, L.bmax, nslot, L.gw) * sizeof(double) +
-         ((size_t)L.npairs * sizeof(unsigned short) + 15) / 16 * 16;
+  return (size_t)G * group_doubles(L.nmax, L.bmax, nslot, L.gw) * sizeof(double);
 }
 
 constexpr size_t kSmemLimit = 227 * 1024;
@@ -983,6 +972,12 @@ int wave_ctas(K kern, const DevGeom& g, const LocalLaunch& L) {
     per_sm = 1;
   if (per_sm < 1) per_sm = 1;
   if (sms < 1) sms = 1;
+  // MSFV_LOCAL_CTAS_PER_SM caps the resident thread groups per SM of the global-window
+  // kernels (their windows share L2)
+  if (L.gw) {
+    const char* cap = getenv("MSFV_LOCAL_CTAS_PER_SM");
+    if (cap && atoi(cap) > 0 && atoi(cap) < per_sm) per_sm = atoi(cap);
+  }
   const long long need = (L.n_ents + G - 1) / G;
   const long long wave = (long long)sms * per_sm;
   return (int)(need < wave ? (need > 0 ? need : 1) : wave);

@@ -376,4 +376,46 @@ void launch_mg_setup(const MGHost& H, int* status, cudaStream_t s);
 cudaError_t launch_mg_solve(const MGHost& H, double* rhs, int Ns, int transpose, int* status,
                             cudaStream_t s);
 
+
+// ---- nested-dissection LU of the pinned coarse matrix (k_nd.cu) ----------------------
+struct NDFrontDev {
+  int p, F;             // pivots, front size (pivots + update nodes)
+  long long off;        // front matrix (F x F, row-major) in the pool
+  long long woff;       // first of its F - p update rows in the update-vector pool
+  int idx;              // its F global node ids in the index pool
+  int ch[2];            // child fronts (-1: none)
+  int cmap[2];          // per child: F ints, position of each node in the child's list or -1
+  int pad_;
+};
+struct NDHost {
+  int d = 0, nlev = 0, Ns = 0, maxF = 0;
+  int max_team = 8;               // largest cluster per front (set before nd_setup)
+  int g[3] = {1, 1, 1};
+  long long Nc = 0;
+  std::vector<int> lev_off;       // fronts of step l (deepest level first): [lev_off[l], lev_off[l+1])
+  std::vector<int> lev_team;      // CTAs (one cluster) per front of each step
+  std::vector<int> lev_maxF;      // largest front of each step
+  std::vector<NDFrontDev> h_fronts;
+  std::vector<int> h_idx, h_cmap;
+  long long pool = 0;             // doubles of front storage
+  long long wpool = 0;            // update rows (times Ns doubles)
+  NDFrontDev* fronts = nullptr;   // device copies
+  int* idx = nullptr;
+  int* cmap = nullptr;
+  double* F = nullptr;            // front pool
+  double* W = nullptr;            // update vectors of the solves: wpool x Ns
+};
+// coarse meshes up to this many nodes use the nested-dissection LU by default (3D; the
+// factor grows as Nc^2 there, as Nc^1.5 in 2D)
+constexpr long long kNdMaxNodes3 = 8192;
+constexpr long long kNdMaxNodes2 = 65536;
+bool nd_setup(NDHost& H, const DevGeom& g, int Ns);
+// largest cluster (CTAs) the factor kernel runs with on this device: 16 or 8
+int nd_max_team();
+long long nd_device_bytes(const NDHost& H);
+// factorisation of the pinned A_c (offset-major 3^d stencil); status[0] = 1 on a zero or
+// non-finite pivot
+cudaError_t launch_nd_factor(const NDHost& H, const double* Ac, int* status, cudaStream_t s);
+// rhs: Ns x Nc, solved in place (entry 0 of every solution is zero); transpose: A_c^T
+cudaError_t launch_nd_solve(const NDHost& H, double* rhs, int Ns, int transpose, cudaStream_t s);
 }  // namespace msfv

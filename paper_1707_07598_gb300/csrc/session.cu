@@ -132,6 +132,8 @@ struct msfv_session {
   BandLU band{};
   MGHost mg{};
   bool use_mg = false;
+  NDHost nd{};
+  bool use_nd = false;   // nested-dissection LU (takes precedence over use_mg)
   bool have_forward = false;
   cudaError_t launch_error = cudaSuccess;
   std::string err;
@@ -740,9 +742,19 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   {
     const double band_work = (double)s->band.n * s->band.kl * (s->band.kl + s->band.ku);
     s->use_mg = band_work > 1e6;
+    // the nested-dissection LU for coarse meshes between the banded LU and the multigrid
+    // range: its factor is reused by every solve at one model
+    s->use_nd = s->use_mg && Nc <= (d == 3 ? kNdMaxNodes3 : kNdMaxNodes2);
     const char* env = getenv("MSFV_COARSE_SOLVER");
-    if (env && !strcmp(env, "band")) s->use_mg = false;
-    if (env && !strcmp(env, "mg")) s->use_mg = true;
+    if (env && !strcmp(env, "band")) s->use_mg = s->use_nd = false;
+    if (env && !strcmp(env, "mg")) {
+      s->use_mg = true;
+      s->use_nd = false;
+    }
+    if (env && !strcmp(env, "nd")) s->use_nd = true;
+    if (s->use_nd) s->nd.max_team = nd_max_team();
+    if (s->use_nd && !nd_setup(s->nd, g, s->Ns)) s->use_nd = false;
+    if (s->use_nd) s->use_mg = false;
     if (s->use_mg) {
       mg_setup_levels(s->mg, g);
       // V-cycle smoothing (pre, post with A_c; pre, post with A_c^T), each 1 or 2 sweeps
@@ -764,8 +776,9 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
                 sizeof(double) * ((size_t)3 * Nc * S3 + (size_t)5 * s->Ns * Nc +
                                   (size_t)4 * s->Ns * s->Nr + 1 + (size_t)s->Ns * s->Nru +
                                   (size_t)s->Nru * Ssz + 2 * N) +
-                (s->use_mg ? sizeof(double) * ((size_t)s->Ns * (2 * s->mg.m + 3) * Nc + 4 * Nc * S3)
-                           : sizeof(double) * (size_t)s->band.ldab * (size_t)s->band.n);
+                (s->use_nd ? (size_t)nd_device_bytes(s->nd)
+                 : s->use_mg ? sizeof(double) * ((size_t)s->Ns * (2 * s->mg.m + 3) * Nc + 4 * Nc * S3)
+                             : sizeof(double) * (size_t)s->band.ldab * (size_t)s->band.n);
   // local-problem scratch (one buffer: the classes run one after another on the stream)
   auto scratch_bytes = [&]() {
     long long m = 0;
@@ -871,7 +884,14 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   s->rec_u = dalloc<int>(s, rec_u.size(), &ce);
   s->status = dalloc<int>(s, 2 + (size_t)s->Ns, &ce);
   s->band.status = s->status + 1;
-  if (!s->use_mg) {
+  if (s->use_nd) {
+    NDHost& H = s->nd;
+    H.fronts = dalloc<NDFrontDev>(s, H.h_fronts.size(), &ce);
+    H.idx = dalloc<int>(s, H.h_idx.size(), &ce);
+    H.cmap = dalloc<int>(s, std::max<size_t>(1, H.h_cmap.size()), &ce);
+    H.F = dalloc<double>(s, (size_t)H.pool, &ce);
+    H.W = dalloc<double>(s, (size_t)std::max(1LL, H.wpool) * s->Ns, &ce);
+  } else if (!s->use_mg) {
     s->band.ab = dalloc<double>(s, (size_t)s->band.ldab * (size_t)s->band.n, &ce);
     s->band.piv = dalloc<int>(s, (size_t)s->band.n, &ce);
   } else {
@@ -975,6 +995,11 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
   if (ce == cudaSuccess) ce = upload(s->rec_p, rec_p, st);
   if (ce == cudaSuccess) ce = upload(s->rec_u, rec_u, st);
   if (ce == cudaSuccess) ce = upload(s->rq, rq, st);
+  if (ce == cudaSuccess && s->use_nd) {
+    ce = upload(s->nd.fronts, s->nd.h_fronts, st);
+    if (ce == cudaSuccess) ce = upload(s->nd.idx, s->nd.h_idx, st);
+    if (ce == cudaSuccess && !s->nd.h_cmap.empty()) ce = upload(s->nd.cmap, s->nd.h_cmap, st);
+  }
   for (int k = 1; k <= d && ce == cudaSuccess; ++k) ce = upload(s->d_ents[k], s->h_ents[k], st);
   if (ce == cudaSuccess && s->d_ents_adj) ce = upload(s->d_ents_adj, s->h_ents_adj, st);
   if ((nodal || s->src_nslots) && ce == cudaSuccess) {
@@ -1075,7 +1100,11 @@ namespace {
 
 void coarse_solve(msfv_session* s, double* rhs, int transpose) {
   const long long Nc = s->geo.Nc;
-  if (s->use_mg) {
+  if (s->use_nd) {
+    const cudaError_t e = launch_nd_solve(s->nd, rhs, s->Ns, transpose, s->stream);
+    if (e != cudaSuccess) s->launch_error = e;
+    s->launches += 2LL * s->nd.nlev;
+  } else if (s->use_mg) {
     MGHost H = s->mg;
     H.iters = s->mg.iters + (transpose ? s->Ns : 0);
     const cudaError_t e = launch_mg_solve(H, rhs, s->Ns, transpose, s->status + 2, s->stream);
@@ -1088,7 +1117,11 @@ void coarse_solve(msfv_session* s, double* rhs, int transpose) {
 
 // factorisation (banded LU) or hierarchy (multigrid) of the new A_c
 void coarse_prepare(msfv_session* s) {
-  if (s->use_mg) {
+  if (s->use_nd) {
+    const cudaError_t e = launch_nd_factor(s->nd, s->Ac, s->status + 1, s->stream);
+    if (e != cudaSuccess) s->launch_error = e;
+    s->launches += 2LL * s->nd.nlev;
+  } else if (s->use_mg) {
     launch_mg_setup(s->mg, s->status + 1, s->stream);
     s->launches += 2 * s->mg.nlev;
   } else {
@@ -1512,7 +1545,8 @@ extern "C" int msfv_info(const msfv_session_t* s, int64_t* out, int n_out) {
   for (int k = 1; k <= s->dg.d; ++k) gw |= s->launch[k].gw ? (1 << k) : 0;
   int64_t v[15] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
                    (int64_t)(s->h_ents[1].size() + s->h_ents[2].size() + s->h_ents[3].size()),
-                   (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, s->use_mg ? 1 : 0, it[0], it[1],
+                   (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, s->use_nd ? 2 : (s->use_mg ? 1 : 0),
+                   it[0], it[1],
                    s->use_mg ? (s->mg.all ? s->mg.ncta : s->mg.group) : 0,
                    s->recompute ? 1 : 0, gw, s->src_nslots, s->src_nvals};
   for (int i = 0; i < n_out && i < 15; ++i) out[i] = v[i];
@@ -1589,6 +1623,8 @@ struct FusedGroup {
   std::vector<int> members;           // batch indices of the member instances
   cudaStream_t st = nullptr;          // the group's branch of the graph
   cudaEvent_t ev_fwd = nullptr, ev_adj = nullptr, ev_end = nullptr;
+  cudaEvent_t t_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // timed run: around the launches
+  double flops = 0.0;                 // algorithmic FP64 flops of the fused forward launch
 };
 
 struct msfv_batch {
@@ -1620,7 +1656,7 @@ void batch_release(msfv_batch* b) {
     if (G.counter) cudaFree(G.counter);
     if (G.scratch) cudaFree(G.scratch);
     if (G.st) cudaStreamDestroy(G.st);
-    for (cudaEvent_t e : {G.ev_fwd, G.ev_adj, G.ev_end})
+    for (cudaEvent_t e : {G.ev_fwd, G.ev_adj, G.ev_end, G.t_ev[0], G.t_ev[1], G.t_ev[2], G.t_ev[3]})
       if (e) cudaEventDestroy(e);
   }
   b->groups.clear();
@@ -1722,6 +1758,8 @@ cudaError_t batch_plan_groups(msfv_batch* b) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking);
     for (cudaEvent_t* ev : {&G.ev_fwd, &G.ev_adj, &G.ev_end})
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) e = cudaEventCreate(&G.t_ev[q]);
+    for (size_t i = 0; i < ents.size(); ++i) G.flops += cost[i];
     G.L.ents = G.d_ents;
     G.L.inst = G.d_inst;
     G.L.counter = G.counter;
@@ -1752,6 +1790,101 @@ int batch_fail(msfv_batch* b, int code, const std::string& msg) {
   return code;
 }
 }  // namespace
+
+// Enqueue one forward + gradient step of every instance, starting on b->origin and
+// ending there: per-instance branches, the fused interior launches of each group between
+// them (see msfv_batch_info).  Used under stream capture (the graph) and eagerly (the timed
+// run, timed = true: events around each fused launch).  On failure *msg names it.
+int batch_enqueue(msfv_batch* b, bool timed, std::string* msg_out, cudaError_t* err_out) {
+  const int K = (int)b->ss.size();
+  // the timed run serialises everything on the batch's stream, so that each fused launch
+  // is timed alone
+  auto BR = [&](int k) { return timed ? b->origin : b->branch[k]; };
+  auto GS = [&](const FusedGroup& G) { return timed ? b->origin : G.st; };
+  std::string msg;
+  int rc = MSFV_OK;
+  cudaError_t e = cudaEventRecord(b->fork, b->origin);
+  std::vector<cudaStream_t> old_st(K);
+  std::vector<bool> old_prof(K);
+  for (int k = 0; k < K; ++k) {
+    msfv_session* s = b->ss[k];
+    old_st[k] = s->stream;
+    old_prof[k] = s->prof;
+    s->prof = false;
+    s->stream = BR(k);
+  }
+  auto fail_at = [&](int k) {
+    if (rc != MSFV_OK && msg.empty()) msg = b->ss[k]->err;
+  };
+  // stage 1: per instance, everything before its interiors (unfused instances: the
+  // whole step)
+  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
+    msfv_session* s = b->ss[k];
+    e = cudaStreamWaitEvent(BR(k), b->fork, 0);
+    if (b->group_of[k] < 0) {
+      if (e == cudaSuccess) rc = msfv_forward(s, b->m[k], b->dpred[k], nullptr);
+      if (e == cudaSuccess && rc == MSFV_OK) rc = msfv_adjoint(s, b->dobs[k], b->grad[k], nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(b->join[k], BR(k));
+    } else {
+      if (e == cudaSuccess) rc = run_forward(s, b->m[k], b->dpred[k], nullptr, 1);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev_pre[k], BR(k));
+    }
+    fail_at(k);
+  }
+  // stage 2: one fused launch of the interiors of each group
+  for (auto& G : b->groups) {
+    for (int k : G.members)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(GS(G), b->ev_pre[k], 0);
+    if (e == cudaSuccess && timed) e = cudaEventRecord(G.t_ev[0], GS(G));
+    if (e == cudaSuccess) launch_local_forward_fused(G.g, G.L, GS(G));
+    if (e == cudaSuccess && timed) e = cudaEventRecord(G.t_ev[1], GS(G));
+    if (e == cudaSuccess) e = cudaEventRecord(G.ev_fwd, GS(G));
+  }
+  // stage 3: per fused instance, the coarse problem, predicted data, residual and the
+  // adjoint up to its interiors
+  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
+    if (b->group_of[k] < 0) continue;
+    msfv_session* s = b->ss[k];
+    e = cudaStreamWaitEvent(BR(k), b->groups[b->group_of[k]].ev_fwd, 0);
+    if (e == cudaSuccess) rc = run_forward(s, b->m[k], b->dpred[k], nullptr, 2);
+    if (e == cudaSuccess && rc == MSFV_OK) {
+      launch_residual(s->dpred, b->dobs[k], s->Ns * s->Nr, s->r, s->phi, s->stream);
+      rc = run_jtvec(s, s->r, b->grad[k], false, 1);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_mid[k], BR(k));
+    fail_at(k);
+  }
+  // stage 4: one fused launch of the interior adjoints of each group
+  for (auto& G : b->groups) {
+    for (int k : G.members)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(GS(G), b->ev_mid[k], 0);
+    if (e == cudaSuccess && timed) e = cudaEventRecord(G.t_ev[2], GS(G));
+    if (e == cudaSuccess) launch_local_adjoint_fused(G.g, G.L, GS(G));
+    if (e == cudaSuccess && timed) e = cudaEventRecord(G.t_ev[3], GS(G));
+    if (e == cudaSuccess) e = cudaEventRecord(G.ev_adj, GS(G));
+  }
+  // stage 5: per fused instance, the lower-dimensional adjoints and the gradient
+  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
+    if (b->group_of[k] < 0) continue;
+    msfv_session* s = b->ss[k];
+    e = cudaStreamWaitEvent(BR(k), b->groups[b->group_of[k]].ev_adj, 0);
+    if (e == cudaSuccess) rc = run_jtvec(s, s->r, b->grad[k], false, 2);
+    if (e == cudaSuccess) e = cudaEventRecord(b->join[k], BR(k));
+    fail_at(k);
+  }
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+  for (auto& G : b->groups) {
+    if (e == cudaSuccess) e = cudaEventRecord(G.ev_end, GS(G));
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, G.ev_end, 0);
+  }
+  for (int k = 0; k < K; ++k) {
+    b->ss[k]->stream = old_st[k];
+    b->ss[k]->prof = old_prof[k];
+  }
+  *msg_out = msg;
+  *err_out = e;
+  return rc;
+}
 
 extern "C" int msfv_batch_create(msfv_session_t* const* sessions, int K,
                                  const double* const* m_dev, const double* const* d_obs_dev,
@@ -1800,82 +1933,8 @@ extern "C" int msfv_batch_create(msfv_session_t* const* sessions, int K,
   e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess)
     return batch_fail(b, MSFV_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-  int rc = MSFV_OK;
   std::string msg;
-  e = cudaEventRecord(b->fork, b->origin);
-  std::vector<cudaStream_t> old_st(K);
-  std::vector<bool> old_prof(K);
-  for (int k = 0; k < K; ++k) {
-    msfv_session* s = b->ss[k];
-    old_st[k] = s->stream;
-    old_prof[k] = s->prof;
-    s->prof = false;
-    s->stream = b->branch[k];
-  }
-  auto fail_at = [&](int k) {
-    if (rc != MSFV_OK && msg.empty()) msg = b->ss[k]->err;
-  };
-  // stage 1: per instance, everything before its interiors (unfused instances: the
-  // whole step)
-  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
-    msfv_session* s = b->ss[k];
-    e = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
-    if (b->group_of[k] < 0) {
-      if (e == cudaSuccess) rc = msfv_forward(s, m_dev[k], d_pred_dev[k], nullptr);
-      if (e == cudaSuccess && rc == MSFV_OK) rc = msfv_adjoint(s, d_obs_dev[k], grad_dev[k], nullptr);
-      if (e == cudaSuccess) e = cudaEventRecord(b->join[k], b->branch[k]);
-    } else {
-      if (e == cudaSuccess) rc = run_forward(s, m_dev[k], d_pred_dev[k], nullptr, 1);
-      if (e == cudaSuccess) e = cudaEventRecord(b->ev_pre[k], b->branch[k]);
-    }
-    fail_at(k);
-  }
-  // stage 2: one fused launch of the interiors of each group
-  for (auto& G : b->groups) {
-    for (int k : G.members)
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(G.st, b->ev_pre[k], 0);
-    if (e == cudaSuccess) launch_local_forward_fused(G.g, G.L, G.st);
-    if (e == cudaSuccess) e = cudaEventRecord(G.ev_fwd, G.st);
-  }
-  // stage 3: per fused instance, the coarse problem, predicted data, residual and the
-  // adjoint up to its interiors
-  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
-    if (b->group_of[k] < 0) continue;
-    msfv_session* s = b->ss[k];
-    e = cudaStreamWaitEvent(b->branch[k], b->groups[b->group_of[k]].ev_fwd, 0);
-    if (e == cudaSuccess) rc = run_forward(s, m_dev[k], d_pred_dev[k], nullptr, 2);
-    if (e == cudaSuccess && rc == MSFV_OK) {
-      launch_residual(s->dpred, d_obs_dev[k], s->Ns * s->Nr, s->r, s->phi, s->stream);
-      rc = run_jtvec(s, s->r, grad_dev[k], false, 1);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(b->ev_mid[k], b->branch[k]);
-    fail_at(k);
-  }
-  // stage 4: one fused launch of the interior adjoints of each group
-  for (auto& G : b->groups) {
-    for (int k : G.members)
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(G.st, b->ev_mid[k], 0);
-    if (e == cudaSuccess) launch_local_adjoint_fused(G.g, G.L, G.st);
-    if (e == cudaSuccess) e = cudaEventRecord(G.ev_adj, G.st);
-  }
-  // stage 5: per fused instance, the lower-dimensional adjoints and the gradient
-  for (int k = 0; k < K && rc == MSFV_OK && e == cudaSuccess; ++k) {
-    if (b->group_of[k] < 0) continue;
-    msfv_session* s = b->ss[k];
-    e = cudaStreamWaitEvent(b->branch[k], b->groups[b->group_of[k]].ev_adj, 0);
-    if (e == cudaSuccess) rc = run_jtvec(s, s->r, grad_dev[k], false, 2);
-    if (e == cudaSuccess) e = cudaEventRecord(b->join[k], b->branch[k]);
-    fail_at(k);
-  }
-  for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->origin, b->join[k], 0);
-  for (auto& G : b->groups) {
-    if (e == cudaSuccess) e = cudaEventRecord(G.ev_end, G.st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, G.ev_end, 0);
-  }
-  for (int k = 0; k < K; ++k) {
-    b->ss[k]->stream = old_st[k];
-    b->ss[k]->prof = old_prof[k];
-  }
+  int rc = batch_enqueue(b, false, &msg, &e);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
   b->graph = g;
@@ -1965,6 +2024,45 @@ extern "C" int msfv_batch_run_host(msfv_batch_t* b, const double* const* m_host,
     return MSFV_ERR_CUDA;
   }
   return msfv_batch_check(b);   // synchronises the stream, then the numerical status
+}
+
+extern "C" int msfv_batch_run_timed(msfv_batch_t* b, double* fused_ms, double* fused_flops,
+                                    int64_t* fused_shape, int n_groups) {
+  if (!b) return MSFV_ERR_ARG;
+  cudaError_t e = cudaEventRecord(b->ev_in, b->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev_in, 0);
+  std::string msg;
+  int rc = MSFV_OK;
+  if (e == cudaSuccess) rc = batch_enqueue(b, true, &msg, &e);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->origin);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_out, 0);
+  if (rc != MSFV_OK) {
+    b->err = "timed run: " + msg;
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    b->err = std::string("timed run: ") + cudaGetErrorString(e);
+    return MSFV_ERR_CUDA;
+  }
+  rc = msfv_batch_check(b);   // synchronises
+  if (rc != MSFV_OK) return rc;
+  for (int gi = 0; gi < (int)b->groups.size() && gi < n_groups; ++gi) {
+    const FusedGroup& G = b->groups[gi];
+    float f = 0.0f, a = 0.0f;
+    cudaEventElapsedTime(&f, G.t_ev[0], G.t_ev[1]);
+    cudaEventElapsedTime(&a, G.t_ev[2], G.t_ev[3]);
+    if (fused_ms) {
+      fused_ms[2 * gi] = f;
+      fused_ms[2 * gi + 1] = a;
+    }
+    if (fused_flops) fused_flops[gi] = G.flops;
+    if (fused_shape) {
+      fused_shape[3 * gi] = G.L.n_ents;
+      fused_shape[3 * gi + 1] = G.L.nmax;
+      fused_shape[3 * gi + 2] = G.L.bmax;
+    }
+  }
+  return MSFV_OK;
 }
 
 extern "C" int msfv_batch_info(const msfv_batch_t* b, int64_t* out, int n_out) {

@@ -98,6 +98,8 @@ def load(path: Optional[str] = None):
     L.msfv_batch_run_host.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                       ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.msfv_batch_run_host.restype = ctypes.c_int
+    L.msfv_batch_run_timed.argtypes = [vp, dp, dp, i64p, ctypes.c_int]
+    L.msfv_batch_run_timed.restype = ctypes.c_int
     L.msfv_batch_info.argtypes = [vp, i64p, ctypes.c_int]
     L.msfv_batch_info.restype = ctypes.c_int
     for f in ("msfv_batch_run", "msfv_batch_check", "msfv_batch_destroy"):
@@ -429,6 +431,25 @@ class Batch:
             s.version += 1
         if rc != MSFV_OK:
             raise MSFVError(rc, self._lib.msfv_batch_last_error(self._h).decode())
+
+    def run_timed(self) -> list:
+        """One step enqueued eagerly with CUDA events around the fused interior launches
+        (msfv_batch_run_timed): per fused group a dict of the forward and adjoint launch
+        times (ms), the forward flops, the entities and their largest size and half
+        bandwidth.  Synchronises."""
+        ng = self.info()["fused_groups"]
+        n = max(1, ng)
+        ms = (ctypes.c_double * (2 * n))()
+        fl = (ctypes.c_double * n)()
+        sh = (ctypes.c_int64 * (3 * n))()
+        rc = self._lib.msfv_batch_run_timed(self._h, ms, fl, sh, n)
+        for s in self.sessions:
+            s.version += 1
+        if rc != MSFV_OK:
+            raise MSFVError(rc, self._lib.msfv_batch_last_error(self._h).decode())
+        return [{"fwd_ms": ms[2 * g], "adj_ms": ms[2 * g + 1], "flops": fl[g],
+                 "entities": int(sh[3 * g]), "nmax": int(sh[3 * g + 1]), "bmax": int(sh[3 * g + 2])}
+                for g in range(ng)]
 
     def info(self) -> dict:
         out = (ctypes.c_int64 * 4)()

@@ -93,7 +93,7 @@ def test_surface_survey_64(dev):
     check_all(prob, m, dev, seed=83, derivs=False)
 
 
-@pytest.mark.parametrize("solver", ["band", "mg"])
+@pytest.mark.parametrize("solver", ["band", "mg", "nd"])
 def test_both_coarse_solvers(dev, monkeypatch, solver):
     monkeypatch.setenv("MSFV_COARSE_SOLVER", solver)
     prob = W.make_problem((32, 32, 32), 4, 3, 40, seed=91, top_layer=False, nodal=True)

@@ -191,18 +191,19 @@ def test_config_3d_128_full(dev):
     s.close()
 
 
-@pytest.mark.parametrize("solver", ["band", "mg"])
+@pytest.mark.parametrize("solver", ["band", "mg", "nd"])
 @pytest.mark.parametrize("n,c,ns,nr", [((32, 32), 4, 2, 16), ((20, 15), 5, 2, 8),
                                        ((16, 16, 16), 4, 3, 20), ((24, 16, 16), 8, 4, 30),
                                        ((12, 10, 6), 2, 2, 9), ((128, 128), 4, 3, 24),
                                        ((320, 256), 4, 2, 20), ((48, 48, 48), 4, 3, 30)])
 def test_both_coarse_solvers_match_oracle(dev, monkeypatch, solver, n, c, ns, nr):
-    """Banded LU and multigrid GMRES both reproduce the oracle's pinned coarse solve."""
+    """Banded LU, multigrid GMRES and the nested-dissection LU all reproduce the oracle's
+    pinned coarse solve (forward, transposed in the gradient, and again in J v)."""
     monkeypatch.setenv("MSFV_COARSE_SOLVER", solver)
     prob = W.make_problem(n, c, ns, nr, seed=51, top_layer=len(n) == 3)
     m = W.gaussian_random_field(n, 0.2, 52)
     orc, st, s, d, u, phi, g, d_obs, phi_ref, g_ref = run_pair(prob, m, dev)
-    assert s.info()["coarse_solver"] == (1 if solver == "mg" else 0)
+    assert s.info()["coarse_solver"] == {"band": 0, "mg": 1, "nd": 2}[solver]
     assert rel(d, st['d']) < TOL and rel(u, st['U']) < TOL and rel(g, g_ref) < TOL
     v = W.noise_like(prob.N, 1.0, 53)
     assert rel(s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy(), orc.jvec(st, v)) < TOL

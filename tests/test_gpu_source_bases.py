@@ -127,7 +127,7 @@ def test_coarsening_16_and_factor_windows(dev, monkeypatch, window):
     check_all(prob, m, dev, seed=83)
 
 
-@pytest.mark.parametrize("solver", ["band", "mg"])
+@pytest.mark.parametrize("solver", ["band", "mg", "nd"])
 def test_both_coarse_solvers(dev, monkeypatch, solver):
     monkeypatch.setenv("MSFV_COARSE_SOLVER", solver)
     prob = W.make_problem((32, 32, 32), 4, 4, 40, seed=91, top_layer=True, source_bases=True)
