@@ -335,9 +335,12 @@ int msfv_set_wait_limit(msfv_session_t* s, int64_t ns);
 
 /* Sizes of the session: out[0]=N, out[1]=Nc, out[2]=Ns, out[3]=Nr, out[4]=number of
  * local problems (edges + faces + dual-cell interiors), out[5]=workspace bytes,
- * out[6]=stored-factor bytes, out[7]=coarse solver (0 banded LU, 1 multigrid GMRES),
+ * out[6]=stored-factor bytes, out[7]=coarse solver (0 banded LU, 1 multigrid GMRES,
+ * 2 nested-dissection LU -- the default for 3D coarse meshes of more than a few hundred and
+ * at most 8192 nodes, 2D ones up to 65536; MSFV_COARSE_SOLVER=band / nd / mg at msfv_setup
+ * forces one),
  * out[8] / out[9]=largest number of GMRES iterations over the right-hand sides of the
- * last coarse solve with A_c / A_c^T (0 for the banded LU; reading them synchronises
+ * last coarse solve with A_c / A_c^T (0 for the LU solvers; reading them synchronises
  * the stream), out[10]=thread-block cluster size (CTAs, one per SM) the multigrid
  * GMRES kernel gives each right-hand side -- or, for coarse meshes of 65536 nodes and
  * more, the CTAs of the cooperative grid that works on all right-hand sides at once
@@ -349,6 +352,9 @@ int msfv_set_wait_limit(msfv_session_t* s, int64_t ns);
  * The environment variable MSFV_LOCAL_WINDOW=global at msfv_setup forces the global-
  * memory factorisation for every class (for testing). */
 int msfv_info(const msfv_session_t* s, int64_t* out, int n_out);
+
+/* (Environment at msfv_setup: MSFV_LOCAL_CTAS_PER_SM=n caps the resident thread groups
+ * per SM of the local kernels whose factor window lives in global memory, 3D c >= 12.) */
 
 /* Barrier time stamps of the multigrid GMRES coarse solver, recorded only when the
  * environment variable MSFV_TRACE_COARSE=1 was set at msfv_setup: each entry is

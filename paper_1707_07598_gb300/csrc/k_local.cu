@@ -144,23 +144,37 @@ struct Smem {
 };
 
 // Panel width of the blocked factorisation (columns factored per rank-KP update).
-constexpr int KP = 4;
+#ifndef MSFV_KP
+#define MSFV_KP 4
+#endif
+constexpr int KP_DEF = MSFV_KP;
+// The forward kernels with the factor window in global memory (3D c >= 12) factor in
+// panels of 8: each panel updates the trailing window (in L2) once, so wider panels halve
+// the window traffic; the shared-memory windows keep panels of 4.
+#ifndef MSFV_KP_GW
+#define MSFV_KP_GW 8
+#endif
+constexpr int KP_GW = MSFV_KP_GW;
 // Rows per block of the blocked solve sweeps.
-constexpr int KS = 8;
+#ifndef MSFV_KS
+#define MSFV_KS 8
+#endif
+constexpr int KS = MSFV_KS;
 
 __host__ __device__ inline int row_stride(int B1) { return (B1 & 1) ? B1 + 1 : B1; }
 // ring of factor columns: the factorisation needs bmax+KP slots, the blocked sweeps
 // bmax+KS for the current block plus two blocks of prefetch
 __host__ __device__ inline int ring_slots(int bmax) { return bmax + 3 * KS; }
-__host__ __device__ inline int panel_stride(int bmax) { return bmax + KP + 1; }
+__host__ __device__ inline int panel_stride(int bmax, int kp) { return bmax + kp + 1; }
 
 constexpr int kGlobalRing = 1 << 30;
 
 // Shared-memory doubles of one thread group: the panel buffers, plus (shared window)
 // the ring, the right-hand sides and the coefficients.
-__host__ __device__ inline long long group_doubles(int nmax, int bmax, int nslot, int gw) {
+__host__ __device__ inline long long group_doubles(int nmax, int bmax, int nslot, int gw,
+                                                   int kp = KP_DEF) {
   const int B1 = bmax + 1;
-  long long v = 4LL * KP * panel_stride(bmax) + 2 * 8 * KP + 2 * KP + 8 * KS;
+  long long v = 4LL * kp * panel_stride(bmax, kp) + 2 * 8 * kp + 2 * kp + 8 * KS;
   if (!gw) v += (long long)ring_slots(bmax) * row_stride(B1) + (long long)nslot * nmax + 4LL * nmax;
   return (v + 1) & ~1LL;
 }
@@ -178,7 +192,7 @@ __host__ __device__ inline long long scratch_group_doubles(int nmax, int bmax, i
 // Carve the group's shared memory (base) and global scratch (gs).  For the global
 // window, W and B1s are set per entity (set_window).
 __device__ __forceinline__ Smem carve(double* base, double* gs, int nmax, int bmax, int nslot,
-                                      int gw, int recompute) {
+                                      int gw, int recompute, int kp = KP_DEF) {
   Smem s;
   const int B1 = bmax + 1;
   s.gw = gw;
@@ -201,10 +215,10 @@ __device__ __forceinline__ Smem carve(double* base, double* gs, int nmax, int bm
     p = base;
   }
   s.lp = p;
-  s.tp = s.lp + 2LL * KP * panel_stride(bmax);
-  s.zj = s.tp + 2LL * KP * panel_stride(bmax);
-  s.misc = s.zj + 2 * 8 * KP;
-  s.zb = s.misc + 2 * KP;
+  s.tp = s.lp + 2LL * kp * panel_stride(bmax, kp);
+  s.zj = s.tp + 2LL * kp * panel_stride(bmax, kp);
+  s.misc = s.zj + 2 * 8 * kp;
+  s.zb = s.misc + 2 * kp;
   return s;
 }
 
@@ -401,12 +415,12 @@ __device__ void forward_sweep(const Loc& E, const Smem& sm, int nmax, int bmax,
 // Factor one panel (columns j .. j+Kc-1, already updated by all earlier panels) into
 // panel buffer set pb: multipliers, unscaled columns, reciprocal pivots, the stored
 // factor columns and the fused forward substitution of the panel rows.  Threads < PA.
-template <int NT>
+template <int NT, int KP>
 __device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int nmax, int bmax,
                                              double* fac_e, int* status, int j, int pb, int tid) {
   constexpr int PA = (NT < 64) ? NT : 64;
   const int n = E.n, b = E.b, nvs = E.nvs, FB = b + 1;
-  const int RS = sm.RS, B1s = sm.B1s, LPS = panel_stride(bmax);
+  const int RS = sm.RS, B1s = sm.B1s, LPS = panel_stride(bmax, KP);
   const int Kc = min(KP, n - j);
   double* lp = sm.lp + pb * KP * LPS;
   double* tp = sm.tp + pb * KP * LPS;
@@ -477,14 +491,14 @@ __device__ __forceinline__ void factor_panel(const Loc& E, const Smem& sm, int n
 // panel.  The window is a ring of RS = ring_slots(bmax) columns (column c in slot
 // c % RS), each holding rows c..c+b.  On return Z holds the solutions; the factor is
 // stored to fac_e: column j at j*(b+1) holds 1/d_j then l_{j+1..j+b, j} (zeros past n).
-template <int NT>
+template <int NT, int KP>
 __device__ void factor_solve(const Loc& E, const Smem& sm, int nmax, int bmax, double* fac_e,
                              int* status, int tid) {
   constexpr int PA = (NT < 64) ? NT : 64;
   const int n = E.n, b = E.b, nvs = E.nvs;
   const int RS = sm.RS;
   const int B1s = sm.B1s;
-  const int LPS = panel_stride(bmax);
+  const int LPS = panel_stride(bmax, KP);
   double* W = sm.W;
   const int ncol0 = RS < n ? RS : n;  // columns loaded up front (all of them for a global window)
   for (int it = tid; it < ncol0 * (b + 1); it += NT) {
@@ -492,7 +506,7 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, int nmax, int bmax, d
     W[col * B1s + k] = (col < n) ? band_entry(E, sm, nmax, col, k) : 0.0;
   }
   gsync<NT>();
-  if (tid < PA) factor_panel<NT>(E, sm, nmax, bmax, fac_e, status, 0, 0, tid);
+  if (tid < PA) factor_panel<NT, KP>(E, sm, nmax, bmax, fac_e, status, 0, 0, tid);
   gsync<NT>();
   int pb = 0;
   for (int j = 0; j < n; j += KP, pb ^= 1) {
@@ -539,7 +553,7 @@ __device__ void factor_solve(const Loc& E, const Smem& sm, int nmax, int bmax, d
     gsync<NT>();
     // (2) the first 64 threads factor the next panel into the other buffer set
     if ((NT == 32 || tid < PA) && j + KP < n)
-      factor_panel<NT>(E, sm, nmax, bmax, fac_e, status, j + KP, pb ^ 1, tid);
+      factor_panel<NT, KP>(E, sm, nmax, bmax, fac_e, status, j + KP, pb ^ 1, tid);
     if (NT == 32 || tid >= PA) {
       const int t2 = (NT == 32) ? tid : tid - PA;
       constexpr int N2 = (NT == 32) ? 32 : NT - 64;
@@ -608,7 +622,7 @@ template <int NT>
 __device__ void derivative_solve(const Loc& E, const Smem& sm, int nmax, int bmax, double* fac_e,
                                  int tid) {
   if (sm.F) {
-    factor_solve<NT>(E, sm, nmax, bmax, fac_e, nullptr, tid);
+    factor_solve<NT, KP_DEF>(E, sm, nmax, bmax, fac_e, nullptr, tid);
   } else {
     forward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
     backward_sweep<NT>(E, sm, nmax, bmax, fac_e, tid);
@@ -651,7 +665,7 @@ constexpr int min_blocks(int nt, int g) { return nt * g == 128 ? 4 : (nt == 256 
 // MULTI: a fused launch over several instances; every array (and the geometry) is the
 // one of the entity's instance (L.inst[ents[e].inst]), the kernel arguments are unused
 // apart from the dimension.
-template <int NT, int G, bool MULTI = false>
+template <int NT, int G, bool MULTI = false, int KP = KP_DEF>
 __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom g0, LocalLaunch L,
                                                      const double* __restrict__ T0,
                                                      double* __restrict__ Pw0, double* fac0,
@@ -659,10 +673,10 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom 
   extern __shared__ double smem[];
   __shared__ int s_next;
   const int nslot = 1 << g0.d;
-  const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw);
+  const long long gd = group_doubles(L.nmax, L.bmax, nslot, L.gw, KP);
   const int grp = threadIdx.x / NT, tid = threadIdx.x - grp * NT;
   double* gs = L.scratch ? L.scratch + (long long)(blockIdx.x * G + grp) * L.scratch_group : nullptr;
-  Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute);
+  Smem sm = carve(smem + grp * gd, gs, L.nmax, L.bmax, nslot, L.gw, L.recompute, KP);
   for (;;) {
     const int eid = next_entity<NT>(L.counter + 0, &s_next, tid);
     if (eid >= L.n_ents) break;
@@ -699,7 +713,7 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom 
       sm.Z[(long long)i * L.nmax + p] = r;
     }
     gsync<NT>();
-    factor_solve<NT>(E, sm, L.nmax, L.bmax, fac_e, status, tid);
+    factor_solve<NT, KP>(E, sm, L.nmax, L.bmax, fac_e, status, tid);
     // write the basis weights of every slot (zeros for slots the entity lacks)
     for (int it = tid; it < E.n * nslot; it += NT) {
       const int p = it / nslot, s = it - (it / nslot) * nslot;
@@ -952,17 +966,17 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_tan(DevGeom 
 // -----------------------------------------------------------------------------
 namespace {
 template <int NT, int G>
-size_t smem_bytes(const DevGeom& g, const LocalLaunch& L) {
+size_t smem_bytes(const DevGeom& g, const LocalLaunch& L, int kp = KP_DEF) {
   const int nslot = 1 << g.d;
-  return (size_t)G * group_doubles(L.nmax, L.bmax, nslot, L.gw) * sizeof(double);
+  return (size_t)G * group_doubles(L.nmax, L.bmax, nslot, L.gw, kp) * sizeof(double);
 }
 
 constexpr size_t kSmemLimit = 227 * 1024;
 
 // CTAs of one full wave of kernel kern (at least 1, at most what the entities need)
 template <int NT, int G, typename K>
-int wave_ctas(K kern, const DevGeom& g, const LocalLaunch& L) {
-  const size_t sh = smem_bytes<NT, G>(g, L);
+int wave_ctas(K kern, const DevGeom& g, const LocalLaunch& L, int kp = KP_DEF) {
+  const size_t sh = smem_bytes<NT, G>(g, L, kp);
   if (sh > kSmemLimit) return 0;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   int per_sm = 0, dev = 0, sms = 0;
@@ -983,10 +997,10 @@ int wave_ctas(K kern, const DevGeom& g, const LocalLaunch& L) {
   return (int)(need < wave ? (need > 0 ? need : 1) : wave);
 }
 
-template <int NT, int G, typename K, typename... Args>
+template <int NT, int G, int KPv = KP_DEF, typename K, typename... Args>
 void launch_k(K kern, int which, const DevGeom& g, const LocalLaunch& L, cudaStream_t s,
               Args... args) {
-  const size_t sh = smem_bytes<NT, G>(g, L);
+  const size_t sh = smem_bytes<NT, G>(g, L, KPv);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
   cudaMemsetAsync(L.counter + which, 0, sizeof(int), s);
   kern<<<L.grid[which], NT * G, sh, s>>>(g, L, args...);
@@ -1018,9 +1032,10 @@ bool local_plan(const DevGeom& g, LocalLaunch& L, int force_gw, int variant) {
   if (local_smem_bytes(g, L) > kSmemLimit) return false;
   const int nslot = 1 << g.d;
   L.scratch_group = scratch_group_doubles(L.nmax, L.bmax, nslot, L.gw, L.recompute);
-#define MSFV_GRIDS(NT, G)                                      \
-  L.grid[0] = wave_ctas<NT, G>(k_local_fwd<NT, G>, g, L);      \
-  L.grid[1] = wave_ctas<NT, G>(k_local_adj<NT, G>, g, L);      \
+#define MSFV_GRIDS(NT, G)                                                                   \
+  L.grid[0] = L.gw ? wave_ctas<NT, G>(k_local_fwd<NT, G, false, KP_GW>, g, L, KP_GW)          \
+                   : wave_ctas<NT, G>(k_local_fwd<NT, G>, g, L);                             \
+  L.grid[1] = wave_ctas<NT, G>(k_local_adj<NT, G>, g, L);                                   \
   L.grid[2] = wave_ctas<NT, G>(k_local_tan<NT, G>, g, L)
   MSFV_VARIANT_SWITCH(L.variant, MSFV_GRIDS)
 #undef MSFV_GRIDS
@@ -1038,7 +1053,11 @@ long long local_scratch_doubles(const LocalLaunch& L) {
 void launch_local_forward(const DevGeom& g, const LocalLaunch& L, const double* T, double* Pw,
                           double* fac, int* status, cudaStream_t s) {
   if (L.n_ents == 0) return;
-#define MSFV_FWD(NT, G) launch_k<NT, G>(k_local_fwd<NT, G>, 0, g, L, s, T, Pw, fac, status)
+#define MSFV_FWD(NT, G)                                                                   \
+  if (L.gw)                                                                               \
+    launch_k<NT, G, KP_GW>(k_local_fwd<NT, G, false, KP_GW>, 0, g, L, s, T, Pw, fac, status); \
+  else                                                                                    \
+    launch_k<NT, G>(k_local_fwd<NT, G>, 0, g, L, s, T, Pw, fac, status)
   MSFV_VARIANT_SWITCH(L.variant, MSFV_FWD)
 #undef MSFV_FWD
 }
@@ -1059,9 +1078,10 @@ bool local_plan_fused(const DevGeom& g, LocalLaunch& L) {
   if (local_smem_bytes(g, L) > kSmemLimit) return false;
   const int nslot = 1 << g.d;
   L.scratch_group = scratch_group_doubles(L.nmax, L.bmax, nslot, L.gw, L.recompute);
-#define MSFV_GRIDS(NT, G)                                             \
-  L.grid[0] = wave_ctas<NT, G>(k_local_fwd<NT, G, true>, g, L);       \
-  L.grid[1] = wave_ctas<NT, G>(k_local_adj<NT, G, true>, g, L);       \
+#define MSFV_GRIDS(NT, G)                                                                   \
+  L.grid[0] = L.gw ? wave_ctas<NT, G>(k_local_fwd<NT, G, true, KP_GW>, g, L, KP_GW)           \
+                   : wave_ctas<NT, G>(k_local_fwd<NT, G, true>, g, L);                        \
+  L.grid[1] = wave_ctas<NT, G>(k_local_adj<NT, G, true>, g, L);                              \
   L.grid[2] = 1
   MSFV_VARIANT_SWITCH(L.variant, MSFV_GRIDS)
 #undef MSFV_GRIDS
@@ -1072,8 +1092,12 @@ void launch_local_forward_fused(const DevGeom& g, const LocalLaunch& L, cudaStre
   if (L.n_ents == 0) return;
   double* np = nullptr;
   int* ni = nullptr;
-#define MSFV_FWD(NT, G) \
-  launch_k<NT, G>(k_local_fwd<NT, G, true>, 0, g, L, s, (const double*)np, np, np, ni)
+#define MSFV_FWD(NT, G)                                                                    \
+  if (L.gw)                                                                                \
+    launch_k<NT, G, KP_GW>(k_local_fwd<NT, G, true, KP_GW>, 0, g, L, s, (const double*)np, np, \
+                           np, ni);                                                        \
+  else                                                                                     \
+    launch_k<NT, G>(k_local_fwd<NT, G, true>, 0, g, L, s, (const double*)np, np, np, ni)
   MSFV_VARIANT_SWITCH(L.variant, MSFV_FWD)
 #undef MSFV_FWD
 }
