@@ -72,6 +72,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=128, help="plain: mesh size per axis (default 128)")
+    p.add_argument("--coarsen", type=int, default=8, help="plain: coarsening factor (default 8)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="batched",
@@ -417,7 +418,8 @@ def plain_measure(args, dev, sess, prob, m, d_obs, world=1):
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_SOURCE,
             "flops_per_launch": flops, "avg_launch_ms": int_avg_s * 1000.0,
-            "traffic": INTERIOR_DRAM_BYTES_128 if (args.n == 128 and args.precision == "fp64")
+            "traffic": INTERIOR_DRAM_BYTES_128
+            if (args.n == 128 and getattr(args, "coarsen", 8) == 8 and args.precision == "fp64")
             else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
                               "this kernel on the 128^3 workload"}
@@ -464,10 +466,11 @@ def open_plain(args, dev, seed_model=2, seed_truth=3, seed_noise=4):
     independent model plus 1% noise, outside any timing)."""
     import torch
     from paper_1707_07598_gb300.msfv import Session
-    prob, m_np = W.config_3d_128(seed=seed_model, n=args.n)
+    c = getattr(args, "coarsen", 8)
+    prob, m_np = W.config_3d_128(seed=seed_model, n=args.n, coarsen=c)
     sess = Session(prob, stream=torch.cuda.current_stream(dev))
     m = torch.from_numpy(m_np).to(dev)
-    m_true = torch.from_numpy(W.config_3d_128(seed=seed_truth, n=args.n)[1]).to(dev)
+    m_true = torch.from_numpy(W.config_3d_128(seed=seed_truth, n=args.n, coarsen=c)[1]).to(dev)
     d_true = sess.forward(m_true).clone()
     noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, seed_noise)).to(dev)
     d_obs = d_true + 0.01 * d_true.abs() * noise
@@ -499,8 +502,9 @@ def run_plain(args):
                "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"],
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f64", "data": "synthetic",
-               "config": {"workload": WORKLOAD if args.n == 128 else f"3d_{args.n}^3_c8",
-                          "n": [args.n] * 3, "coarsen": 8, "n_src": prob.n_src,
+               "config": {"workload": WORKLOAD if (args.n == 128 and args.coarsen == 8)
+                          else f"3d_{args.n}^3_c{args.coarsen}",
+                          "n": [args.n] * 3, "coarsen": args.coarsen, "n_src": prob.n_src,
                           "n_rec": prob.n_rec, "parallelism": f"replicas x{world}",
                           "l2": "flushed before every timed step (512 MiB write)",
                           "factor_mode": "store", "precision": args.precision,

@@ -19,13 +19,14 @@
 //    complements its two children left in their fronts, gathered (each front entry reads
 //    at most one value per child, in a fixed order: deterministic, no atomics);
 //  * partial LU of the pivot block by a thread-block cluster per front (blocked right-
-//    looking, panels of 16 columns: the panel, the U block row, then the rank-16 update of
-//    the trailing block with both blocks staged in shared memory; hardware cluster
-//    barriers between the phases), leaving the Schur complement for the parent.
+//    looking, panels of 16 columns: every CTA factors the diagonal block, then its share
+//    of the L rows and U columns, then the rank-16 update of its trailing rows with the U
+//    block row staged in shared memory; hardware cluster barriers between the phases),
+//    leaving the Schur complement for the parent.
 // Solves go up the tree (forward substitution, per front a unit lower or, transposed, a
 // non-unit lower triangle; the children's contributions to ancestor nodes are carried in
 // per-front update vectors) and back down (backward substitution), one level per launch,
-// one warp per right-hand side.  Everything is FP64.
+// one CTA per (front, right-hand side).  Everything is FP64.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,7 +43,7 @@ namespace msfv {
 
 namespace {
 
-constexpr int kNdThreads = 512;     // threads per CTA of the factor and solve kernels
+constexpr int kNdThreads = 512;     // threads per CTA of the assembly and factor kernels
 constexpr int kNdPanel = 16;        // panel width of the blocked factorisation
 constexpr int kNdLeaf = 8;          // boxes of at most this many nodes are leaves
 

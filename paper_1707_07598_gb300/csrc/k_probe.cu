@@ -17,11 +17,14 @@ constexpr int kProbeChains = 8;
 __global__ void __launch_bounds__(kProbeThreads) k_dfma_probe(int iters, double a, double b,
                                                               double* __restrict__ sink) {
   double x[kProbeChains];
+  // the multiplier and addend in registers (a per-thread perturbation keeps the compiler
+  // from folding them into constant-bank operands, which slows the FMA issue)
+  const double ar = a + 1e-20 * threadIdx.x, br = b - 1e-22 * threadIdx.x;
 #pragma unroll
   for (int q = 0; q < kProbeChains; ++q) x[q] = (double)(threadIdx.x + q) * 1e-3;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
-    for (int q = 0; q < kProbeChains; ++q) x[q] = fma(x[q], a, b);
+    for (int q = 0; q < kProbeChains; ++q) x[q] = fma(x[q], ar, br);
   }
   double s = 0.0;
 #pragma unroll

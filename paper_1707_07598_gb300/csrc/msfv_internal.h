@@ -407,7 +407,7 @@ struct NDHost {
 };
 // coarse meshes up to this many nodes use the nested-dissection LU by default (3D; the
 // factor grows as Nc^2 there, as Nc^1.5 in 2D)
-constexpr long long kNdMaxNodes3 = 8192;
+constexpr long long kNdMaxNodes3 = 16384;
 constexpr long long kNdMaxNodes2 = 65536;
 bool nd_setup(NDHost& H, const DevGeom& g, int Ns);
 // largest cluster (CTAs) the factor kernel runs with on this device: 16 or 8

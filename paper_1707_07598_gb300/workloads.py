@@ -168,12 +168,12 @@ def config_2d_64(seed: int = 1):
     return prob, m
 
 
-def config_3d_128(seed: int = 2, n: int = 128):
-    """3D, n^3 cells (128 by default), c=8, GRF l=0.15 plus two +/-2 boxes,
+def config_3d_128(seed: int = 2, n: int = 128, coarsen: int = 8):
+    """3D, n^3 cells (128 by default), c=8 (by default), GRF l=0.15 plus two +/-2 boxes,
     16 dipoles and 512 receivers on the top layer."""
     nn = (n, n, n)
-    prob = make_problem(nn, 8, 16, 512 if n >= 32 else min(512, n * n // 2), seed,
-                        top_layer=True, name=f"3d_{n}^3_c8_s16_r512")
+    prob = make_problem(nn, coarsen, 16, 512 if n >= 32 else min(512, n * n // 2), seed,
+                        top_layer=True, name=f"3d_{n}^3_c{coarsen}_s16_r512")
     m = gaussian_random_field(nn, 0.15, seed)
     m = add_box(m, nn, (0.3, 0.5, 0.6), 0.2, +2.0)
     m = add_box(m, nn, (0.7, 0.5, 0.6), 0.2, -2.0)
