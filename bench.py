@@ -58,11 +58,11 @@ COARSE_SOLVERS = {0: "banded-lu", 1: "mg-gmres", 2: "nested-dissection-lu"}
 # to None whenever the kernel changes, until it is captured again.
 INTERIOR_DRAM_BYTES_128 = 117296896.0 + 549022464.0
 # DRAM bytes per algorithmic FP64 flop of the c = 16 interior kernel (global-memory window,
-# panels of 8), from an ncu capture of one launch on a 192^3, c = 16 instance (2197
-# interiors: 80.10 GB read + 119.03 GB written for 2.684e11 flops).  The kernel's traffic is
+# panels of 8), from an ncu capture of one launch on the 192^3, c = 16 plain workload (2197
+# interiors: 80.06 GB read + 118.99 GB written for 2.684e11 flops).  The kernel's traffic is
 # its windows' passes through L2 and HBM, which grow with its flops, so a fused launch over
 # c = 16 interiors is scaled by its flop count.  Set to None whenever the kernel changes.
-C16_DRAM_BYTES_PER_FLOP = (80102701312.0 + 119030783744.0) / 268362314256.0
+C16_DRAM_BYTES_PER_FLOP = (80062537216.0 + 118986263296.0) / 268362314256.0
 
 
 def parse():
@@ -783,7 +783,7 @@ def run_batched(args):
         pres = plain_measure(args, dev, psess, pprob, pm, pdobs, 1)
         psess.close()
         plain128 = dict(pres, workload=WORKLOAD,
-                        note="configuration 2 of the task: one instance, 128^3, c = 8, 16 "
+                        note="the plain one-instance configuration: 128^3, c = 8, 16 "
                              "dipoles, 512 receivers; L2 flushed before each step; first "
                              "order in h at even c (coarse vertex half a cell off the "
                              "coarse-cell centre)")

@@ -442,13 +442,14 @@ __global__ void __launch_bounds__(kNdSolveThreads) k_nd_forward(
       if (qq < qb) v = tr ? M[(long long)(q0 + qq) * F + r] : M[(long long)r * F + q0 + qq];
       Cb[(r - q0) * kNdCS + qq] = v;
     }
-    if (tr && tid < qb) dg[tid] = M[(long long)(q0 + tid) * F + q0 + tid];
+    // reciprocals of the block's pivots (transposed: U's diagonal), taken in parallel
+    if (tr && tid < qb) dg[tid] = 1.0 / M[(long long)(q0 + tid) * F + q0 + tid];
     __syncthreads();
     // the block's triangle: one warp, a lane per row of the block
     if (tid < 32) {
       for (int qq = 0; qq < qb; ++qq) {
         double y = t[q0 + qq];
-        if (tr) y = y / dg[qq];
+        if (tr) y = y * dg[qq];
         __syncwarp();
         if (lane == qq) t[q0 + qq] = y;
         if (lane > qq && lane < qb) t[q0 + lane] = fma(-Cb[lane * kNdCS + qq], y, t[q0 + lane]);
@@ -537,12 +538,12 @@ __global__ void __launch_bounds__(kNdSolveThreads) k_nd_backward(
       if (qq < qb) v = tr ? M[(long long)(q0 + qq) * F + r] : M[(long long)r * F + q0 + qq];
       Cb[r * kNdCS + qq] = v;
     }
-    if (!tr && tid < qb) dg[tid] = M[(long long)(q0 + tid) * F + q0 + tid];
+    if (!tr && tid < qb) dg[tid] = 1.0 / M[(long long)(q0 + tid) * F + q0 + tid];
     __syncthreads();
     if (tid < 32) {
       for (int qq = qb - 1; qq >= 0; --qq) {
         double x = t[q0 + qq];
-        if (!tr) x = x / dg[qq];
+        if (!tr) x = x * dg[qq];
         __syncwarp();
         if (lane == qq) t[q0 + qq] = x;
         if (lane < qq) t[q0 + lane] = fma(-Cb[(q0 + lane) * kNdCS + qq], x, t[q0 + lane]);

@@ -1612,7 +1612,7 @@ extern "C" int64_t msfv_launch_count(const msfv_session_t* s) { return s ? s->la
 // A group of batch instances whose top-dimensional local problems (the dual-cell
 // interiors) run in one fused persistent launch: the same kernel shape, window kind and
 // factor mode, so one kernel takes every instance's entities from one list sorted by
-// cost (uneven dual-cell sizes and instances in one persistent kernel).
+// cost: uneven dual-cell sizes of several instances in one persistent kernel.
 struct FusedGroup {
   LocalLaunch L{};
   DevGeom g{};                        // dimension and geometry of the first member
