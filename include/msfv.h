@@ -382,6 +382,16 @@ const char* msfv_phase_name(int k);
  * those of the axis order the kernel uses (shortest tangential axis fastest). */
 double msfv_interior_flops(const msfv_session_t* s);
 
+/* Symbolic analysis of the nested-dissection coarse LU for a coarse grid of nc[0] x nc[1]
+ * (x nc[2]) nodes with the 3^dim-point stencil, on the host only (no CUDA call): the plan
+ * msfv_setup builds for that coarse grid.  out (host, up to 7 int64): [0] fronts, [1] tree
+ * levels, [2] doubles of front storage, [3] update rows of the solves, [4] largest front,
+ * [5] factor flops (sum over the fronts of 2/3 (F^3 - (F - p)^3)), [6] 1 when the plan
+ * passes its structural checks (every node a pivot of exactly one front, every child's
+ * update nodes in its parent's index list).  MSFV_ERR_ARG for other dims, non-positive
+ * sizes or coarse grids beyond 2^26 nodes. */
+int msfv_nd_analyse(int dim, const int* nc, int64_t* out, int n_out);
+
 /* Number of kernel launches this session has enqueued since setup. */
 int64_t msfv_launch_count(const msfv_session_t* s);
 

@@ -654,6 +654,38 @@ cudaError_t launch_nd_solve(const NDHost& H, double* rhs, int Ns, int transpose,
   return cudaGetLastError();
 }
 
+// Structural checks of a symbolic analysis (host only): every node is the pivot of exactly
+// one front, pivots come first in each index list, and every node of a child's update set
+// appears in its parent's list at the position the child map gives.
+bool nd_check(const NDHost& H) {
+  std::vector<int> seen((size_t)H.Nc, 0);
+  for (const NDFrontDev& f : H.h_fronts) {
+    if (f.p < 1 || f.F < f.p) return false;
+    for (int r = 0; r < f.p; ++r) {
+      const int v = H.h_idx[f.idx + r];
+      if (v < 0 || v >= H.Nc) return false;
+      seen[v]++;
+    }
+  }
+  for (int v : seen)
+    if (v != 1) return false;
+  for (const NDFrontDev& f : H.h_fronts)
+    for (int k = 0; k < 2; ++k) {
+      if (f.ch[k] < 0) continue;
+      const NDFrontDev& C = H.h_fronts[f.ch[k]];
+      std::vector<int> hit((size_t)C.F, 0);
+      for (int r = 0; r < f.F; ++r) {
+        const int a = H.h_cmap[f.cmap[k] + r];
+        if (a < 0) continue;
+        if (a < C.p || a >= C.F || H.h_idx[C.idx + a] != H.h_idx[f.idx + r]) return false;
+        hit[a]++;
+      }
+      for (int a = C.p; a < C.F; ++a)
+        if (hit[a] != 1) return false;
+    }
+  return true;
+}
+
 long long nd_device_bytes(const NDHost& H) {
   return (long long)sizeof(NDFrontDev) * (long long)H.h_fronts.size() +
          (long long)sizeof(int) * (long long)(H.h_idx.size() + H.h_cmap.size()) +
@@ -661,3 +693,24 @@ long long nd_device_bytes(const NDHost& H) {
 }
 
 }  // namespace msfv
+
+extern "C" int msfv_nd_analyse(int dim, const int* nc, int64_t* out, int n_out) {
+  if ((dim != 2 && dim != 3) || !nc || !out) return MSFV_ERR_ARG;
+  msfv::DevGeom g{};
+  g.d = dim;
+  for (int a = 0; a < 3; ++a) g.nc[a] = (a < dim) ? nc[a] : 1;
+  for (int a = 0; a < dim; ++a)
+    if (nc[a] < 1) return MSFV_ERR_ARG;
+  msfv::NDHost H;
+  if (!msfv::nd_setup(H, g, 1)) return MSFV_ERR_ARG;
+  double flops = 0.0;
+  for (const msfv::NDFrontDev& f : H.h_fronts) {
+    const double F = f.F, rest = (double)(f.F - f.p);
+    flops += 2.0 / 3.0 * (F * F * F - rest * rest * rest);
+  }
+  const int64_t v[7] = {(int64_t)H.h_fronts.size(), (int64_t)H.nlev, (int64_t)H.pool,
+                        (int64_t)H.wpool, (int64_t)H.maxF, (int64_t)flops,
+                        msfv::nd_check(H) ? 1 : 0};
+  for (int i = 0; i < n_out && i < 7; ++i) out[i] = v[i];
+  return MSFV_OK;
+}

@@ -98,6 +98,8 @@ def load(path: Optional[str] = None):
     L.msfv_batch_run_host.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                       ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.msfv_batch_run_host.restype = ctypes.c_int
+    L.msfv_nd_analyse.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p, ctypes.c_int]
+    L.msfv_nd_analyse.restype = ctypes.c_int
     L.msfv_batch_run_timed.argtypes = [vp, dp, dp, i64p, ctypes.c_int]
     L.msfv_batch_run_timed.restype = ctypes.c_int
     L.msfv_batch_info.argtypes = [vp, i64p, ctypes.c_int]
@@ -353,6 +355,20 @@ def misfit_static(d_pred, d_obs, r=None, phi=None, stream=None):
     if rc != MSFV_OK:
         raise MSFVError(rc, L.msfv_last_error(None).decode())
     return phi
+
+
+def nd_analyse(nc) -> dict:
+    """Host-side plan of the nested-dissection coarse LU for a coarse grid of nc nodes per
+    axis (msfv_nd_analyse; no GPU needed)."""
+    L = load()
+    nc = [int(v) for v in nc]
+    arr = (ctypes.c_int * 3)(*(nc + [1] * (3 - len(nc))))
+    out = (ctypes.c_int64 * 7)()
+    rc = L.msfv_nd_analyse(len(nc), arr, out, 7)
+    if rc != MSFV_OK:
+        raise MSFVError(rc, "msfv_nd_analyse failed")
+    keys = ["fronts", "levels", "pool_doubles", "update_rows", "max_front", "factor_flops", "ok"]
+    return dict(zip(keys, list(out)))
 
 
 def fp64_probe(stream=None):
