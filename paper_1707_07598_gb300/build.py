@@ -33,8 +33,19 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def checked() -> bool:
+    """MSFV_CHECKED=1 selects the checked build: the local and nested-dissection kernels
+    validate every work descriptor before they touch its storage (-DMSFV_CHECKED), in a
+    library of its own (lib/checked/)."""
+    return os.environ.get("MSFV_CHECKED", "0") not in ("", "0")
+
+
+def _libdir() -> str:
+    return os.path.join(LIBDIR, "checked") if checked() else LIBDIR
+
+
 def lib_path() -> str:
-    return os.path.join(LIBDIR, LIBNAME)
+    return os.path.join(_libdir(), LIBNAME)
 
 
 def _up_to_date(target, deps) -> bool:
@@ -46,7 +57,9 @@ def _up_to_date(target, deps) -> bool:
 
 def build(verbose: bool = False, force: bool = False) -> str:
     """Compile (if needed) and return the path of libmsfv.so."""
-    os.makedirs(os.path.join(LIBDIR, "obj"), exist_ok=True)
+    libdir = _libdir()
+    extra = ["-DMSFV_CHECKED"] if checked() else []
+    os.makedirs(os.path.join(libdir, "obj"), exist_ok=True)
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "msfv.h"))
@@ -56,8 +69,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(LIBDIR, "obj", os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(libdir, "obj", os.path.basename(src) + ".o")
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

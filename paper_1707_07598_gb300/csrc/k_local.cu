@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdio>
 #include <cstdlib>
 
 #include "msfv_internal.h"
@@ -629,6 +630,51 @@ __device__ void derivative_solve(const Loc& E, const Smem& sm, int nmax, int bma
   }
 }
 
+#ifdef MSFV_CHECKED
+// Checked builds (-DMSFV_CHECKED): every local kernel validates an entity's work
+// descriptor before it touches global memory for it -- its box inside the mesh, its size
+// and half bandwidth against the launch's buffers, its corner slots, its factor and
+// receiver ranges inside their arrays, the thread group's scratch inside the scratch
+// buffer -- and skips an entity that fails, naming it with a device printf.
+__device__ bool entity_ok(const char* who, int eid, int inst, const EntDesc& e, const DevGeom& g,
+                          const LocalLaunch& L, const double* fac, long long fac_n,
+                          long long rec_n, long long gs_end, int tid) {
+  int bad = 0;
+  const int nslot = 1 << g.d;
+  long long prod = 1;
+  if (e.dim < 1 || e.dim > g.d) bad = 1;
+  for (int k = 0; k < 3 && !bad; ++k) {
+    if (k >= e.dim) continue;
+    const int a = e.perm[k];
+    if (a < 0 || a >= g.d) bad = 2;
+    else prod *= e.len[a];
+  }
+  for (int a = 0; a < g.d && !bad; ++a)
+    if (e.org[a] < 0 || e.len[a] < 1 || e.org[a] + e.len[a] > g.n[a]) bad = 3;
+  if (!bad && (e.n < 1 || e.n != prod || e.n > L.nmax)) bad = 4;
+  if (!bad && (e.b < 0 || e.b > L.bmax)) bad = 5;
+  if (!bad && (e.slots <= 0 || e.slots >= (1 << nslot))) bad = 6;
+  if (!bad && !L.recompute &&
+      (!fac || e.fac < 0 || e.fac + (long long)e.n * (e.b + 1) > fac_n))
+    bad = 7;
+  if (!bad && (e.rec_off < 0 || e.rec_cnt < 0 || (long long)e.rec_off + e.rec_cnt > rec_n)) bad = 8;
+  if (!bad && (L.gw || L.recompute) && (!L.scratch || gs_end > L.scratch_n)) bad = 9;
+  if (bad && tid == 0)
+    printf("msfv checked: %s entity %d (instance %d) failed check %d: dim %d n %d b %d slots %d "
+           "org %d %d %d len %d %d %d fac %lld of %lld rec %d+%d of %lld nmax %d bmax %d\n",
+           who, eid, inst, bad, e.dim, e.n, e.b, e.slots, e.org[0], e.org[1], e.org[2], e.len[0],
+           e.len[1], e.len[2], e.fac, fac_n, e.rec_off, e.rec_cnt, rec_n, L.nmax, L.bmax);
+  return !bad;
+}
+
+__device__ bool inst_ok(const char* who, int eid, int inst, const LocalLaunch& L, int tid) {
+  const bool ok = inst >= 0 && inst < L.n_inst && L.inst != nullptr;
+  if (!ok && tid == 0)
+    printf("msfv checked: %s entity %d names instance %d of %d\n", who, eid, inst, L.n_inst);
+  return ok;
+}
+#endif
+
 // Next entity of a thread group from the launch's work counter (dynamic schedule).
 template <int NT>
 __device__ __forceinline__ int next_entity(int* counter, int* s_next, int tid) {
@@ -682,12 +728,21 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_fwd(DevGeom 
     if (eid >= L.n_ents) break;
     Loc E;
     load_loc(L.ents[eid], E);
+#ifdef MSFV_CHECKED
+    if (MULTI && !inst_ok("forward", eid, L.ents[eid].inst, L, tid)) continue;
+#endif
     const InstPtrs* ip = MULTI ? L.inst + L.ents[eid].inst : nullptr;
     const DevGeom& g = MULTI ? ip->g : g0;
     const double* __restrict__ T = MULTI ? ip->T : T0;
     double* __restrict__ Pw = MULTI ? ip->Pw : Pw0;
     double* fac = MULTI ? ip->fac : fac0;
     int* status = MULTI ? ip->status : status0;
+#ifdef MSFV_CHECKED
+    if (!entity_ok("forward", eid, MULTI ? L.ents[eid].inst : -1, L.ents[eid], g, L, fac,
+                   MULTI ? ip->fac_n : L.fac_n, MULTI ? ip->rec_n : L.rec_n,
+                   (long long)(blockIdx.x * G + grp + 1) * L.scratch_group, tid))
+      continue;
+#endif
     double* fac_e = set_window(sm, E, fac);
     build_coef<NT>(g, E, T, sm, L.nmax, tid);
     // right-hand sides: T * phi_v at Dirichlet neighbours across the box boundary
@@ -755,6 +810,9 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_adj(DevGeom 
     Loc E;
     load_loc(L.ents[eid], E);
     if (E.nvs < 2) continue;  // constant basis on this entity: no derivative
+#ifdef MSFV_CHECKED
+    if (MULTI && !inst_ok("adjoint", eid, L.ents[eid].inst, L, tid)) continue;
+#endif
     const InstPtrs* ip = MULTI ? L.inst + L.ents[eid].inst : nullptr;
     const DevGeom& g = MULTI ? ip->g : g0;
     const double* __restrict__ T = MULTI ? ip->T : T0;
@@ -766,6 +824,12 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_adj(DevGeom 
     const double* __restrict__ ZT = MULTI ? ip->ZT : ZT0;
     double* __restrict__ MU = MULTI ? ip->MU : MU0;
     double* __restrict__ gTloc = MULTI ? ip->gTloc : gTloc0;
+#ifdef MSFV_CHECKED
+    if (!entity_ok("adjoint", eid, MULTI ? L.ents[eid].inst : -1, L.ents[eid], g, L, fac,
+                   MULTI ? ip->fac_n : L.fac_n, MULTI ? ip->rec_n : L.rec_n,
+                   (long long)(blockIdx.x * G + grp + 1) * L.scratch_group, tid))
+      continue;
+#endif
     double* fac_e = set_window(sm, E, fac);
     if (L.recompute) {
       build_coef<NT>(g, E, T, sm, L.nmax, tid);
@@ -897,6 +961,11 @@ __global__ void __launch_bounds__(NT* G, min_blocks(NT, G)) k_local_tan(DevGeom 
     if (eid >= L.n_ents) break;
     Loc E;
     load_loc(L.ents[eid], E);
+#ifdef MSFV_CHECKED
+    if (!entity_ok("tangent", eid, -1, L.ents[eid], g, L, fac, L.fac_n, L.rec_n,
+                   (long long)(blockIdx.x * G + grp + 1) * L.scratch_group, tid))
+      continue;
+#endif
     if (E.nvs < 2) {
       for (int it = tid; it < E.n * nslot; it += NT) {
         const int p = it / nslot, s = it - (it / nslot) * nslot;

@@ -32,6 +32,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <vector>
 
@@ -211,6 +212,41 @@ namespace {
 
 __device__ __forceinline__ double ldg_cg(const double* p) { return __ldcg(p); }
 
+// Array sizes of a plan, passed to every kernel; checked builds (-DMSFV_CHECKED) verify a
+// front's ranges against them before touching its storage and skip (with a device printf)
+// a front that fails.
+struct NDSizes {
+  long long pool_n;   // doubles of the front pool
+  long long w_n;      // doubles of the update-vector pool
+  int idx_n;          // entries of the index pool
+  int cmap_n;         // entries of the child maps
+  int nf;             // fronts
+  int pad_;
+};
+
+#ifdef MSFV_CHECKED
+__device__ bool front_ok(const char* who, int fid, const NDFrontDev& f, const NDFrontDev* fronts,
+                         const int* idx, const NDSizes& z, long long Nc, int maxF, int Ns) {
+  int bad = 0;
+  if (fid < 0 || fid >= z.nf) bad = 1;
+  if (!bad && (f.p < 1 || f.F < f.p || f.F > maxF)) bad = 2;
+  if (!bad && (f.off < 0 || f.off + (long long)f.F * f.F > z.pool_n)) bad = 3;
+  if (!bad && (f.woff < 0 || (f.woff + f.F - f.p) * Ns > z.w_n)) bad = 4;
+  if (!bad && (f.idx < 0 || (long long)f.idx + f.F > z.idx_n)) bad = 5;
+  for (int k = 0; k < 2 && !bad; ++k) {
+    if (f.ch[k] < -1 || f.ch[k] >= z.nf) bad = 6;
+    else if (f.ch[k] >= 0 && (f.cmap[k] < 0 || (long long)f.cmap[k] + f.F > z.cmap_n)) bad = 7;
+  }
+  for (int r = 0; r < f.F && !bad; ++r)
+    if (idx[f.idx + r] < 0 || idx[f.idx + r] >= Nc) bad = 8;
+  if (bad && threadIdx.x == 0)
+    printf("msfv checked: %s front %d failed check %d: p %d F %d off %lld woff %lld idx %d "
+           "ch %d %d maxF %d\n", who, fid, bad, f.p, f.F, f.off, f.woff, f.idx, f.ch[0], f.ch[1],
+           maxF);
+  return !bad;
+}
+#endif
+
 // Front entries of one tree level: the original entries of A_c (pinned: row and column 0
 // of the identity) in the pivot rows and columns, plus each child's Schur complement.
 // grid: (CTAs per front, fronts of the level).
@@ -219,8 +255,12 @@ __global__ void __launch_bounds__(kNdThreads) k_nd_assemble(const NDFrontDev* __
                                                             const int* __restrict__ cmap,
                                                             double* pool,
                                                             const double* __restrict__ Ac,
-                                                            long long Nc, int g0, int g1, int d) {
+                                                            long long Nc, int g0, int g1, int d,
+                                                            NDSizes zs, int maxF) {
   const NDFrontDev f = fronts[f0 + blockIdx.y];
+#ifdef MSFV_CHECKED
+  if (!front_ok("assemble", f0 + blockIdx.y, f, fronts, idx, zs, Nc, maxF, 1)) return;
+#endif
   const int F = f.F, p = f.p;
   const int* I = idx + f.idx;
   double* M = pool + f.off;
@@ -274,7 +314,8 @@ __global__ void __launch_bounds__(kNdThreads) k_nd_assemble(const NDFrontDev* __
 // Values another CTA wrote are read from L2 (ld.global.cg).
 __global__ void __launch_bounds__(kNdThreads, 1) k_nd_factor(const NDFrontDev* __restrict__ fronts,
                                                              int f0, int Q, double* pool,
-                                                             int* status) {
+                                                             int* status, NDSizes zs, int maxF,
+                                                             const int* idx, long long Nc) {
   extern __shared__ double sm[];
   __shared__ double D[kNdPanel * kNdPanel];
   __shared__ double lq[kNdPanel];
@@ -282,6 +323,10 @@ __global__ void __launch_bounds__(kNdThreads, 1) k_nd_factor(const NDFrontDev* _
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (Q > 1) ? (int)cl.block_rank() : 0;
   const NDFrontDev f = fronts[f0 + blockIdx.x / Q];
+#ifdef MSFV_CHECKED
+  // uniform over the cluster (every CTA reads the same front), so a skip skips all of it
+  if (!front_ok("factor", f0 + blockIdx.x / Q, f, fronts, idx, zs, Nc, maxF, 1)) return;
+#endif
   const int F = f.F, p = f.p;
   double* M = pool + f.off;
   const int tid = threadIdx.x;
@@ -398,9 +443,12 @@ constexpr int kNdCS = kNdPanel + 1;   // padded row stride of a staged coefficie
 __global__ void __launch_bounds__(kNdSolveThreads) k_nd_forward(
     const NDFrontDev* __restrict__ fronts, int f0, const int* __restrict__ idx,
     const int* __restrict__ cmap, const double* __restrict__ pool, double* W, double* rhs, int Ns,
-    long long Nc, int maxF, int tr) {
+    long long Nc, int maxF, int tr, NDSizes zs) {
   extern __shared__ double tsm[];
   const NDFrontDev f = fronts[f0 + blockIdx.x];
+#ifdef MSFV_CHECKED
+  if (!front_ok("forward solve", f0 + blockIdx.x, f, fronts, idx, zs, Nc, maxF, Ns)) return;
+#endif
   const int j = blockIdx.y;
   const int F = f.F, p = f.p;
   const int* I = idx + f.idx;
@@ -481,9 +529,13 @@ __global__ void __launch_bounds__(kNdSolveThreads) k_nd_forward(
 // triangle of U (transposed: the unit upper triangle L^T), in blocks from the last pivot.
 __global__ void __launch_bounds__(kNdSolveThreads) k_nd_backward(
     const NDFrontDev* __restrict__ fronts, int f0, const int* __restrict__ idx,
-    const double* __restrict__ pool, double* rhs, int Ns, long long Nc, int maxF, int tr) {
+    const double* __restrict__ pool, double* rhs, int Ns, long long Nc, int maxF, int tr,
+    NDSizes zs) {
   extern __shared__ double tsm[];
   const NDFrontDev f = fronts[f0 + blockIdx.x];
+#ifdef MSFV_CHECKED
+  if (!front_ok("backward solve", f0 + blockIdx.x, f, fronts, idx, zs, Nc, maxF, Ns)) return;
+#endif
   const int j = blockIdx.y;
   const int F = f.F, p = f.p;
   const int* I = idx + f.idx;
@@ -602,13 +654,24 @@ int nd_max_team() {
   return 16;
 }
 
+NDSizes nd_sizes(const NDHost& H) {
+  NDSizes z{};
+  z.pool_n = H.pool;
+  z.w_n = std::max(1LL, H.wpool) * H.Ns;
+  z.idx_n = (int)H.h_idx.size();
+  z.cmap_n = (int)std::max<size_t>(1, H.h_cmap.size());
+  z.nf = (int)H.h_fronts.size();
+  return z;
+}
+
 cudaError_t launch_nd_factor(const NDHost& H, const double* Ac, int* status, cudaStream_t s) {
+  const NDSizes zs = nd_sizes(H);
   for (int l = 0; l < H.nlev; ++l) {
     const int f0 = H.lev_off[l], nf = H.lev_off[l + 1] - f0;
     if (nf <= 0) continue;
     const int Q = H.lev_team[l];
     k_nd_assemble<<<dim3(Q, nf), kNdThreads, 0, s>>>(H.fronts, f0, H.idx, H.cmap, H.F, Ac, H.Nc,
-                                                     H.g[0], H.g[1], H.d);
+                                                     H.g[0], H.g[1], H.d, zs, H.lev_maxF[l]);
     const size_t sh = factor_smem(H.lev_maxF[l], Q);
     cudaError_t e = cudaFuncSetAttribute(k_nd_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sh);
@@ -625,13 +688,15 @@ cudaError_t launch_nd_factor(const NDHost& H, const double* Ac, int* status, cud
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_nd_factor, (const NDFrontDev*)H.fronts, f0, Q, H.F, status);
+    e = cudaLaunchKernelEx(&cfg, k_nd_factor, (const NDFrontDev*)H.fronts, f0, Q, H.F, status, zs,
+                           H.lev_maxF[l], (const int*)H.idx, H.Nc);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
 cudaError_t launch_nd_solve(const NDHost& H, double* rhs, int Ns, int transpose, cudaStream_t s) {
+  const NDSizes zs = nd_sizes(H);
   const int shmax = (int)solve_smem(H.maxF);
   cudaError_t e = cudaFuncSetAttribute(k_nd_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, shmax);
   if (e == cudaSuccess)
@@ -642,14 +707,14 @@ cudaError_t launch_nd_solve(const NDHost& H, double* rhs, int Ns, int transpose,
     if (nf <= 0) continue;
     const size_t sh = solve_smem(H.lev_maxF[l]);
     k_nd_forward<<<dim3(nf, Ns), kNdSolveThreads, sh, s>>>(H.fronts, f0, H.idx, H.cmap, H.F, H.W, rhs, Ns, H.Nc,
-                                            H.lev_maxF[l], transpose);
+                                            H.lev_maxF[l], transpose, zs);
   }
   for (int l = H.nlev - 1; l >= 0; --l) {
     const int f0 = H.lev_off[l], nf = H.lev_off[l + 1] - f0;
     if (nf <= 0) continue;
     const size_t sh = solve_smem(H.lev_maxF[l]);
     k_nd_backward<<<dim3(nf, Ns), kNdSolveThreads, sh, s>>>(H.fronts, f0, H.idx, H.F, rhs, Ns, H.Nc,
-                                             H.lev_maxF[l], transpose);
+                                             H.lev_maxF[l], transpose, zs);
   }
   return cudaGetLastError();
 }

@@ -78,6 +78,14 @@ struct LocalLaunch {
   double* scratch;    // per-group scratch in global memory (null when not needed)
   long long scratch_group;  // doubles of scratch per thread group
   const InstPtrs* inst;     // fused launch: per-instance arrays (null: one instance)
+  // sizes for the work-descriptor checks of a checked build (MSFV_CHECKED): doubles of
+  // the scratch buffer, of the stored factors and entries of the receiver lists (one
+  // instance; a fused launch has them per instance), instances of a fused launch
+  long long scratch_n;
+  long long fac_n;
+  long long rec_n;
+  int n_inst;
+  int pad_;
 };
 
 struct DevGeom {
@@ -100,6 +108,8 @@ struct InstPtrs {
   const double* ZT;    // adjoint: receiver seeds
   double* MU;          // adjoint: mu for the lower-dimensional entities
   double* gTloc;       // adjoint: transmissibility gradient of the local problems
+  long long fac_n;     // doubles of fac (checked builds verify the entities' ranges)
+  long long rec_n;     // entries of rec_p / rec_u
 };
 
 // Cells and primal blocks of the nodal Galerkin variant (the DevGeom of a nodal session

@@ -166,6 +166,35 @@ int cuda_fail(msfv_session* s, cudaError_t e, const char* where) {
   return fail(s, MSFV_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// MSFV_DEBUG_SYNC=1 (read once): after every phase and every fused launch enqueued on a
+// stream that is not being captured, synchronise that stream and name the first step
+// that failed on stderr, with the instance it belongs to.  A debugging aid: it
+// serialises the work.
+bool debug_sync_on() {
+  static const bool on = [] {
+    const char* e = getenv("MSFV_DEBUG_SYNC");
+    return e && atoi(e) > 0;
+  }();
+  return on;
+}
+
+std::string session_tag(const msfv_session* s) {
+  char buf[128];
+  const DevGeom& g = s->dg;
+  snprintf(buf, sizeof(buf), "%dD %dx%dx%d c=%d Ns=%d", g.d, g.n[0], g.n[1], g.d == 3 ? g.n[2] : 1,
+           g.c, s->Ns);
+  return buf;
+}
+
+void debug_check(cudaStream_t st, const char* what, const std::string& who) {
+  if (!debug_sync_on()) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess)
+    fprintf(stderr, "msfv debug: %s of %s failed: %s\n", what, who.c_str(), cudaGetErrorString(e));
+}
+
 struct PhaseScope {
   msfv_session* s;
   int ph;
@@ -182,6 +211,7 @@ struct PhaseScope {
       cudaEventRecord(b, s->stream);
       s->pending.push_back({ph, a, b});
     }
+    if (debug_sync_on()) debug_check(s->stream, kPhaseNames[ph], session_tag(s));
   }
 };
 
@@ -1043,15 +1073,24 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     delete s;
     return fail(nullptr, MSFV_ERR_CUDA, msg);
   }
+  const long long fac_n = s->fac ? (s->mixed_top ? fac_lower : fac_total) : 0;
   for (int k = 1; k <= d; ++k) {
     s->launch[k].ents = s->d_ents[k];
     s->launch[k].counter = s->local_ctr + 3 * k;
     s->launch[k].scratch = s->launch[k].scratch_group ? s->local_scratch : nullptr;
+    s->launch[k].scratch_n = s->launch[k].scratch ? s->local_scratch_n : 0;
+    s->launch[k].fac_n = fac_n;
+    s->launch[k].rec_n = (long long)rec_p.size();
+    s->launch[k].n_inst = 1;
   }
   if (nodal) {
     s->launch_adj.ents = s->d_ents_adj;
     s->launch_adj.counter = s->launch[d].counter;
     s->launch_adj.scratch = s->launch[d].scratch;
+    s->launch_adj.scratch_n = s->launch[d].scratch_n;
+    s->launch_adj.fac_n = fac_n;
+    s->launch_adj.rec_n = (long long)rec_p.size();
+    s->launch_adj.n_inst = 1;
   }
   for (int k = 0; k <= 3; ++k) {
     SrcLaunch& SL = s->src_L[k];
@@ -1113,6 +1152,10 @@ void coarse_solve(msfv_session* s, double* rhs, int transpose) {
     launch_band_solve(s->band, rhs, s->Ns, Nc, transpose, s->stream);
   }
   s->launches += 1;
+  if (debug_sync_on())
+    debug_check(s->stream, s->use_nd ? "nested-dissection solve" : s->use_mg ? "multigrid GMRES solve"
+                                                                           : "banded LU solve",
+                session_tag(s));
 }
 
 // factorisation (banded LU) or hierarchy (multigrid) of the new A_c
@@ -1129,6 +1172,10 @@ void coarse_prepare(msfv_session* s) {
     launch_band_factor(s->band, s->stream);
     s->launches += 2;
   }
+  if (debug_sync_on())
+    debug_check(s->stream, s->use_nd ? "nested-dissection factorisation"
+                           : s->use_mg ? "multigrid set-up" : "banded LU factorisation",
+                session_tag(s));
 }
 
 // ---- nodal Galerkin variant ------------------------------------------------------------
@@ -1730,6 +1777,8 @@ cudaError_t batch_plan_groups(msfv_batch* b) {
       ip.ZT = s->ZT;
       ip.MU = s->X;
       ip.gTloc = s->gT;
+      ip.fac_n = L.fac_n;
+      ip.rec_n = L.rec_n;
       inst.push_back(ip);
     }
     // largest first, so the persistent launch ends with the small entities
@@ -1764,6 +1813,10 @@ cudaError_t batch_plan_groups(msfv_batch* b) {
     G.L.inst = G.d_inst;
     G.L.counter = G.counter;
     G.L.scratch = G.scratch;
+    G.L.scratch_n = G.scratch ? scr : 0;
+    G.L.n_inst = (int)inst.size();
+    G.L.fac_n = 0;   // per instance (InstPtrs)
+    G.L.rec_n = 0;
     const int gi = (int)b->groups.size();
     b->groups.push_back(G);   // released with the batch even when a later step failed
     if (e != cudaSuccess) return e;
@@ -1837,6 +1890,8 @@ int batch_enqueue(msfv_batch* b, bool timed, std::string* msg_out, cudaError_t* 
       if (e == cudaSuccess) e = cudaStreamWaitEvent(GS(G), b->ev_pre[k], 0);
     if (e == cudaSuccess && timed) e = cudaEventRecord(G.t_ev[0], GS(G));
     if (e == cudaSuccess) launch_local_forward_fused(G.g, G.L, GS(G));
+    if (e == cudaSuccess && debug_sync_on())
+      debug_check(GS(G), "fused interior forward", "fused group of " + session_tag(b->ss[G.members[0]]));
     if (e == cudaSuccess && timed) e = cudaEventRecord(G.t_ev[1], GS(G));
     if (e == cudaSuccess) e = cudaEventRecord(G.ev_fwd, GS(G));
   }
@@ -1860,6 +1915,8 @@ int batch_enqueue(msfv_batch* b, bool timed, std::string* msg_out, cudaError_t* 
       if (e == cudaSuccess) e = cudaStreamWaitEvent(GS(G), b->ev_mid[k], 0);
     if (e == cudaSuccess && timed) e = cudaEventRecord(G.t_ev[2], GS(G));
     if (e == cudaSuccess) launch_local_adjoint_fused(G.g, G.L, GS(G));
+    if (e == cudaSuccess && debug_sync_on())
+      debug_check(GS(G), "fused interior adjoint", "fused group of " + session_tag(b->ss[G.members[0]]));
     if (e == cudaSuccess && timed) e = cudaEventRecord(G.t_ev[3], GS(G));
     if (e == cudaSuccess) e = cudaEventRecord(G.ev_adj, GS(G));
   }

@@ -322,7 +322,9 @@ class GpuBackend:
     def ok(self, tok) -> bool:
         """Numerical status of a finished request (its event has completed, so reading the
         status waits for nothing but a few bytes): False when the session's local pivots
-        or coarse solve failed or a device-side wait expired."""
+        or coarse solve failed or a device-side wait expired.  Any other error (a CUDA
+        error: the context is no longer usable) is raised, not counted as a failed
+        request."""
         from .msfv import MSFVError
         h = tok[2]
         try:
@@ -330,8 +332,10 @@ class GpuBackend:
                 h["batch"].check()
             else:
                 h["sess"].check()
-        except MSFVError:
-            return False
+        except MSFVError as e:
+            if e.code in (3, 4):          # MSFV_ERR_NUMERIC, MSFV_ERR_TIMEOUT
+                return False
+            raise
         return True
 
     def result(self, tok):
