@@ -273,7 +273,9 @@ int msfv_batch_destroy(msfv_batch_t* b);
  * results are bit for bit those of the instances run alone).  MSFV_BATCH_FUSE=0 at
  * msfv_batch_create keeps every instance in its own branch.
  *   out[0] instances, out[1] fused groups, out[2] instances in them, out[3] their
- *   interiors (one entry per fused launch's work item); n_out may be smaller than 4. */
+ *   interiors (one entry per fused launch's work item), out[4] the device bytes the
+ *   batch allocated itself for them (work lists, instance tables, scratch), beyond the
+ *   sessions' workspaces; n_out may be smaller than 5. */
 int msfv_batch_info(const msfv_batch_t* b, int64_t* out, int n_out);
 /* One step like msfv_batch_run, enqueued eagerly on the same streams instead of as the
  * graph, with CUDA events around every fused interior launch; synchronises and reports

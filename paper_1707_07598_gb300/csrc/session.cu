@@ -1015,7 +1015,9 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     return fail(nullptr, oom ? MSFV_ERR_OOM : MSFV_ERR_CUDA, msg);
   }
   cudaStream_t st = s->stream;
-  ce = upload(s->rec, rec, st);
+  // no forward has run yet: the numerical status reads as clean
+  ce = cudaMemsetAsync(s->status, 0, sizeof(int) * (2 + (size_t)s->Ns), st);
+  if (ce == cudaSuccess) ce = upload(s->rec, rec, st);
   if (ce == cudaSuccess) ce = upload(s->ru_cell, ru, st);
   if (ce == cudaSuccess) ce = upload(s->ru_off, ru_off, st);
   if (ce == cudaSuccess) ce = upload(s->ru_idx, ru_idx, st);
@@ -1672,6 +1674,7 @@ struct FusedGroup {
   cudaEvent_t ev_fwd = nullptr, ev_adj = nullptr, ev_end = nullptr;
   cudaEvent_t t_ev[4] = {nullptr, nullptr, nullptr, nullptr};  // timed run: around the launches
   double flops = 0.0;                 // algorithmic FP64 flops of the fused forward launch
+  long long bytes = 0;                // device bytes of the group's tables and scratch
 };
 
 struct msfv_batch {
@@ -1809,6 +1812,8 @@ cudaError_t batch_plan_groups(msfv_batch* b) {
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     for (int q = 0; q < 4 && e == cudaSuccess; ++q) e = cudaEventCreate(&G.t_ev[q]);
     for (size_t i = 0; i < ents.size(); ++i) G.flops += cost[i];
+    G.bytes = (long long)(sizeof(EntDesc) * sorted.size() + sizeof(InstPtrs) * inst.size() +
+                          sizeof(int) * 4 + sizeof(double) * (size_t)std::max(0LL, scr));
     G.L.ents = G.d_ents;
     G.L.inst = G.d_inst;
     G.L.counter = G.counter;
@@ -1984,7 +1989,7 @@ extern "C" int msfv_batch_create(msfv_session_t* const* sessions, int K,
   e = batch_plan_groups(b);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return batch_fail(b, MSFV_ERR_CUDA,
+    return batch_fail(b, e == cudaErrorMemoryAllocation ? MSFV_ERR_OOM : MSFV_ERR_CUDA,
                       std::string("batch fused launches: ") + cudaGetErrorString(e));
   }
   e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
@@ -2124,12 +2129,13 @@ extern "C" int msfv_batch_run_timed(msfv_batch_t* b, double* fused_ms, double* f
 
 extern "C" int msfv_batch_info(const msfv_batch_t* b, int64_t* out, int n_out) {
   if (!b || !out) return MSFV_ERR_ARG;
-  int64_t v[4] = {(int64_t)b->ss.size(), (int64_t)b->groups.size(), 0, 0};
+  int64_t v[5] = {(int64_t)b->ss.size(), (int64_t)b->groups.size(), 0, 0, 0};
   for (const auto& G : b->groups) {
     v[2] += (int64_t)G.members.size();
     v[3] += G.L.n_ents;
+    v[4] += G.bytes;
   }
-  for (int i = 0; i < n_out && i < 4; ++i) out[i] = v[i];
+  for (int i = 0; i < n_out && i < 5; ++i) out[i] = v[i];
   return MSFV_OK;
 }
 

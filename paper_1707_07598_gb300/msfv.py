@@ -468,12 +468,12 @@ class Batch:
                 for g in range(ng)]
 
     def info(self) -> dict:
-        out = (ctypes.c_int64 * 4)()
-        rc = self._lib.msfv_batch_info(self._h, out, 4)
+        out = (ctypes.c_int64 * 5)()
+        rc = self._lib.msfv_batch_info(self._h, out, 5)
         if rc != MSFV_OK:
             raise MSFVError(rc, "msfv_batch_info failed")
-        return dict(zip(["instances", "fused_groups", "fused_instances", "fused_entities"],
-                        list(out)))
+        return dict(zip(["instances", "fused_groups", "fused_instances", "fused_entities",
+                         "device_bytes"], list(out)))
 
     def check(self):
         rc = self._lib.msfv_batch_check(self._h)

@@ -250,6 +250,10 @@ class GpuBackend:
         self.factor_mode = factor_mode
         self.use_graph = use_graph
         self.copy_back = copy_back
+        # the inputs of every new client are drawn on this one stream: torch caches the
+        # temporaries of the field synthesis (up to ~10 GB at 256^3) per stream, so one
+        # stream keeps that cache bounded instead of growing with the number of clients
+        self.setup_stream = None
 
     def open(self, spec, budget_bytes: int):
         from . import workloads as W
@@ -274,24 +278,49 @@ class GpuBackend:
             # the library's up-front estimate was short of what it allocated
             sess.close()
             raise DoesNotFit()
-        with torch.cuda.stream(stream):
-            m0 = W.gaussian_random_field_device(prob.n, spec.corr_len, spec.seed, self.device)
+        if self.setup_stream is None:
+            self.setup_stream = torch.cuda.Stream(device=self.device)
+        with torch.cuda.stream(self.setup_stream):
+            m0_t = W.gaussian_random_field_device(prob.n, spec.corr_len, spec.seed, self.device)
             g = torch.Generator(device=self.device)
             g.manual_seed(spec.seed + 1)
-            dm = torch.randn(prob.N, generator=g, device=self.device, dtype=torch.float64)
-            d_obs = 1e-3 * torch.randn((prob.n_src, prob.n_rec), generator=g,
-                                       device=self.device, dtype=torch.float64)
+            dm_t = torch.randn(prob.N, generator=g, device=self.device, dtype=torch.float64)
+            dobs_t = 1e-3 * torch.randn((prob.n_src, prob.n_rec), generator=g,
+                                        device=self.device, dtype=torch.float64)
+        self.setup_stream.synchronize()
+        # the client's own buffers live on its stream; the set-up temporaries are released
+        # only after the copies that read them have run
+        with torch.cuda.stream(stream):
+            m0, dm, d_obs = m0_t.clone(), dm_t.clone(), dobs_t.clone()
             m = m0.clone()
+        stream.synchronize()
+        del m0_t, dm_t, dobs_t
         h = {"sess": sess, "stream": stream, "prob": prob, "m0": m0, "dm": dm, "m": m,
              "d_obs": d_obs, "batch": None}
+        extra = 0
         if self.use_graph:
-            stream.synchronize()
-            h["batch"] = Batch([sess], [m], [d_obs], stream=stream)
+            try:
+                with torch.cuda.stream(stream):
+                    h["batch"] = Batch([sess], [m], [d_obs], stream=stream)
+            except MSFVError as e:
+                sess.close()
+                if e.code == 2:          # its fused-launch buffers do not fit right now
+                    raise DoesNotFit() from e
+                raise
+            # the batch's own buffers (fused work lists and scratch) count against the
+            # budget like the session's
+            extra = int(h["batch"].info()["device_bytes"])
         else:
-            h["d_pred"] = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64,
-                                      device=self.device)
-            h["grad"] = torch.empty(prob.N, dtype=torch.float64, device=self.device)
-        nbytes = int(sess.info()["workspace_bytes"]) + own
+            with torch.cuda.stream(stream):
+                h["d_pred"] = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64,
+                                          device=self.device)
+                h["grad"] = torch.empty(prob.N, dtype=torch.float64, device=self.device)
+        nbytes = int(sess.info()["workspace_bytes"]) + own + extra
+        if nbytes > budget_bytes:
+            if h["batch"] is not None:
+                h["batch"].close()
+            sess.close()
+            raise DoesNotFit()
         return h, nbytes
 
     def launch(self, h, req):
