@@ -824,7 +824,11 @@ def run_batched(args):
 
 def run_served(args):
     """The Poisson request stream (rate x duration), fine sizes 32..256^3, c in {4, 8, 16},
-    1-64 dipoles, 150 GB budget: continuous batching against one request at a time."""
+    1-64 dipoles, 150 GB budget: continuous batching against one request at a time.
+    Runs the checked build of the library (MSFV_CHECKED=1 unless set otherwise): its local
+    and nested-dissection kernels validate every work descriptor before they touch its
+    storage."""
+    os.environ.setdefault("MSFV_CHECKED", "1")
     torch, dev = _gpu_setup()
     from paper_1707_07598_gb300.serve import GpuBackend, Server
     reqs = W.served_requests(rate=args.rate, duration=args.duration)
@@ -853,6 +857,7 @@ def run_served(args):
            "steps": len(reqs), "warmup": len(warm), "ms_per_step": 1000.0 / max(sv["value"], 1e-12),
            "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "build": "checked" if os.environ.get("MSFV_CHECKED", "0") not in ("", "0") else "default",
            "config": {"workload": f"served_poisson_{args.rate:g}_per_s_{args.duration:g}_s",
                       "requests": len(reqs), "sizes": [32, 64, 128, 256],
                       "coarsenings": [4, 8, 16], "sources": "1-64", "hbm_budget_bytes": budget,
