@@ -782,7 +782,17 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       s->use_nd = false;
     }
     if (env && !strcmp(env, "nd")) s->use_nd = true;
-    if (s->use_nd) s->nd.max_team = nd_max_team();
+    if (s->use_nd) {
+      // largest cluster per front: what the device runs (16 or 8), or MSFV_ND_MAX_TEAM
+      // (1, 2, 4, 8, 16; at most the device's)
+      s->nd.max_team = nd_max_team();
+      const char* te = getenv("MSFV_ND_MAX_TEAM");
+      if (te && atoi(te) > 0) {
+        int t = 1;
+        while (t * 2 <= atoi(te) && t * 2 <= s->nd.max_team) t *= 2;
+        s->nd.max_team = t;
+      }
+    }
     if (s->use_nd && !nd_setup(s->nd, g, s->Ns)) s->use_nd = false;
     if (s->use_nd) s->use_mg = false;
     if (s->use_mg) {
