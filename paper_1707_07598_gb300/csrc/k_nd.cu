@@ -360,25 +360,28 @@ __global__ void __launch_bounds__(kNdThreads, 1) k_nd_factor(const NDFrontDev* _
     const int r0 = min(nrow, rank * rper), r1 = min(nrow, r0 + rper);
     double* Ls = sm;                                   // (r1 - r0) x kNdPanel
     double* Us = sm + (long long)rper * kNdPanel;      // kNdPanel x nrow
-    // 2. L block rows: x U11 = a (row by row)
+    // 2. L block rows: x U11 = a (row by row; the row's loads are issued together,
+    // before the solve and its stores, instead of one L2 round trip per column)
     for (int i = r0 + tid; i < r1; i += kNdThreads) {
       double* Mi = M + (long long)(e0 + i) * F + k0;
       double x[kNdPanel];
 #pragma unroll
+      for (int q = 0; q < kNdPanel; ++q) x[q] = (q < kb) ? ldg_cg(Mi + q) : 0.0;
+#pragma unroll
       for (int q = 0; q < kNdPanel; ++q) {
         if (q < kb) {
-          double v = ldg_cg(Mi + q);
+          double v = x[q];
 #pragma unroll
           for (int q2 = 0; q2 < kNdPanel; ++q2)
             if (q2 < q) v = fma(-x[q2], D[q2 * kNdPanel + q], v);
           x[q] = v * rdg[q];
-          Mi[q] = x[q];
-        } else {
-          x[q] = 0.0;
         }
       }
 #pragma unroll
-      for (int q = 0; q < kNdPanel; ++q) Ls[(i - r0) * kNdPanel + q] = x[q];
+      for (int q = 0; q < kNdPanel; ++q) {
+        if (q < kb) Mi[q] = x[q];
+        Ls[(i - r0) * kNdPanel + q] = x[q];
+      }
     }
     // 3. U block row: L11 u = a (column by column)
     {
@@ -387,16 +390,21 @@ __global__ void __launch_bounds__(kNdThreads, 1) k_nd_factor(const NDFrontDev* _
       for (int c = c0 + tid; c < c1; c += kNdThreads) {
         double u[kNdPanel];
 #pragma unroll
+        for (int q = 0; q < kNdPanel; ++q)
+          u[q] = (q < kb) ? ldg_cg(M + (long long)(k0 + q) * F + e0 + c) : 0.0;
+#pragma unroll
         for (int q = 0; q < kNdPanel; ++q) {
           if (q < kb) {
-            double v = ldg_cg(M + (long long)(k0 + q) * F + e0 + c);
+            double v = u[q];
 #pragma unroll
             for (int q2 = 0; q2 < kNdPanel; ++q2)
               if (q2 < q) v = fma(-D[q * kNdPanel + q2], u[q2], v);
             u[q] = v;
-            M[(long long)(k0 + q) * F + e0 + c] = v;
           }
         }
+#pragma unroll
+        for (int q = 0; q < kNdPanel; ++q)
+          if (q < kb) M[(long long)(k0 + q) * F + e0 + c] = u[q];
       }
     }
     if (Q > 1) cl.sync(); else __syncthreads();
