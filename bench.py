@@ -87,7 +87,8 @@ def parse():
     p.add_argument("--instance-budget-gb", type=float, default=0.0,
                    help="batched: per-instance HBM budget (0 = store every local factor)")
     p.add_argument("--no-autotune", action="store_true",
-                   help="batched: skip the autotuner (default: tune each instance class once)")
+                   help="skip the autotuner (default: the batched line tunes each instance "
+                        "class once, the plain lines their session)")
     p.add_argument("--plain-reps", type=int, default=2,
                    help="batched: timed passes of the one-at-a-time comparison")
     p.add_argument("--rate", type=float, default=50.0, help="served: requests per second")
@@ -458,7 +459,8 @@ def plain_measure(args, dev, sess, prob, m, d_obs, world=1):
             "roofline": roof, "e2e": e2e, "gpu_launches": launches,
             "phases_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in phases.items() if v[1]},
             "coarse": {"solver": COARSE_SOLVERS[info["coarse_solver"]],
-                       "iters_fwd": info["coarse_iters"], "iters_adj": info["coarse_iters_T"]}}
+                       "iters_fwd": info["coarse_iters"], "iters_adj": info["coarse_iters_T"]},
+            "kernel_shapes": getattr(args, "tuned_shapes", None)}
 
 
 def open_plain(args, dev, seed_model=2, seed_truth=3, seed_noise=4):
@@ -470,6 +472,9 @@ def open_plain(args, dev, seed_model=2, seed_truth=3, seed_noise=4):
     prob, m_np = W.config_3d_128(seed=seed_model, n=args.n, coarsen=c)
     sess = Session(prob, stream=torch.cuda.current_stream(dev))
     m = torch.from_numpy(m_np).to(dev)
+    if not getattr(args, "no_autotune", False):
+        # kernel shape per entity class (set-up, outside any timing)
+        args.tuned_shapes = {k: v[0] for k, v in sess.autotune(m).items()}
     m_true = torch.from_numpy(W.config_3d_128(seed=seed_truth, n=args.n, coarsen=c)[1]).to(dev)
     d_true = sess.forward(m_true).clone()
     noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, seed_noise)).to(dev)
@@ -512,7 +517,8 @@ def run_plain(args):
                                    "the coarse-cell centre)"},
                "roofline": res["roofline"], "cpu_baseline": None, "e2e": res["e2e"],
                "gpu_launches": res["gpu_launches"], "clocks": clk,
-               "phases_ms_per_step": res["phases_ms_per_step"], "coarse": res["coarse"]}
+               "phases_ms_per_step": res["phases_ms_per_step"], "coarse": res["coarse"],
+               "kernel_shapes": res["kernel_shapes"]}
         print(json.dumps(out))
     sess.close()
     if world > 1:
