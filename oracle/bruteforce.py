@@ -28,12 +28,21 @@ def _coords(n):
     return out
 
 
-def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec, source_bases=False):
+def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec, source_bases=False, oversample=0):
     """Predicted data (Ns, Nr) for model m (real or complex), dense linear algebra.
 
     source_bases: also solve, level by level, the tangential systems with the source
     as forcing and zero vertex values (Sec. 3.2, source bases) and add that field
-    with coefficient one, the reduced right-hand side becoming R (q - A C)."""
+    with coefficient one, the reduced right-hand side becoming R (q - A C).
+
+    oversample = w > 0 (Sec. 6 names oversampling without a construction; the reading
+    is the oracle's): on the levels below d every piece of the level is solved on its
+    own, on the cells that share its off-vertex intervals and lie within w of its
+    vertex coordinates.  That system is cut out of the dense fine operator A: the rows
+    and columns of those cells, with the flux across the sides normal to the piece
+    taken off the diagonal; every neighbour across a tangential end contributes the
+    already known basis row of its projection onto the piece's vertex coordinates.
+    All Nc basis columns are solved at once, so no corner bookkeeping is needed."""
     n = tuple(int(v) for v in n)
     d = len(n)
     N = int(np.prod(n))
@@ -80,6 +89,9 @@ def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec, source_bases=False):
         rows = np.nonzero(level == k)[0]
         if len(rows) == 0:
             continue
+        if oversample and k < d:
+            _oversampled_level(A, Tface, Phi, X, rows, isvert, n, c, stride, oversample)
+            continue
         M = np.zeros((len(rows), N), dtype=dt)
         for r, x in enumerate(rows):
             for a in range(d):
@@ -113,10 +125,55 @@ def forward_dense(m, n, c, src_pos, src_neg, src_amp, rec, source_bases=False):
     return out, Phi, Ac
 
 
+def _oversampled_level(A, Tface, Phi, X, rows, isvert, n, c, stride, w):
+    """Fill Phi on the cells `rows` of one level, piece by piece, by oversampled solves."""
+    d = len(n)
+    half = c // 2
+    N = A.shape[0]
+    interval = (X - half) // c            # per axis: which open interval (off-vertex axes)
+    pieces = {}
+    for x in rows:
+        key = tuple(int(X[x, a]) if isvert[x, a] else ('I', int(interval[x, a]))
+                    for a in range(d))
+        pieces.setdefault(key, []).append(int(x))
+    for key, own in pieces.items():
+        x0 = own[0]
+        vert = [a for a in range(d) if isvert[x0, a]]
+        offv = [a for a in range(d) if not isvert[x0, a]]
+        sel = np.ones(N, dtype=bool)
+        for a in offv:
+            sel &= (~isvert[:, a]) & (interval[:, a] == interval[x0, a])
+        for b in vert:
+            sel &= np.abs(X[:, b] - X[x0, b]) <= w
+        box = np.nonzero(sel)[0]
+        pos = {int(y): i for i, y in enumerate(box)}
+        M = A[np.ix_(box, box)].copy()
+        rhs = np.zeros((len(box), Phi.shape[1]), dtype=Phi.dtype)
+        for i, x in enumerate(box):
+            for a in range(d):
+                for s in (-1, 1):
+                    ca = X[x, a] + s
+                    if not 0 <= ca < n[a]:
+                        continue
+                    y = int(x + s * stride[a])
+                    if y in pos:
+                        continue
+                    t = Tface[(int(x), y)]
+                    if a in vert:
+                        M[i, i] -= t                  # normal side of the box: no flux
+                    else:
+                        yp = y - sum((X[y, b] - X[x0, b]) * stride[b] for b in vert)
+                        rhs[i] += t * Phi[yp]         # Dirichlet value at the projection
+        sol = np.linalg.solve(M, rhs)
+        for x in own:
+            Phi[x] = sol[pos[x]]
+
+
 def data(m, prob):
     d, _, _ = forward_dense(m, prob.n, prob.coarsen, prob.src_pos, prob.src_neg,
                             prob.src_amp, prob.rec_cell,
-                            source_bases=bool(getattr(prob, 'source_bases', False)))
+                            source_bases=bool(getattr(prob, 'source_bases', False)),
+                            oversample=int(getattr(prob, 'oversample', 0)))
     return d
 
 

@@ -44,6 +44,18 @@ system keeps the finite-volume restriction, A_c t_j = R (q_j - A C_j).  Its
 sensitivity adds the chain d C_j (same local operators, no new matrices):
 J = Pr^T ( Y(t) + dC + P dt/dm ),  dt/dm = -A_c^{-1} R ( G(u) + A Y(t) + A dC ).
 
+Oversampling (with width w > 0; Sec. 6 names it as a way to lessen the effect of the
+local boundary conditions on the basis but gives no construction, so this reading is
+ours): every dual edge and dual face solves its local problem on a box widened by w
+cells on both sides along its normal (vertex) axes, clipped to the mesh.  Inside that
+box all fluxes count, tangential and normal; across its normal sides none passes;
+across its tangential ends the Dirichlet value of a cell is the basis value already
+computed at the cell's projection onto the entity's own vertex planes (vertex values for
+an edge, edge values for a face).  Only the values on the entity's own cells enter P, so
+each cell still takes its basis values from exactly one local problem and the basis
+stays conforming; the dual-cell interiors are unchanged.  w = 0 is the plain method.
+Source bases are not defined with oversampling.
+
 Readings of the paper where it is silent or garbled are listed in the design
 notes of the repository; the ones that matter here: cell-centred FV with
 harmonic face averages, coarse vertex at fine index c*I + floor(c/2) per axis,
@@ -187,6 +199,12 @@ class Entity:
     g_ent: np.ndarray = None         # entity id of each boundary cell
     g_loc: np.ndarray = None         # local index of each boundary cell in its entity
     g_pos: np.ndarray = None         # (n_bnd, n_corners) corner position in that entity or -1
+    # oversampling: the cells the local problem is solved on (the entity itself unless it
+    # is widened), the positions of the entity's own cells among them, and the vertex
+    # coordinate of each normal axis (-1 on tangential axes)
+    solve_cells: np.ndarray = None
+    keep: np.ndarray = None
+    centre: tuple = None
 
 
 class Oracle:
@@ -206,6 +224,11 @@ class Oracle:
         self.st = strides_of(self.n)
         self.cst = strides_of(self.nc)
         self.source_bases = bool(getattr(prob, 'source_bases', False))
+        self.w = int(getattr(prob, 'oversample', 0))
+        if self.w < 0:
+            raise ValueError("oversampling width must be >= 0")
+        if self.w and self.source_bases:
+            raise ValueError("source bases are not defined with oversampling")
         self._build_entities()
         self._build_restriction_and_sources()
 
@@ -223,18 +246,23 @@ class Oracle:
                     ranges.append(np.arange(pc[3], pc[3] + pc[4]))
                     corner_lists.append([k for k in (pc[1], pc[2]) if k is not None])
                     axes.append(a)
-            # cells, axis 0 fastest
-            grids = np.meshgrid(*ranges[::-1], indexing='ij')
-            cells = np.zeros(grids[0].size, dtype=np.int64)
-            for k, g in enumerate(grids):
-                a = self.d - 1 - k
-                cells += g.reshape(-1) * self.st[a]
+            cells = self._box_cells(ranges)
             corners = []
             for ks in itertools.product(*corner_lists[::-1]):
                 ks = ks[::-1]
                 corners.append(sum(ks[a] * self.cst[a] for a in range(self.d)))
+            # oversampled box of an edge or face: +-w cells along its normal axes
+            centre = tuple(int(pc[2]) if pc[0] == 'V' else -1 for pc in combo)
+            solve_cells, keep = cells, np.arange(len(cells))
+            if self.w and 0 < len(axes) < self.d:
+                wide = [np.arange(max(0, centre[a] - self.w), min(self.n[a], centre[a] + self.w + 1))
+                        if centre[a] >= 0 else ranges[a] for a in range(self.d)]
+                solve_cells = self._box_cells(wide)
+                where = {int(x): i for i, x in enumerate(solve_cells)}
+                keep = np.array([where[int(x)] for x in cells], dtype=np.int64)
             ents.append(Entity(dim=len(axes), axes=tuple(axes), cells=cells,
-                               corners=np.array(corners, dtype=np.int64)))
+                               corners=np.array(corners, dtype=np.int64),
+                               solve_cells=solve_cells, keep=keep, centre=centre))
         ents.sort(key=lambda e: e.dim)
         self.entities = ents
         self.cell2ent = np.full(self.N, -1, dtype=np.int64)
@@ -248,31 +276,54 @@ class Oracle:
             if e.dim > 0:
                 self._describe(e, coords)
 
+    def _box_cells(self, ranges):
+        """Global indices of the box ranges[0] x ranges[1] (x ranges[2]), axis 0 fastest."""
+        grids = np.meshgrid(*ranges[::-1], indexing='ij')
+        cells = np.zeros(grids[0].size, dtype=np.int64)
+        for k, g in enumerate(grids):
+            a = self.d - 1 - k
+            cells += g.reshape(-1) * self.st[a]
+        return cells
+
+    def _project(self, e, y, coords):
+        """Cell y moved onto the entity's vertex planes (its normal coordinates set to
+        the entity's vertex coordinates): the source of y's Dirichlet value."""
+        for a in range(self.d):
+            if e.centre[a] >= 0:
+                y = y + (e.centre[a] - coords[y, a]) * self.st[a]
+        return int(y)
+
     def _describe(self, e, coords):
-        """Faces, boundary cells and gather indices of one local problem."""
-        me = self.cell2ent[e.cells[0]]
+        """Faces, boundary cells and gather indices of one local problem (on e.solve_cells:
+        the entity, or its oversampled box).  A face leaving the box along a tangential
+        axis couples to a Dirichlet cell; along a normal axis it is dropped (no flux)."""
+        loc = {int(x): i for i, x in enumerate(e.solve_cells)}
         fa, fb, fq, fax, fidx, bnd = [], [], [], [], [], {}
-        for p, x in enumerate(e.cells):
-            for a in e.axes:
+        for p, x in enumerate(e.solve_cells):
+            for a in range(self.d):
+                tangential = a in e.axes
                 for sgn in (+1, -1):
                     ca = coords[x, a] + sgn
                     if ca < 0 or ca >= self.n[a]:
                         continue                       # outer boundary: no flux
-                    y = x + sgn * self.st[a]
-                    inside = self.cell2ent[y] == me
+                    y = int(x + sgn * self.st[a])
+                    inside = y in loc
                     if inside and sgn < 0:
                         continue                       # internal faces once
+                    if not inside and not tangential:
+                        continue                       # normal side of the box: no flux
                     fax.append(a)
-                    fidx.append(min(x, y))
+                    fidx.append(min(int(x), y))
                     fa.append(p)
                     if inside:
-                        fb.append(self.cell2loc[y])
+                        fb.append(loc[y])
                         fq.append(-1)
                     else:
-                        if y not in bnd:
-                            bnd[y] = len(bnd)
+                        yb = self._project(e, y, coords)
+                        if yb not in bnd:
+                            bnd[yb] = len(bnd)
                         fb.append(-1)
-                        fq.append(bnd[y])
+                        fq.append(bnd[yb])
         e.f_axis = np.array(fax, dtype=np.int64)
         e.f_idx = np.array(fidx, dtype=np.int64)
         e.f_a = np.array(fa, dtype=np.int64)
@@ -314,7 +365,7 @@ class Oracle:
         (L_E phi_E + B_E phi_bnd)_a = sum over tangential faces (a,b) of
         T_ab (phi_a - phi_b); linear in T, so the same routine gives dL, dB.
         """
-        nE, nB = len(e.cells), len(e.bnd)
+        nE, nB = len(e.solve_cells), len(e.bnd)
         t = np.array([Tface[a][i] for a, i in zip(e.f_axis, e.f_idx)],
                      dtype=Tface[0].dtype) if len(e.f_axis) else np.zeros(0)
         inner = e.f_b >= 0
@@ -372,10 +423,11 @@ class Oracle:
         T, Dx, Dy = transmissibility(m, self.n)
         st['m'], st['T'], st['Dx'], st['Dy'] = m, T, Dx, Dy
         Ns = self.prob.n_src
-        vals, lus, cvals = [], [], []
+        vals, lus, cvals, fulls = [], [], [], []
         for e in self.entities:
             if e.dim == 0:
                 vals.append(np.ones((1, 1)))
+                fulls.append(vals[-1])
                 lus.append(None)
                 cvals.append(np.zeros((1, Ns)))
                 continue
@@ -383,7 +435,9 @@ class Oracle:
             lu = spla.splu(L)
             phib = self.gather_boundary(e, vals)
             rhs = -(B @ phib)
-            vals.append(np.asarray(lu.solve(np.asarray(rhs))).reshape(len(e.cells), len(e.corners)))
+            full = np.asarray(lu.solve(np.asarray(rhs))).reshape(len(e.solve_cells), len(e.corners))
+            fulls.append(full)                         # the whole (oversampled) solution
+            vals.append(full[e.keep])                  # its values on the entity's cells
             lus.append(lu)
             if self.source_bases:
                 # L_E c_E = q_E - B_E c_bnd, one column per source
@@ -392,7 +446,7 @@ class Oracle:
                 cvals.append(np.asarray(lu.solve(np.asarray(rhs_c))).reshape(len(e.cells), Ns))
             else:
                 cvals.append(np.zeros((len(e.cells), Ns)))
-        st['vals'], st['lus'], st['cvals'] = vals, lus, cvals
+        st['vals'], st['lus'], st['cvals'], st['fulls'] = vals, lus, cvals, fulls
         P = self.assemble_P(vals)
         A = fine_operator(T, self.n)
         Ac = (self.R @ A @ P).tocsr()
@@ -447,7 +501,7 @@ class Oracle:
         dT = self.dT_of(st, v)
         Ns = self.prob.n_src
         dvals, dcvals = [], []
-        for e, val, cval, lu in zip(self.entities, st['vals'], st['cvals'], st['lus']):
+        for e, full, cval, lu in zip(self.entities, st['fulls'], st['cvals'], st['lus']):
             if e.dim == 0:
                 dvals.append(np.zeros((1, 1)))
                 dcvals.append(np.zeros((1, Ns)))
@@ -456,8 +510,9 @@ class Oracle:
             dL, dB = self.local_matrices(e, dT)
             phib = self.gather_boundary(e, st['vals'])
             dphib = self.gather_boundary(e, dvals)
-            rhs = -(dL @ val + dB @ phib + B @ dphib)
-            dvals.append(np.asarray(lu.solve(np.asarray(rhs))).reshape(val.shape))
+            rhs = -(dL @ full + dB @ phib + B @ dphib)
+            dfull = np.asarray(lu.solve(np.asarray(rhs))).reshape(full.shape)
+            dvals.append(dfull[e.keep])
             if self.source_bases:
                 cb = self.gather_source_boundary(e, st['cvals'])
                 dcb = self.gather_source_boundary(e, dcvals)
@@ -509,14 +564,17 @@ class Oracle:
             e = self.entities[eid]
             if e.dim == 0:
                 continue
-            val, lu = st['vals'][eid], st['lus'][eid]
+            full, lu = st['fulls'][eid], st['lus'][eid]
             L, B = self.local_matrices(e, T)
-            parts = [(val, self.gather_boundary(e, st['vals']), seeds, self.scatter_boundary)]
+            parts = [(full, self.gather_boundary(e, st['vals']), seeds, self.scatter_boundary)]
             if self.source_bases:
                 parts.append((st['cvals'][eid], self.gather_source_boundary(e, st['cvals']),
                               seeds_c, self.scatter_source_boundary))
             for sol, solb, sd, scatter in parts:
-                mu = np.asarray(lu.solve(np.asarray(sd[eid]))).reshape(sol.shape)
+                # the seeds live on the entity's own cells; zero elsewhere in its box
+                seed = np.zeros(sol.shape)
+                seed[e.keep] = sd[eid]
+                mu = np.asarray(lu.solve(seed)).reshape(sol.shape)
                 # -mu^T d(L x + B x_b)/dT_f = -(mu_a - mu_b)(x_a - x_b)
                 inner = e.f_b >= 0
                 mu_b = np.zeros((len(e.f_a), mu.shape[1]))

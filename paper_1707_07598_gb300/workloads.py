@@ -43,6 +43,8 @@ class Problem:
     source_bases: bool = False   # add one source basis function per source (Sec. 3.2)
     nodal: bool = False          # nodal Galerkin variant: sources / receivers index the
                                  # (n+1)^d nodes, m the n^d cells
+    oversample: int = 0          # oversampling width w of the dual edge / face problems
+                                 # (cells on each side, normal to the entity; 0: none)
 
     @property
     def dim(self) -> int:
@@ -140,7 +142,8 @@ def _distinct_cells(rng, n, count, top_layer: bool) -> np.ndarray:
 
 def make_problem(n: Sequence[int], coarsen: int, n_src: int, n_rec: int, seed: int,
                  top_layer: bool | None = None, name: str = "",
-                 source_bases: bool = False, nodal: bool = False) -> Problem:
+                 source_bases: bool = False, nodal: bool = False,
+                 oversample: int = 0) -> Problem:
     """Dipole sources and point receivers at seeded random distinct cells (nodes of the
     (n+1)^d node lattice when nodal)."""
     n = tuple(int(v) for v in n)
@@ -154,7 +157,8 @@ def make_problem(n: Sequence[int], coarsen: int, n_src: int, n_rec: int, seed: i
     rec = np.sort(_distinct_cells(rng, lat, n_rec, top_layer))
     return Problem(n=n, coarsen=int(coarsen), src_pos=src_pos, src_neg=src_neg,
                    src_amp=np.ones(n_src), rec_cell=rec, name=name,
-                   source_bases=bool(source_bases), nodal=bool(nodal))
+                   source_bases=bool(source_bases), nodal=bool(nodal),
+                   oversample=int(oversample))
 
 
 # ---------------------------------------------------------------------------
