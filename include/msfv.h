@@ -117,6 +117,22 @@ typedef struct msfv_desc {
                                index the nodes (x fastest).  Needs stored factors
                                (factor_mode 2 and source_bases are rejected);
                                msfv_gn_step is not available                           */
+  int oversample;           /* oversampling width w >= 0 of the dual edge and face
+                               problems (Sec. 6 names oversampling as a way to lessen
+                               the effect of the local boundary conditions; the
+                               construction is this library's reading).  0: none (the
+                               plain method).  w > 0: every dual edge and face solves
+                               its local problem on its box widened by w cells on both
+                               sides along its normal axes (clipped to the mesh), with
+                               all fluxes inside the box, none across its normal sides,
+                               and at its tangential ends the basis values at the
+                               projection onto its vertex planes; only its own cells
+                               enter P, so the basis stays conforming; the interiors
+                               are unchanged.  Needs w <= coarsen - 1, discretization
+                               0 and no source bases (MSFV_ERR_ARG otherwise).  The
+                               widened problems' factors are always stored.  Callers
+                               that built this struct before the field existed must
+                               zero it.                                                */
 } msfv_desc_t;
 
 typedef struct msfv_session msfv_session_t;

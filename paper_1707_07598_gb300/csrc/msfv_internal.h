@@ -428,4 +428,75 @@ long long nd_device_bytes(const NDHost& H);
 cudaError_t launch_nd_factor(const NDHost& H, const double* Ac, int* status, cudaStream_t s);
 // rhs: Ns x Nc, solved in place (entry 0 of every solution is zero); transpose: A_c^T
 cudaError_t launch_nd_solve(const NDHost& H, double* rhs, int Ns, int transpose, cudaStream_t s);
+// ---- oversampled dual edge and face problems (k_over.cu) -------------------------------
+// With oversampling width w > 0 every dual edge and dual face solves its local problem on
+// its box widened by w cells on both sides along its normal (vertex) axes, clipped to the
+// mesh: all fluxes inside the box, none across its normal sides, and at its tangential
+// ends the Dirichlet value of a cell taken from the basis value at the cell's projection
+// onto the entity's vertex planes.  Only the values on the entity's own cells (the box
+// cells at the vertex coordinates, "kept" cells) enter P.
+struct OvDesc {
+  int org[3], len[3];   // widened box per global axis (len 1 on axes >= d)
+  int str[3];           // local index stride per global axis (0 on axes >= d)
+  int ctr[3];           // vertex coordinate of each normal axis, -1 on tangential axes
+  int tang;             // bitmask of the entity's tangential axes
+  int slots, nvs;       // corner slots of the entity and their number
+  int n, b;             // box cells, half bandwidth of the box operator
+  int rec_off, rec_cnt; // receivers in kept cells: [rec_off, rec_off + rec_cnt) of the lists
+  long long fac;        // offsets (doubles): band factor n*(b+1)
+  long long sol;        //   whole-box solution, nvs*n (right-hand side major)
+  long long wrk;        //   adjoint / tangent solution, nvs*n
+  long long prv;        //   gradient contribution of each box face, 6*n (cell, axis, side)
+  long long sprv;       //   seeds for the lower level, 6*n*nvs, or -1
+  long long seed;       //   seeds from the upper level, nvs*n, or -1
+};
+// Device view of one level (edges or faces) for the kernels.
+struct OvLaunch {
+  const OvDesc* ents = nullptr;
+  int n_ents = 0;
+  int pull_mu = 0;      // 1: the interiors next to the kept cells pass mu (dim == d - 1)
+  double* fac = nullptr;
+  double* sol = nullptr;
+  double* wrk = nullptr;
+  double* prv = nullptr;
+  double* sprv = nullptr;
+  double* seed = nullptr;   // this level's seeds (written by the upper level's gather)
+  const int* rec_p = nullptr;
+  const int* rec_u = nullptr;
+  // sizes (doubles / entries) for the descriptor checks of a checked build
+  long long n_fac = 0, n_sol = 0, n_prv = 0, n_sprv = 0, n_seed = 0, n_rec = 0;
+  int n_ru = 0, pad_ = 0;
+};
+// out[dst[r]] (+)= sum of src[idx[k]], k in [ptr[r], ptr[r+1]): contributions of
+// overlapping boxes summed in a fixed order
+struct OvGather {
+  long long nrows = 0;
+  const long long* ptr = nullptr;
+  const long long* idx = nullptr;
+  const long long* dst = nullptr;
+};
+struct OvHost {
+  std::vector<OvDesc> h_ents;
+  std::vector<int> h_rec_p, h_rec_u;
+  std::vector<long long> g_ptr, g_idx, g_dst;   // face-gradient gather (rows: fine faces)
+  std::vector<long long> s_ptr, s_idx, s_dst;   // seed gather into the lower level
+  long long n_fac = 0, n_sol = 0, n_prv = 0, n_sprv = 0, n_seed = 0;
+  OvLaunch L;
+  OvGather G, S;
+};
+// Plan one level (k = 1 edges, k = 2 faces) from the plain entity list: boxes, offsets,
+// receivers (from the plain lists rec_p / rec_u) and the face-gradient gather.  lower:
+// the planned edge level when k = 2 and d = 3 (its seed gather is built here), else
+// null.  Returns an empty string or the reason it failed.
+std::string over_plan(const DevGeom& g, const std::vector<EntDesc>& ents,
+                      const std::vector<int>& rec_p, const std::vector<int>& rec_u, int w,
+                      int k, OvHost& H, OvHost* lower);
+void launch_over_forward(const DevGeom& g, const OvLaunch& L, const double* T, double* Pw,
+                         int* status, cudaStream_t s);
+void launch_over_adjoint(const DevGeom& g, const OvLaunch& L, const double* T, const double* Pw,
+                         const double* Lam, const double* ZT, const double* MU, cudaStream_t s);
+void launch_over_tangent(const DevGeom& g, const OvLaunch& L, const double* T, const double* Dl,
+                         const double* v, const double* Pw, double* dPw, cudaStream_t s);
+void launch_over_gather(const OvGather& G, const double* src, double* out, int accumulate,
+                        cudaStream_t s);
 }  // namespace msfv

@@ -134,6 +134,9 @@ struct msfv_session {
   bool use_mg = false;
   NDHost nd{};
   bool use_nd = false;   // nested-dissection LU (takes precedence over use_mg)
+  // oversampled dual edges (level 1) and faces (level 2 in 3D), width ov_w > 0
+  int ov_w = 0;
+  OvHost ov[3];
   bool have_forward = false;
   cudaError_t launch_error = cudaSuccess;
   std::string err;
@@ -322,6 +325,15 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     return fail(nullptr, MSFV_ERR_ARG, "source_bases must be 0 or 1");
   if (desc->source_bases && desc->factor_mode == 2)
     return fail(nullptr, MSFV_ERR_ARG, "source bases need the stored local factors");
+  if (desc->oversample < 0) return fail(nullptr, MSFV_ERR_ARG, "oversample must be >= 0");
+  if (desc->oversample > 0) {
+    if (nodal)
+      return fail(nullptr, MSFV_ERR_ARG, "oversampling is not available for the nodal variant");
+    if (desc->source_bases)
+      return fail(nullptr, MSFV_ERR_ARG, "source bases are not defined with oversampling");
+    if (desc->oversample > c - 1)
+      return fail(nullptr, MSFV_ERR_ARG, "oversample must be <= coarsen - 1");
+  }
 
   msfv_session* s = new msfv_session();
   s->stream = static_cast<cudaStream_t>(stream);
@@ -568,6 +580,19 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
         !local_plan(g, s->launch_adj, force_gw, s->launch[d].variant)) {
       delete s;
       return fail(nullptr, MSFV_ERR_ARG, "coarsening too large for the local problems");
+    }
+  }
+  // oversampled edges and faces: boxes, offsets, receivers and the gathers of their
+  // overlapping contributions (edges first: the faces' seed gather targets them)
+  if (desc->oversample > 0) {
+    s->ov_w = desc->oversample;
+    for (int k = 1; k < d; ++k) {
+      const std::string why = over_plan(g, s->h_ents[k], rec_p, rec_u, s->ov_w, k, s->ov[k],
+                                        (k == 2 && d == 3) ? &s->ov[1] : nullptr);
+      if (!why.empty()) {
+        delete s;
+        return fail(nullptr, MSFV_ERR_ARG, why);
+      }
     }
   }
   std::vector<int> cj_off(Nc + 1, 0), cj_u, cj_s;
@@ -881,6 +906,13 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
     for (auto& e : s->h_ents[d]) e.fac -= fac_lower;
     for (auto& e : s->h_ents_adj) e.fac -= fac_lower;
   }
+  for (int k = 1; k < d && s->ov_w; ++k) {
+    const OvHost& H = s->ov[k];
+    need += sizeof(double) * (size_t)(H.n_fac + 2 * H.n_sol + H.n_prv + H.n_sprv + H.n_seed) +
+            sizeof(OvDesc) * H.h_ents.size() + sizeof(int) * 2 * H.h_rec_p.size() +
+            sizeof(long long) * (H.g_ptr.size() + H.g_idx.size() + H.g_dst.size() +
+                                 H.s_ptr.size() + H.s_idx.size() + H.s_dst.size());
+  }
   need += s->fac_bytes + scr + sizeof(int) * 12;
   if (desc->hbm_budget_bytes && need > desc->hbm_budget_bytes) {
     delete s;
@@ -1017,6 +1049,38 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       s->src_F.e_sign = dalloc<double>(s, fl_sign.size(), &ce);
     }
   }
+  for (int k = 1; k < d && s->ov_w; ++k) {
+    OvHost& H = s->ov[k];
+    OvLaunch& L = H.L;
+    L.ents = dalloc<OvDesc>(s, H.h_ents.size(), &ce);
+    L.n_ents = (int)H.h_ents.size();
+    L.pull_mu = (k == d - 1) ? 1 : 0;
+    L.fac = dalloc<double>(s, (size_t)H.n_fac, &ce);
+    L.sol = dalloc<double>(s, (size_t)H.n_sol, &ce);
+    L.wrk = dalloc<double>(s, (size_t)H.n_sol, &ce);
+    L.prv = dalloc<double>(s, (size_t)H.n_prv, &ce);
+    L.sprv = H.n_sprv ? dalloc<double>(s, (size_t)H.n_sprv, &ce) : nullptr;
+    L.seed = H.n_seed ? dalloc<double>(s, (size_t)H.n_seed, &ce) : nullptr;
+    L.rec_p = dalloc<int>(s, H.h_rec_p.size(), &ce);
+    L.rec_u = dalloc<int>(s, H.h_rec_u.size(), &ce);
+    L.n_fac = H.n_fac;
+    L.n_sol = H.n_sol;
+    L.n_prv = H.n_prv;
+    L.n_sprv = H.n_sprv;
+    L.n_seed = H.n_seed;
+    L.n_rec = (long long)H.h_rec_p.size();
+    L.n_ru = s->Nru;
+    H.G.nrows = (long long)H.g_dst.size();
+    H.G.ptr = dalloc<long long>(s, H.g_ptr.size(), &ce);
+    H.G.idx = dalloc<long long>(s, H.g_idx.size(), &ce);
+    H.G.dst = dalloc<long long>(s, H.g_dst.size(), &ce);
+    H.S.nrows = (long long)H.s_dst.size();
+    if (H.S.nrows) {
+      H.S.ptr = dalloc<long long>(s, H.s_ptr.size(), &ce);
+      H.S.idx = dalloc<long long>(s, H.s_idx.size(), &ce);
+      H.S.dst = dalloc<long long>(s, H.s_dst.size(), &ce);
+    }
+  }
   if (ce != cudaSuccess) {
     const bool oom = (ce == cudaErrorMemoryAllocation);
     std::string msg = std::string("device allocation failed: ") + cudaGetErrorString(ce);
@@ -1074,6 +1138,28 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       if (ce == cudaSuccess) ce = upload(const_cast<long long*>(s->src_F.e_face), fl_face, st);
       if (ce == cudaSuccess) ce = upload(const_cast<double*>(s->src_F.e_sign), fl_sign, st);
     }
+  }
+  for (int k = 1; k < d && s->ov_w && ce == cudaSuccess; ++k) {
+    OvHost& H = s->ov[k];
+    OvLaunch& L = H.L;
+    ce = upload(const_cast<OvDesc*>(L.ents), H.h_ents, st);
+    if (ce == cudaSuccess) ce = upload(const_cast<int*>(L.rec_p), H.h_rec_p, st);
+    if (ce == cudaSuccess) ce = upload(const_cast<int*>(L.rec_u), H.h_rec_u, st);
+    if (ce == cudaSuccess) ce = upload(const_cast<long long*>(H.G.ptr), H.g_ptr, st);
+    if (ce == cudaSuccess) ce = upload(const_cast<long long*>(H.G.idx), H.g_idx, st);
+    if (ce == cudaSuccess) ce = upload(const_cast<long long*>(H.G.dst), H.g_dst, st);
+    if (ce == cudaSuccess && H.S.nrows) {
+      ce = upload(const_cast<long long*>(H.S.ptr), H.s_ptr, st);
+      if (ce == cudaSuccess) ce = upload(const_cast<long long*>(H.S.idx), H.s_idx, st);
+      if (ce == cudaSuccess) ce = upload(const_cast<long long*>(H.S.dst), H.s_dst, st);
+    }
+    // private slots no box writes (faces that do not exist, boxes without a derivative)
+    // and seeds nothing passes must read as zero
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(L.prv, 0, sizeof(double) * std::max(1LL, H.n_prv), st);
+    if (ce == cudaSuccess && L.sprv)
+      ce = cudaMemsetAsync(L.sprv, 0, sizeof(double) * (size_t)H.n_sprv, st);
+    if (ce == cudaSuccess && L.seed)
+      ce = cudaMemsetAsync(L.seed, 0, sizeof(double) * (size_t)H.n_seed, st);
   }
   if (ce == cudaSuccess) ce = cudaMemsetAsync(s->status, 0, (2 + s->Ns) * sizeof(int), st);
   if (ce == cudaSuccess && s->mg.trace)
@@ -1341,6 +1427,11 @@ int run_forward(msfv_session* s, const double* m, double* d_pred, double* u, int
   for (int k = 1; k <= d; ++k) {
     if ((part == 1 && k == d) || (part == 2 && k < d)) continue;
     PhaseScope ps(s, k == d ? PH_INTERIOR : (k == 1 ? PH_EDGE : PH_FACE));
+    if (k < d && s->ov_w) {
+      launch_over_forward(g, s->ov[k].L, s->T, s->Pw, s->status, st);
+      s->launches += s->ov[k].L.n_ents ? 1 : 0;
+      continue;
+    }
     if (k == d && s->mixed_top)
       launch_mixed_forward(g, s->launch[k], s->T, s->Pw, s->fac32, s->status, st);
     else if (!(part == 2 && k == d))
@@ -1424,6 +1515,16 @@ int run_jtvec(msfv_session* s, const double* w, double* out, bool fixed_basis = 
   for (int k = d; k >= 1 && !fixed_basis; --k) {
     if (part == 2 && k == d) continue;
     PhaseScope ps(s, k == d ? PH_ADJ_INTERIOR : (k == 1 ? PH_ADJ_EDGE : PH_ADJ_FACE));
+    if (k < d && s->ov_w) {
+      // oversampled boxes: private contributions, then the gathers (face gradient, and
+      // the faces' seeds of the edges)
+      const OvHost& H = s->ov[k];
+      launch_over_adjoint(g, H.L, s->T, s->Pw, s->Lam, s->ZT, s->X, st);
+      launch_over_gather(H.G, H.L.prv, s->gT, 1, st);
+      if (H.S.nrows) launch_over_gather(H.S, H.L.sprv, s->ov[1].L.seed, 0, st);
+      s->launches += (H.L.n_ents ? 1 : 0) + (H.G.nrows ? 1 : 0) + (H.S.nrows ? 1 : 0);
+      continue;
+    }
     if (k == d && s->mixed_top)
       launch_mixed_adjoint(g, s->launch[k], s->T, s->Pw, s->fac32, s->Lam, s->rec_p, s->rec_u,
                            s->ZT, s->X, s->gT, st);
@@ -1459,6 +1560,11 @@ int run_jvec(msfv_session* s, const double* v, double* jv) {
   PhaseScope ps(s, PH_TANGENT);
   cudaMemsetAsync(s->X, 0, sizeof(double) * (size_t)g.N * g.S, st);
   for (int k = 1; k <= d; ++k) {
+    if (k < d && s->ov_w) {
+      launch_over_tangent(g, s->ov[k].L, s->T, Dl, v, s->Pw, s->X, st);
+      s->launches += s->ov[k].L.n_ents ? 1 : 0;
+      continue;
+    }
     if (k == d && s->mixed_top)
       launch_mixed_tangent(g, s->launch[k], s->T, s->T, Dl, v, s->Pw, s->fac32, s->X, st);
     else

@@ -49,7 +49,8 @@ class _Desc(ctypes.Structure):
                 ("src_amp", ctypes.POINTER(ctypes.c_double)),
                 ("n_rec", ctypes.c_int), ("rec_cell", ctypes.POINTER(ctypes.c_int64)),
                 ("factor_mode", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
-                ("source_bases", ctypes.c_int), ("discretization", ctypes.c_int)]
+                ("source_bases", ctypes.c_int), ("discretization", ctypes.c_int),
+                ("oversample", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -185,6 +186,7 @@ class Session:
         d.factor_mode = int(factor_mode)
         d.hbm_budget_bytes = int(hbm_budget_bytes)
         d.source_bases = 1 if getattr(prob, "source_bases", False) else 0
+        d.oversample = int(getattr(prob, "oversample", 0))
         d.discretization = 1 if getattr(prob, "nodal", False) else 0
         h = ctypes.c_void_p()
         self._h = None

@@ -1,0 +1,133 @@
+"""GPU path with oversampled dual edge and face problems against the CPU oracle.
+
+Oversampling is named in Sec. 6 as a way to lessen the effect of the local boundary
+conditions on the basis; the library and the oracle implement the same reading (a dual
+edge or face solved on its box widened by w cells along its normal axes, only its own
+cells kept).  Bar: 1e-9 relative error in the 2-norm and the max-norm on predicted
+data, fields u, misfit, gradient, J v and J^T w.  Cases: 2D and 3D, several dual cells
+per axis with partial dual cells at the boundary, widths from 1 to c - 1 (boxes that
+reach the neighbouring vertex planes' cells and boxes clipped by the mesh), c = 4, 8
+and 16, and a 64^3 case with c = 8.  Also: the gradient is bitwise repeatable (the
+overlapping boxes' contributions are gathered in a fixed order), a batch graph with
+oversampled instances gives the plain path's bits, and invalid widths are rejected."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.msfv_oracle import Oracle  # noqa: E402
+from paper_1707_07598_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-9
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    r2 = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    rinf = np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300) if b.size else 0.0
+    return max(r2, rinf)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1707_07598_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+CASES = [
+    ((48, 40), 8, 1, 3, 20),
+    ((48, 40), 8, 3, 2, 20),
+    ((40, 24), 8, 7, 2, 16),
+    ((20, 15), 5, 2, 2, 8),
+    ((12, 8, 8), 4, 1, 2, 9),
+    ((24, 16, 16), 8, 2, 3, 24),
+    ((24, 24, 16), 8, 7, 2, 20),
+    ((16, 16, 12), 4, 3, 2, 12),
+    ((32, 32, 32), 16, 3, 2, 24),
+]
+
+
+@pytest.mark.parametrize("n,c,w,ns,nr", CASES)
+def test_oversampled_forward_gradient_jvec_jtvec_match_oracle(dev, n, c, w, ns, nr):
+    from paper_1707_07598_gb300.msfv import Session
+    prob = W.make_problem(n, c, ns, nr, seed=31, top_layer=len(n) == 3, oversample=w)
+    m = 1.5 * W.gaussian_random_field(n, 0.15, 32)
+    orc = Oracle(prob)
+    st = orc.forward(m)
+    d_obs = st['d'] * 1.02 + W.noise_like(st['d'].shape, 1e-3 * np.abs(st['d']).max(), 33)
+    phi_ref, g_ref = orc.misfit_gradient(st, d_obs)
+    s = Session(prob)
+    u = torch.empty((prob.n_src, prob.N), dtype=torch.float64, device=dev)
+    d = s.forward(torch.from_numpy(m).to(dev), u=u)
+    phi, g = s.adjoint(torch.from_numpy(d_obs).to(dev))
+    assert rel(d.cpu().numpy(), st['d']) < TOL
+    assert rel(u.cpu().numpy(), st['U']) < TOL
+    assert abs(phi - phi_ref) <= TOL * abs(phi_ref)
+    assert rel(g.cpu().numpy(), g_ref) < TOL
+    v = W.noise_like(prob.N, 1.0, 34)
+    wt = W.noise_like((prob.n_src, prob.n_rec), 1.0, 35)
+    jv = s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy()
+    jtw = s.jtvec(torch.from_numpy(wt).to(dev)).cpu().numpy()
+    assert rel(jv, orc.jvec(st, v)) < TOL
+    assert rel(jtw, orc.jtvec(st, wt)) < TOL
+    s.close()
+
+
+def test_oversampled_64cube_matches_oracle(dev):
+    from paper_1707_07598_gb300.msfv import Session
+    n, c, w = (64, 64, 64), 8, 2
+    prob = W.make_problem(n, c, 4, 64, seed=41, top_layer=True, oversample=w)
+    m = W.gaussian_random_field(n, 0.1, 42)
+    orc = Oracle(prob)
+    st = orc.forward(m)
+    d_obs = st['d'] * 1.01
+    phi_ref, g_ref = orc.misfit_gradient(st, d_obs)
+    s = Session(prob)
+    d = s.forward(torch.from_numpy(m).to(dev))
+    phi, g = s.adjoint(torch.from_numpy(d_obs).to(dev))
+    assert rel(d.cpu().numpy(), st['d']) < TOL
+    assert abs(phi - phi_ref) <= TOL * abs(phi_ref)
+    assert rel(g.cpu().numpy(), g_ref) < TOL
+    # the contributions of overlapping boxes are summed in a fixed order: same bits
+    _, g2 = s.adjoint(torch.from_numpy(d_obs).to(dev))
+    assert torch.equal(g, g2)
+    s.close()
+
+
+def test_oversampled_instances_in_a_batch_graph_match_the_plain_path(dev):
+    from paper_1707_07598_gb300.msfv import Batch, Session
+    probs = [W.make_problem((32, 32, 32), 8, 3, 24, seed=51, top_layer=True, oversample=2),
+             W.make_problem((48, 40), 8, 2, 16, seed=52, top_layer=False, oversample=3),
+             W.make_problem((32, 32, 32), 8, 3, 24, seed=53, top_layer=True)]
+    ms = [torch.from_numpy(W.gaussian_random_field(p.n, 0.15, 60 + k)).to(dev)
+          for k, p in enumerate(probs)]
+    dobs = [torch.from_numpy(W.noise_like((p.n_src, p.n_rec), 1e-3, 70 + k)).to(dev)
+            for k, p in enumerate(probs)]
+    sessions = [Session(p, stream=torch.cuda.Stream(dev)) for p in probs]
+    torch.cuda.synchronize()
+    b = Batch(sessions, ms, dobs)
+    b.run()
+    b.check()
+    for s in sessions:
+        s.set_stream(torch.cuda.current_stream(dev))
+    for k, s in enumerate(sessions):
+        d = s.forward(ms[k])
+        _, g = s.adjoint(dobs[k], want_phi=False)
+        assert torch.equal(d, b.d_pred[k]) and torch.equal(g, b.grad[k]), k
+    b.close()
+    for s in sessions:
+        s.close()
+
+
+def test_invalid_oversampling_is_rejected(dev):
+    from paper_1707_07598_gb300.msfv import MSFVError, Session
+    for kw in (dict(oversample=8), dict(oversample=-1),
+               dict(oversample=1, source_bases=True), dict(oversample=1, nodal=True)):
+        prob = W.make_problem((16, 16), 8, 1, 4, seed=1, top_layer=False, **kw)
+        with pytest.raises(MSFVError):
+            Session(prob)
