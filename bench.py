@@ -14,7 +14,7 @@ two, oracle parity on one instance, the end-to-end rate through host buffers, th
 128^3 single-instance line with its roofline, and the CPU oracle on a sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload batched|plain|served|diff|gn|sources|nodal]
+                  [--workload batched|plain|served|diff|gn|sources|nodal|oversample]
 
 Under torchrun (N > 1) every rank runs an independent replica (the path has no
 exchange step); value = solves of all ranks / max-over-ranks time.
@@ -76,7 +76,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--workload", default="batched",
-                   choices=["batched", "plain", "served", "diff", "gn", "sources", "nodal"],
+                   choices=["batched", "plain", "served", "diff", "gn", "sources", "nodal",
+                            "oversample"],
                    help="batched: 64 uneven instances in one CUDA graph per step vs one at a "
                         "time (default); plain: the one-instance 128^3 step; served: the "
                         "Poisson request stream; diff: 256^3, c=16 gradient, J v, J^T w; gn: "
@@ -95,6 +96,9 @@ def parse():
     p.add_argument("--duration", type=float, default=10.0,
                    help="served: seconds of the arrival stream that are replayed")
     p.add_argument("--fd-dirs", type=int, default=20, help="diff: finite-difference directions")
+    p.add_argument("--oversample", type=int, default=2,
+                   help="oversampling width of the dual edge and face problems "
+                        "(--workload oversample)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                    help="local problems of the top dimension: FP64 factor (default) or FP32 "
                         "factor with two FP64 refinement steps")
@@ -1056,6 +1060,93 @@ def run_sources(args):
     return 0
 
 
+def run_oversample(args):
+    """The default workload (128^3, c = 8, 16 dipoles, 512 receivers) with oversampled dual
+    edge and face problems (width --oversample; Sec. 6 names oversampling, the
+    construction is the library's reading): one forward + gradient per step, timed like
+    the default line, beside the same steps without oversampling on the same inputs.  The
+    roofline is that of the face boxes' basis kernel (k_over_fwd), FP64 flops over the
+    phase timer of its launch."""
+    torch, dev = _gpu_setup()
+    from paper_1707_07598_gb300.msfv import Session
+    n = args.n
+    prob, m_np = W.config_3d_128(n=n)
+    stream = torch.cuda.current_stream(dev)
+    m = torch.from_numpy(m_np).to(dev)
+    m_true = torch.from_numpy(W.config_3d_128(seed=3, n=n)[1]).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for w in (0, args.oversample):
+        prob.oversample = w
+        sess = Session(prob, stream=stream)
+        d_true = sess.forward(m_true).clone()
+        noise = torch.from_numpy(W.noise_like(tuple(d_true.shape), 1.0, 4)).to(dev)
+        d_obs = d_true + 0.01 * d_true.abs() * noise
+        grad = torch.empty(prob.N, dtype=torch.float64, device=dev)
+        d_pred = torch.empty((prob.n_src, prob.n_rec), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            sess.forward(m, d_pred)
+            sess.adjoint(d_obs, grad, want_phi=False)
+        torch.cuda.synchronize(dev)
+        sess.profile(True)
+        sess.phase_times(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.3)
+        l0 = sess.launch_count()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            sess.forward(m, d_pred)
+            sess.adjoint(d_obs, grad, want_phi=False)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        launches = sess.launch_count() - l0
+        clk = clocks.stop()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        ph = sess.phase_times(reset=True)
+        info = sess.info()
+        res[w] = {"ms": sum(ms) / len(ms), "p50": float(np.percentile(ms, 50)),
+                  "p99": float(np.percentile(ms, 99)), "launches": launches, "clocks": clk,
+                  "phases": {k: v[0] / args.steps for k, v in ph.items() if v[1]},
+                  "phase_calls": {k: v[1] for k, v in ph.items() if v[1]},
+                  "info": info, "d": d_pred.clone(), "g": grad.clone()}
+        sess.close()
+    r1, r0 = res[args.oversample], res[0]
+    info = r1["info"]
+    face_ms = r1["phases"].get("basis_faces", 0.0)
+    face_calls = max(1, r1["phase_calls"].get("basis_faces", 1) // max(args.steps, 1))
+    launch_s = face_ms / face_calls / 1000.0
+    flops = float(info["oversampled_face_flops"])
+    achieved = flops / launch_s / 1e12 if launch_s > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "k_over_fwd (oversampled dual-face boxes)",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_SOURCE,
+            "flops_per_launch": flops, "avg_launch_ms": launch_s * 1000.0, "traffic": None}
+    dd = (r1["d"] - r0["d"]).norm().item() / max(r0["d"].norm().item(), 1e-300)
+    out = {"metric": METRIC, "value": 1000.0 / r1["ms"], "unit": "solves/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r1["ms"],
+           "p50_ms": r1["p50"], "p99_ms": r1["p99"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"3d_{n}^3_c8_16dipoles_512rec_fwd+grad_oversample{args.oversample}",
+                      "oversample": args.oversample,
+                      "l2": "flushed before every timed step (512 MiB write)",
+                      "factor_mode": "store"},
+           "roofline": roof, "gpu_launches": r1["launches"], "clocks": r1["clocks"],
+           "oversampled_boxes": info["oversampled_boxes"],
+           "oversampled_face_kernel": {"smem_bytes": info["oversampled_smem_bytes"],
+                                       "grid": info["oversampled_grid"]},
+           "plain": {"value": 1000.0 / r0["ms"], "ms_per_step": r0["ms"]},
+           "overhead": r1["ms"] / r0["ms"] - 1.0,
+           "data_change_vs_plain": dd,
+           "phases_ms_per_step": r1["phases"],
+           "plain_phases_ms_per_step": r0["phases"]}
+    print(json.dumps(out))
+    return 0
+
+
 def run_nodal(args):
     """The paper's own variant (nodal operator, Lagrange block data, Galerkin A_k) on the
     default survey shape: 128^3 cells (129^3 nodes), c = 8, 16 dipoles and 512
@@ -1126,7 +1217,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     runners = {"batched": run_batched, "plain": run_plain, "served": run_served,
-               "diff": run_diff, "gn": run_gn, "sources": run_sources, "nodal": run_nodal}
+               "diff": run_diff, "gn": run_gn, "sources": run_sources, "nodal": run_nodal,
+               "oversample": run_oversample}
     return runners[args.workload](args)
 
 

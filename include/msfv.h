@@ -366,7 +366,12 @@ int msfv_set_wait_limit(msfv_session_t* s, int64_t ns);
  * recomputed (0 stored), out[12]=bit k set when the k-dimensional local problems are
  * factored in global memory, out[13]=number of source-basis slots ((entity, source)
  * pairs; 0 without source bases), out[14]=their values (doubles per copy of C, mu and
- * dC).  n_out may be smaller than 15.
+ * dC), out[15]=oversampling width w, out[16]=number of oversampled boxes (edges and
+ * faces; 0 when w = 0), out[17] / out[18]=FP64 flops of one forward launch over the
+ * oversampled edge / face boxes (factors and solves), out[19]=dynamic shared memory
+ * (bytes) per box of the highest oversampled level's kernels (faces in 3D, edges in 2D;
+ * 0 when its boxes run in global memory), out[20]=the persistent grid (CTAs) of its basis
+ * kernel.  n_out may be smaller than 21.
  * The environment variable MSFV_LOCAL_WINDOW=global at msfv_setup forces the global-
  * memory factorisation for every class (for testing). */
 int msfv_info(const msfv_session_t* s, int64_t* out, int n_out);

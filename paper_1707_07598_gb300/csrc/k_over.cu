@@ -30,6 +30,7 @@
 // fixed order (deterministic, no atomics).
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -42,6 +43,7 @@ namespace {
 
 constexpr int OV_NT = 128;     // threads per box
 constexpr int OV_MAXB = 512;   // largest half bandwidth (shared column buffer)
+constexpr int OV_LOOK = 4;     // columns the shared-memory factorisation loads ahead
 
 __host__ __device__ __forceinline__ void box_coords(const OvDesc& e, int p, int* xc) {
   for (int a = 0; a < 3; ++a) xc[a] = e.org[a] + (e.str[a] ? (p / e.str[a]) % e.len[a] : 0);
@@ -117,6 +119,8 @@ __device__ bool ov_ok(const char* who, int eid, const OvDesc& e, const DevGeom& 
 }
 #endif
 
+// ---- the global-memory variant (boxes whose working set exceeds shared memory) ----------
+
 // In-place banded LDL^T of F (n columns, half bandwidth b), all threads of the CTA;
 // status[0] = 1 on a non-positive pivot.  Ends with a block barrier.
 __device__ void band_factor(double* F, int n, int b, double* col, int* status) {
@@ -172,11 +176,172 @@ __device__ __forceinline__ void box_solve(const OvDesc& e, const double* F, doub
   __syncthreads();
 }
 
+// ---- the shared-memory variant -----------------------------------------------------------
+
+__device__ __forceinline__ void ov_cp8(double* dst, const double* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void ov_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void ov_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One box in shared memory: a ring of RB = b + 1 + OV_LOOK band columns (b + 1 doubles
+// each; also the staging buffer of the solves), the current column, and the right-hand
+// sides (nvs x n, right-hand side major).
+struct OvSm {
+  double* ring;
+  double* col;
+  double* x;
+  int RB;
+};
+// doubles of the shared-memory working set of a box (the layout of ov_carve)
+__host__ __device__ __forceinline__ long long ov_smem_doubles(int n, int b, int nvs) {
+  const long long B1 = b + 1, RB = b + 1 + OV_LOOK;
+  return RB * B1 + ((B1 + 1) & ~1LL) + (long long)n * nvs;
+}
+__device__ __forceinline__ OvSm ov_carve(double* base, const OvDesc& e) {
+  OvSm s;
+  const long long B1 = e.b + 1;
+  s.RB = e.b + 1 + OV_LOOK;
+  s.ring = base;
+  s.col = base + (long long)s.RB * B1;
+  s.x = s.col + ((B1 + 1) & ~1LL);
+  return s;
+}
+
+// Banded LDL^T with the active columns in a shared-memory ring: column c sits in slot
+// c % RB from its load (OV_LOOK + 1 steps before its first update, by cp.async) until it
+// is final and written to F (global) in place of the assembled column.  F holds the
+// assembled band on entry; status[0] = 1 on a non-positive pivot.  Ends with a block
+// barrier and no copy in flight.
+__device__ void ring_factor(double* F, const OvDesc& e, const OvSm& sm, int* status) {
+  const int tid = threadIdx.x, n = e.n, b = e.b, RB = sm.RB;
+  const long long B1 = b + 1;
+  for (long long q = tid; q < (long long)min(n, RB) * B1; q += OV_NT) sm.ring[q] = F[q];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const int kb = min(b, n - 1 - j);
+    double* slot = sm.ring + (long long)(j % RB) * B1;
+    for (int k = tid; k <= kb; k += OV_NT) sm.col[k] = slot[k];
+    __syncthreads();
+    // the slot is free: bring in column j + RB
+    const int c = j + RB;
+    if (c < n)
+      for (int k = tid; k < (int)B1; k += OV_NT) ov_cp8(slot + k, F + (long long)c * B1 + k);
+    ov_commit();
+    const double dj = sm.col[0];
+    if (tid == 0 && !(dj > 0.0)) status[0] = 1;
+    const double rd = 1.0 / dj;
+    // rank-1 update of the trailing triangle: warp w takes the columns k2 = 1 + w, 5 + w,
+    // ...; its lanes run down the rows k1 >= k2 of that column (consecutive addresses)
+    {
+      const int wid = tid >> 5, lane = tid & 31, s0 = j % RB;
+      for (int k2 = 1 + wid; k2 <= kb; k2 += OV_NT / 32) {
+        int sl = s0 + k2;
+        if (sl >= RB) sl -= RB;
+        double* cp = sm.ring + (long long)sl * B1 - k2;   // entry (j + k1, j + k2) at cp[k1]
+        const double l2 = sm.col[k2] * rd;
+        for (int k1 = k2 + lane; k1 <= kb; k1 += 32) cp[k1] = fma(-l2, sm.col[k1], cp[k1]);
+      }
+    }
+    double* Fj = F + (long long)j * B1;
+    for (int k = tid; k <= kb; k += OV_NT) Fj[k] = k ? sm.col[k] * rd : dj;
+    // the column the next step's update reaches furthest was requested OV_LOOK + 1
+    // steps ago
+    ov_wait<OV_LOOK>();
+    __syncthreads();
+  }
+  ov_wait<0>();
+  __syncthreads();
+}
+
+// L D L^T x = x for the nvs right-hand sides in shared memory, the factor read from F
+// (global) in chunks of C columns staged through the two halves of the ring (every
+// thread copies, one warp per right-hand side solves).  Ends with a block barrier.
+__device__ void staged_solve(const double* F, const OvDesc& e, const OvSm& sm) {
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int n = e.n, b = e.b;
+  const long long B1 = b + 1;
+  const int C = max(1, sm.RB / 2);
+  const int nch = (n + C - 1) / C;
+  // chunk m of a sweep: columns [j0, j1), ascending (down = false) or descending
+  auto bounds = [&](int m, bool down, int* j0, int* j1) {
+    if (!down) {
+      *j0 = m * C;
+      *j1 = min(n, *j0 + C);
+    } else {
+      *j1 = n - m * C;
+      *j0 = max(0, *j1 - C);
+    }
+  };
+  auto load = [&](int m, bool down) {
+    int j0, j1;
+    bounds(m, down, &j0, &j1);
+    double* dst = sm.ring + (long long)(m & 1) * C * B1;
+    const double* src = F + (long long)j0 * B1;
+    for (long long q = tid; q < (long long)(j1 - j0) * B1; q += OV_NT) ov_cp8(dst + q, src + q);
+    ov_commit();
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool down = pass == 1;
+    load(0, down);
+    for (int m = 0; m < nch; ++m) {
+      if (m + 1 < nch) {
+        load(m + 1, down);
+        ov_wait<1>();
+      } else {
+        ov_wait<0>();
+      }
+      __syncthreads();
+      int j0, j1;
+      bounds(m, down, &j0, &j1);
+      const double* Fs = sm.ring + (long long)(m & 1) * C * B1;
+      if (wid < e.nvs) {
+        double* x = sm.x + (long long)wid * n;
+        if (!down) {
+          for (int j = j0; j < j1; ++j) {
+            const double xj = x[j];
+            const int kb = min(b, n - 1 - j);
+            const double* Fj = Fs + (long long)(j - j0) * B1;
+            for (int k = 1 + lane; k <= kb; k += 32) x[j + k] = fma(-Fj[k], xj, x[j + k]);
+            __syncwarp();
+          }
+        } else {
+          for (int j = j1 - 1; j >= j0; --j) {
+            const int kb = min(b, n - 1 - j);
+            const double* Fj = Fs + (long long)(j - j0) * B1;
+            double acc = 0.0;
+            for (int k = 1 + lane; k <= kb; k += 32) acc = fma(Fj[k], x[j + k], acc);
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) x[j] -= acc;
+            __syncwarp();
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!down) {
+      for (int q = tid; q < n * e.nvs; q += OV_NT)
+        sm.x[q] = sm.x[q] / F[(long long)(q % n) * B1];
+      __syncthreads();
+    }
+  }
+}
+
 // ---- basis ------------------------------------------------------------------------------
+// SM: the shared-memory variant (ring factorisation, staged solves, right-hand sides in
+// shared memory); else everything in global memory.
+template <bool SM>
 __global__ void __launch_bounds__(OV_NT) k_over_fwd(DevGeom g, OvLaunch L,
                                                     const double* __restrict__ T,
                                                     double* __restrict__ Pw, int* status) {
-  __shared__ double col[OV_MAXB + 1];
+  extern __shared__ double ov_dyn[];
+  __shared__ double colg[SM ? 2 : OV_MAXB + 1];
   const int nslot = 1 << g.d, tid = threadIdx.x;
   for (int eid = blockIdx.x; eid < L.n_ents; eid += gridDim.x) {
     const OvDesc e = L.ents[eid];
@@ -185,7 +350,14 @@ __global__ void __launch_bounds__(OV_NT) k_over_fwd(DevGeom g, OvLaunch L,
 #endif
     const long long B1 = e.b + 1;
     double* F = L.fac + e.fac;
-    double* x = L.sol + e.sol;
+    OvSm sm{};
+    double* x;
+    if constexpr (SM) {
+      sm = ov_carve(ov_dyn, e);
+      x = sm.x;
+    } else {
+      x = L.sol + e.sol;
+    }
     for (long long q = tid; q < (long long)e.n * B1; q += OV_NT) F[q] = 0.0;
     __syncthreads();
     // box operator (every face inside the box and every Dirichlet coupling on the
@@ -195,7 +367,8 @@ __global__ void __launch_bounds__(OV_NT) k_over_fwd(DevGeom g, OvLaunch L,
       box_coords(e, p, xc);
       const long long xg = cell_of(g, xc);
       double dg = 0.0;
-      for (int a = 0; a < g.d; ++a)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) if (a < g.d)
         for (int dir = -1; dir <= 1; dir += 2) {
           const int kind = face_kind(g, e, xc, a, dir);
           if (!kind) continue;
@@ -207,7 +380,8 @@ __global__ void __launch_bounds__(OV_NT) k_over_fwd(DevGeom g, OvLaunch L,
       for (int i = 0; i < e.nvs; ++i) {
         const int s = nth_slot_of(e.slots, i);
         double r = 0.0;
-        for (int a = 0; a < g.d; ++a)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (a < g.d)
           for (int dir = -1; dir <= 1; dir += 2) {
             if (face_kind(g, e, xc, a, dir) != 2) continue;
             const int sp = map_slot(s, a, dir);
@@ -221,8 +395,14 @@ __global__ void __launch_bounds__(OV_NT) k_over_fwd(DevGeom g, OvLaunch L,
       }
     }
     __syncthreads();
-    band_factor(F, e.n, e.b, col, status);
-    box_solve(e, F, x);
+    if constexpr (SM) {
+      ring_factor(F, e, sm, status);
+      staged_solve(F, e, sm);
+      for (int q = tid; q < e.n * e.nvs; q += OV_NT) L.sol[e.sol + q] = x[q];
+    } else {
+      band_factor(F, e.n, e.b, colg, status);
+      box_solve(e, F, x);
+    }
     for (int p = tid; p < e.n; p += OV_NT) {
       int xc[3];
       box_coords(e, p, xc);
@@ -237,12 +417,14 @@ __global__ void __launch_bounds__(OV_NT) k_over_fwd(DevGeom g, OvLaunch L,
 }
 
 // ---- adjoint ----------------------------------------------------------------------------
+template <bool SM>
 __global__ void __launch_bounds__(OV_NT) k_over_adj(DevGeom g, OvLaunch L,
                                                     const double* __restrict__ T,
                                                     const double* __restrict__ Pw,
                                                     const double* __restrict__ Lam,
                                                     const double* __restrict__ ZT,
                                                     const double* __restrict__ MU) {
+  extern __shared__ double ov_dyn[];
   const int nslot = 1 << g.d, tid = threadIdx.x;
   const int S3 = (g.d == 3) ? 27 : 9;
   for (int eid = blockIdx.x; eid < L.n_ents; eid += gridDim.x) {
@@ -253,7 +435,14 @@ __global__ void __launch_bounds__(OV_NT) k_over_adj(DevGeom g, OvLaunch L,
 #endif
     const double* F = L.fac + e.fac;
     const double* phi = L.sol + e.sol;
-    double* mu = L.wrk + e.wrk;
+    OvSm sm{};
+    double* mu;
+    if constexpr (SM) {
+      sm = ov_carve(ov_dyn, e);
+      mu = sm.x;
+    } else {
+      mu = L.wrk + e.wrk;
+    }
     // seeds on the kept cells: -(A Lambda_v)(x) through the coarse-stencil collapse, the
     // receivers inside, the mu of the interiors next to them and the seeds the upper
     // level passed; zero on the other box cells
@@ -267,7 +456,8 @@ __global__ void __launch_bounds__(OV_NT) k_over_adj(DevGeom g, OvLaunch L,
         const long long xg = cell_of(g, xc);
         int v[3] = {0, 0, 0}, K[3] = {0, 0, 0};
         long long vid = 0;
-        for (int a = 0; a < g.d; ++a) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (a < g.d) {
           const int t0 = xc[a] - g.half;
           v[a] = (t0 >= 0 ? t0 / g.c : -((-t0 + g.c - 1) / g.c)) + ((s >> a) & 1);
           K[a] = xc[a] / g.c;
@@ -275,9 +465,11 @@ __global__ void __launch_bounds__(OV_NT) k_over_adj(DevGeom g, OvLaunch L,
         }
         const double* Lv = Lam + vid * S3;
         int ox = 0;
-        for (int a = 0; a < g.d; ++a) ox += (K[a] - v[a] + 1) * (a == 0 ? 1 : (a == 1 ? 3 : 9));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (a < g.d) ox += (K[a] - v[a] + 1) * (a == 0 ? 1 : (a == 1 ? 3 : 9));
         const double lx = Lv[ox];
-        for (int a = 0; a < g.d; ++a) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) if (a < g.d) {
           const int mul = (a == 0) ? 1 : (a == 1 ? 3 : 9);
           if (xc[a] + 1 < g.n[a] && (xc[a] + 1) / g.c != K[a])
             w -= tface(T, g, a, xg) * (lx - Lv[ox + mul]);
@@ -287,7 +479,8 @@ __global__ void __launch_bounds__(OV_NT) k_over_adj(DevGeom g, OvLaunch L,
         for (int r = 0; r < e.rec_cnt; ++r)
           if (L.rec_p[e.rec_off + r] == p) w += ZT[(long long)L.rec_u[e.rec_off + r] * nslot + s];
         if (L.pull_mu)
-          for (int a = 0; a < g.d; ++a) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) if (a < g.d) {
             if (e.ctr[a] < 0) continue;
             if (xc[a] + 1 < g.n[a]) w += tface(T, g, a, xg) * MU[(xg + g.st[a]) * nslot + s];
             if (xc[a] > 0)
@@ -298,14 +491,18 @@ __global__ void __launch_bounds__(OV_NT) k_over_adj(DevGeom g, OvLaunch L,
       mu[(long long)i * e.n + p] = w;
     }
     __syncthreads();
-    box_solve(e, F, mu);
+    if constexpr (SM)
+      staged_solve(F, e, sm);
+    else
+      box_solve(e, F, mu);
     // private contributions: the gradient of every box face, and the seeds of the
     // projected lower-level cells
     for (int p = tid; p < e.n; p += OV_NT) {
       int xc[3];
       box_coords(e, p, xc);
       const long long xg = cell_of(g, xc);
-      for (int a = 0; a < g.d; ++a)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) if (a < g.d)
         for (int dir = -1; dir <= 1; dir += 2) {
           const int kind = face_kind(g, e, xc, a, dir);
           if (!kind || (kind == 1 && dir < 0)) continue;
@@ -338,12 +535,14 @@ __global__ void __launch_bounds__(OV_NT) k_over_adj(DevGeom g, OvLaunch L,
 }
 
 // ---- tangent ----------------------------------------------------------------------------
+template <bool SM>
 __global__ void __launch_bounds__(OV_NT) k_over_tan(DevGeom g, OvLaunch L,
                                                     const double* __restrict__ T,
                                                     const double* __restrict__ Dl,
                                                     const double* __restrict__ v,
                                                     const double* __restrict__ Pw,
                                                     double* __restrict__ dPw) {
+  extern __shared__ double ov_dyn[];
   const int nslot = 1 << g.d, tid = threadIdx.x;
   for (int eid = blockIdx.x; eid < L.n_ents; eid += gridDim.x) {
     const OvDesc e = L.ents[eid];
@@ -362,7 +561,14 @@ __global__ void __launch_bounds__(OV_NT) k_over_tan(DevGeom g, OvLaunch L,
     }
     const double* F = L.fac + e.fac;
     const double* phi = L.sol + e.sol;
-    double* x = L.wrk + e.wrk;
+    OvSm sm{};
+    double* x;
+    if constexpr (SM) {
+      sm = ov_carve(ov_dyn, e);
+      x = sm.x;
+    } else {
+      x = L.wrk + e.wrk;
+    }
     for (int it = tid; it < e.n * e.nvs; it += OV_NT) {
       const int i = it / e.n, p = it - (it / e.n) * e.n;
       const int s = nth_slot_of(e.slots, i);
@@ -372,7 +578,8 @@ __global__ void __launch_bounds__(OV_NT) k_over_tan(DevGeom g, OvLaunch L,
       const long long o = (long long)i * e.n;
       const double px = phi[o + p];
       double r = 0.0;
-      for (int a = 0; a < g.d; ++a)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) if (a < g.d)
         for (int dir = -1; dir <= 1; dir += 2) {
           const int kind = face_kind(g, e, xc, a, dir);
           if (!kind) continue;
@@ -396,7 +603,10 @@ __global__ void __launch_bounds__(OV_NT) k_over_tan(DevGeom g, OvLaunch L,
       x[o + p] = r;
     }
     __syncthreads();
-    box_solve(e, F, x);
+    if constexpr (SM)
+      staged_solve(F, e, sm);
+    else
+      box_solve(e, F, x);
     for (int p = tid; p < e.n; p += OV_NT) {
       int xc[3];
       box_coords(e, p, xc);
@@ -421,8 +631,6 @@ __global__ void k_over_gather(OvGather G, const double* __restrict__ src, double
     out[q] = accumulate ? out[q] + acc : acc;
   }
 }
-
-int ov_grid(int n) { return std::max(1, std::min(n, 152 * 12)); }
 
 // pairs (target, source) sorted by target, then source: rows of a gather
 void build_rows(std::vector<std::pair<long long, long long>>& pr, std::vector<long long>& ptr,
@@ -514,6 +722,12 @@ std::string over_plan(const DevGeom& g, const std::vector<EntDesc>& ents,
       H.h_rec_u.push_back(rec_u[r]);
     }
     e.rec_cnt = (int)H.h_rec_p.size() - e.rec_off;
+    // flops of its forward: per column the rank-kb update (kb (kb + 1) / 2 FMAs), the kb
+    // scalings and, per right-hand side, 2 kb FMAs of the two sweeps and one division
+    for (int j = 0; j < e.n; ++j) {
+      const double kb = std::min(e.b, e.n - 1 - j);
+      H.flops += kb * (kb + 1.0) + kb + e.nvs * (4.0 * kb + 1.0);
+    }
     H.h_ents.push_back(e);
   }
   H.n_fac = fac;
@@ -593,22 +807,101 @@ std::string over_plan(const DevGeom& g, const std::vector<EntDesc>& ents,
   return "";
 }
 
+namespace {
+// Persistent grid: the resident CTAs per SM (the larger of the occupancy query and an
+// estimate from the kernel's registers and shared memory and the SM's limits) times the
+// SMs, at most one CTA per box.  CTAs beyond what is resident only wait their turn.
+template <class K>
+int ov_grid(K kern, long long smem, int n_ents, int dev, int nsm) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, OV_NT, (size_t)smem) != cudaSuccess) {
+    cudaGetLastError();
+    nb = 0;
+  }
+  cudaFuncAttributes fa{};
+  int regs_sm = 0, smem_sm = 0, thr_sm = 0, blk_sm = 0;
+  if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess &&
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) == cudaSuccess) {
+    const long long regs_cta = (long long)((fa.numRegs * 32 + 255) / 256 * 256) * (OV_NT / 32);
+    const long long smem_cta = (long long)fa.sharedSizeBytes + smem + 1024;
+    long long est = std::min<long long>(thr_sm / OV_NT, blk_sm);
+    if (regs_cta > 0) est = std::min<long long>(est, regs_sm / regs_cta);
+    est = std::min<long long>(est, smem_sm / smem_cta);
+    nb = std::max<int>(nb, (int)est);
+  } else {
+    cudaGetLastError();
+  }
+  return std::max(1, std::min(n_ents, std::max(1, nb) * nsm));
+}
+template <class K>
+cudaError_t ov_allow_smem(K kern, long long bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+}  // namespace
+
+cudaError_t over_configure(OvHost& H, bool force_global) {
+  static std::mutex mu;
+  static long long allowed = 0;   // dynamic shared memory the kernels are set up for
+  OvLaunch& L = H.L;
+  long long need = 0;
+  for (const OvDesc& e : H.h_ents)
+    need = std::max(need, ov_smem_doubles(e.n, e.b, e.nvs) * (long long)sizeof(double));
+  int dev = 0, maxopt = 0, nsm = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess)
+    err = cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (err != cudaSuccess) return err;
+  const bool use_sm = !force_global && need > 0 && need + 1024 <= maxopt;
+  L.smem = use_sm ? need : 0;
+  if (use_sm) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (need > allowed) {
+      err = ov_allow_smem(k_over_fwd<true>, need);
+      if (err == cudaSuccess) err = ov_allow_smem(k_over_adj<true>, need);
+      if (err == cudaSuccess) err = ov_allow_smem(k_over_tan<true>, need);
+      if (err != cudaSuccess) return err;
+      allowed = need;
+    }
+    L.grid[0] = ov_grid(k_over_fwd<true>, L.smem, L.n_ents, dev, nsm);
+    L.grid[1] = ov_grid(k_over_adj<true>, L.smem, L.n_ents, dev, nsm);
+    L.grid[2] = ov_grid(k_over_tan<true>, L.smem, L.n_ents, dev, nsm);
+  } else {
+    L.grid[0] = ov_grid(k_over_fwd<false>, 0, L.n_ents, dev, nsm);
+    L.grid[1] = ov_grid(k_over_adj<false>, 0, L.n_ents, dev, nsm);
+    L.grid[2] = ov_grid(k_over_tan<false>, 0, L.n_ents, dev, nsm);
+  }
+  return cudaSuccess;
+}
+
 void launch_over_forward(const DevGeom& g, const OvLaunch& L, const double* T, double* Pw,
                          int* status, cudaStream_t s) {
   if (!L.n_ents) return;
-  k_over_fwd<<<ov_grid(L.n_ents), OV_NT, 0, s>>>(g, L, T, Pw, status);
+  if (L.smem)
+    k_over_fwd<true><<<L.grid[0], OV_NT, (size_t)L.smem, s>>>(g, L, T, Pw, status);
+  else
+    k_over_fwd<false><<<L.grid[0], OV_NT, 0, s>>>(g, L, T, Pw, status);
 }
 
 void launch_over_adjoint(const DevGeom& g, const OvLaunch& L, const double* T, const double* Pw,
                          const double* Lam, const double* ZT, const double* MU, cudaStream_t s) {
   if (!L.n_ents) return;
-  k_over_adj<<<ov_grid(L.n_ents), OV_NT, 0, s>>>(g, L, T, Pw, Lam, ZT, MU);
+  if (L.smem)
+    k_over_adj<true><<<L.grid[1], OV_NT, (size_t)L.smem, s>>>(g, L, T, Pw, Lam, ZT, MU);
+  else
+    k_over_adj<false><<<L.grid[1], OV_NT, 0, s>>>(g, L, T, Pw, Lam, ZT, MU);
 }
 
 void launch_over_tangent(const DevGeom& g, const OvLaunch& L, const double* T, const double* Dl,
                          const double* v, const double* Pw, double* dPw, cudaStream_t s) {
   if (!L.n_ents) return;
-  k_over_tan<<<ov_grid(L.n_ents), OV_NT, 0, s>>>(g, L, T, Dl, v, Pw, dPw);
+  if (L.smem)
+    k_over_tan<true><<<L.grid[2], OV_NT, (size_t)L.smem, s>>>(g, L, T, Dl, v, Pw, dPw);
+  else
+    k_over_tan<false><<<L.grid[2], OV_NT, 0, s>>>(g, L, T, Dl, v, Pw, dPw);
 }
 
 void launch_over_gather(const OvGather& G, const double* src, double* out, int accumulate,

@@ -466,6 +466,12 @@ struct OvLaunch {
   // sizes (doubles / entries) for the descriptor checks of a checked build
   long long n_fac = 0, n_sol = 0, n_prv = 0, n_sprv = 0, n_seed = 0, n_rec = 0;
   int n_ru = 0, pad_ = 0;
+  // launch shape (over_configure): dynamic shared memory per box of the shared-memory
+  // kernels (0: the global-memory kernels run) and the persistent grids of the basis,
+  // adjoint and tangent kernels
+  long long smem = 0;
+  int grid[3] = {1, 1, 1};
+  int pad2_ = 0;
 };
 // out[dst[r]] (+)= sum of src[idx[k]], k in [ptr[r], ptr[r+1]): contributions of
 // overlapping boxes summed in a fixed order
@@ -481,6 +487,7 @@ struct OvHost {
   std::vector<long long> g_ptr, g_idx, g_dst;   // face-gradient gather (rows: fine faces)
   std::vector<long long> s_ptr, s_idx, s_dst;   // seed gather into the lower level
   long long n_fac = 0, n_sol = 0, n_prv = 0, n_sprv = 0, n_seed = 0;
+  double flops = 0.0;   // FP64 flops of one forward launch (factors and solves)
   OvLaunch L;
   OvGather G, S;
 };
@@ -491,6 +498,9 @@ struct OvHost {
 std::string over_plan(const DevGeom& g, const std::vector<EntDesc>& ents,
                       const std::vector<int>& rec_p, const std::vector<int>& rec_u, int w,
                       int k, OvHost& H, OvHost* lower);
+// Launch shapes of a planned level on the current device: the shared-memory kernels when
+// every box's working set fits (unless force_global), else the global-memory ones.
+cudaError_t over_configure(OvHost& H, bool force_global);
 void launch_over_forward(const DevGeom& g, const OvLaunch& L, const double* T, double* Pw,
                          int* status, cudaStream_t s);
 void launch_over_adjoint(const DevGeom& g, const OvLaunch& L, const double* T, const double* Pw,

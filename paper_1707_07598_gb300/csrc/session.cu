@@ -1139,10 +1139,14 @@ extern "C" int msfv_setup(const msfv_desc_t* desc, void* stream, msfv_session_t*
       if (ce == cudaSuccess) ce = upload(const_cast<double*>(s->src_F.e_sign), fl_sign, st);
     }
   }
+  // MSFV_OVER_GLOBAL=1 at msfv_setup: the global-memory box kernels even where the
+  // shared-memory ones fit (for testing)
+  const char* ovg = getenv("MSFV_OVER_GLOBAL");
   for (int k = 1; k < d && s->ov_w && ce == cudaSuccess; ++k) {
     OvHost& H = s->ov[k];
     OvLaunch& L = H.L;
-    ce = upload(const_cast<OvDesc*>(L.ents), H.h_ents, st);
+    ce = over_configure(H, ovg && atoi(ovg) > 0);
+    if (ce == cudaSuccess) ce = upload(const_cast<OvDesc*>(L.ents), H.h_ents, st);
     if (ce == cudaSuccess) ce = upload(const_cast<int*>(L.rec_p), H.h_rec_p, st);
     if (ce == cudaSuccess) ce = upload(const_cast<int*>(L.rec_u), H.h_rec_u, st);
     if (ce == cudaSuccess) ce = upload(const_cast<long long*>(H.G.ptr), H.g_ptr, st);
@@ -1709,13 +1713,17 @@ extern "C" int msfv_info(const msfv_session_t* s, int64_t* out, int n_out) {
   }
   int gw = 0;
   for (int k = 1; k <= s->dg.d; ++k) gw |= s->launch[k].gw ? (1 << k) : 0;
-  int64_t v[15] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
+  const OvLaunch& top_ov = s->ov[s->dg.d == 3 ? 2 : 1].L;
+  int64_t v[21] = {s->dg.N, s->dg.Nc, s->Ns, s->Nr,
                    (int64_t)(s->h_ents[1].size() + s->h_ents[2].size() + s->h_ents[3].size()),
                    (int64_t)s->ws_bytes, (int64_t)s->fac_bytes, s->use_nd ? 2 : (s->use_mg ? 1 : 0),
                    it[0], it[1],
                    s->use_mg ? (s->mg.all ? s->mg.ncta : s->mg.group) : 0,
-                   s->recompute ? 1 : 0, gw, s->src_nslots, s->src_nvals};
-  for (int i = 0; i < n_out && i < 15; ++i) out[i] = v[i];
+                   s->recompute ? 1 : 0, gw, s->src_nslots, s->src_nvals, s->ov_w,
+                   (int64_t)(s->ov[1].h_ents.size() + s->ov[2].h_ents.size()),
+                   (int64_t)s->ov[1].flops, (int64_t)s->ov[2].flops,
+                   s->ov_w ? top_ov.smem : 0, s->ov_w ? top_ov.grid[0] : 0};
+  for (int i = 0; i < n_out && i < 21; ++i) out[i] = v[i];
   return MSFV_OK;
 }
 

@@ -301,11 +301,13 @@ class Session:
 
     # -- introspection ----------------------------------------------------------------
     def info(self) -> dict:
-        out = (ctypes.c_int64 * 15)()
-        self._check(self._lib.msfv_info(self._h, out, 15))
+        out = (ctypes.c_int64 * 21)()
+        self._check(self._lib.msfv_info(self._h, out, 21))
         keys = ["N", "Nc", "Ns", "Nr", "n_local_problems", "workspace_bytes", "factor_bytes",
                 "coarse_solver", "coarse_iters", "coarse_iters_T", "coarse_group_ctas",
-                "recompute", "global_window_mask", "source_slots", "source_values"]
+                "recompute", "global_window_mask", "source_slots", "source_values",
+                "oversample", "oversampled_boxes", "oversampled_edge_flops",
+                "oversampled_face_flops", "oversampled_smem_bytes", "oversampled_grid"]
         return dict(zip(keys, list(out)))
 
     def check(self):

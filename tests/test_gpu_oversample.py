@@ -7,9 +7,11 @@ cells kept).  Bar: 1e-9 relative error in the 2-norm and the max-norm on predict
 data, fields u, misfit, gradient, J v and J^T w.  Cases: 2D and 3D, several dual cells
 per axis with partial dual cells at the boundary, widths from 1 to c - 1 (boxes that
 reach the neighbouring vertex planes' cells and boxes clipped by the mesh), c = 4, 8
-and 16, and a 64^3 case with c = 8.  Also: the gradient is bitwise repeatable (the
-overlapping boxes' contributions are gathered in a fixed order), a batch graph with
-oversampled instances gives the plain path's bits, and invalid widths are rejected."""
+and 16, and a 64^3 case with c = 8; the shared-memory box kernels and the global-memory
+ones (boxes too large for shared memory, or forced).  Also: the gradient is bitwise
+repeatable (the overlapping boxes' contributions are gathered in a fixed order), a batch
+graph with oversampled instances gives the plain path's bits, and invalid widths are
+rejected."""
 import numpy as np
 import pytest
 
@@ -49,6 +51,8 @@ CASES = [
     ((24, 24, 16), 8, 7, 2, 20),
     ((16, 16, 12), 4, 3, 2, 12),
     ((32, 32, 32), 16, 3, 2, 24),
+    # face boxes too large for shared memory (global-memory kernels), edge boxes in it
+    ((32, 32, 32), 16, 5, 2, 24),
 ]
 
 
@@ -75,6 +79,29 @@ def test_oversampled_forward_gradient_jvec_jtvec_match_oracle(dev, n, c, w, ns, 
     jtw = s.jtvec(torch.from_numpy(wt).to(dev)).cpu().numpy()
     assert rel(jv, orc.jvec(st, v)) < TOL
     assert rel(jtw, orc.jtvec(st, wt)) < TOL
+    s.close()
+
+
+@pytest.mark.parametrize("n,c,w", [((24, 16, 16), 8, 2), ((40, 24), 8, 3)])
+def test_oversampled_global_memory_kernels_match_oracle(dev, n, c, w, monkeypatch):
+    """MSFV_OVER_GLOBAL=1 at set-up: the global-memory box kernels where the shared-memory
+    ones would run."""
+    from paper_1707_07598_gb300.msfv import Session
+    monkeypatch.setenv("MSFV_OVER_GLOBAL", "1")
+    prob = W.make_problem(n, c, 2, 16, seed=81, top_layer=False, oversample=w)
+    m = W.gaussian_random_field(n, 0.15, 82)
+    orc = Oracle(prob)
+    st = orc.forward(m)
+    d_obs = st['d'] * 1.01
+    _, g_ref = orc.misfit_gradient(st, d_obs)
+    s = Session(prob)
+    d = s.forward(torch.from_numpy(m).to(dev))
+    _, g = s.adjoint(torch.from_numpy(d_obs).to(dev))
+    v = W.noise_like(prob.N, 1.0, 83)
+    jv = s.jvec(torch.from_numpy(v).to(dev)).cpu().numpy()
+    assert rel(d.cpu().numpy(), st['d']) < TOL
+    assert rel(g.cpu().numpy(), g_ref) < TOL
+    assert rel(jv, orc.jvec(st, v)) < TOL
     s.close()
 
 
