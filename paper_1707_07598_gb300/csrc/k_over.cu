@@ -195,62 +195,99 @@ __device__ __forceinline__ void ov_wait() {
 // sides (nvs x n, right-hand side major).
 struct OvSm {
   double* ring;
-  double* col;
+  double* col;    // the current column as it stands (col[0] the pivot)
+  double* lcol;   // the current column scaled by the pivot's reciprocal (the factor L)
+  double* rpiv;   // reciprocal of the current pivot (one double)
   double* x;
   int RB;
 };
 // doubles of the shared-memory working set of a box (the layout of ov_carve)
 __host__ __device__ __forceinline__ long long ov_smem_doubles(int n, int b, int nvs) {
   const long long B1 = b + 1, RB = b + 1 + OV_LOOK;
-  return RB * B1 + ((B1 + 1) & ~1LL) + (long long)n * nvs;
+  return RB * B1 + 2 * ((B1 + 1) & ~1LL) + 2 + (long long)n * nvs;
 }
 __device__ __forceinline__ OvSm ov_carve(double* base, const OvDesc& e) {
   OvSm s;
-  const long long B1 = e.b + 1;
+  const long long B1 = e.b + 1, B1e = (B1 + 1) & ~1LL;
   s.RB = e.b + 1 + OV_LOOK;
   s.ring = base;
   s.col = base + (long long)s.RB * B1;
-  s.x = s.col + ((B1 + 1) & ~1LL);
+  s.lcol = s.col + B1e;
+  s.rpiv = s.lcol + B1e;
+  s.x = s.rpiv + 2;
   return s;
+}
+
+// (k1, k2), 1 <= k2 <= k1, of entry q of the lower triangle enumerated row by row (row k1
+// holds q in [k1 (k1 - 1) / 2, k1 (k1 + 1) / 2)); the rows of a smaller triangle are a
+// prefix.  The square root is FP32 (exact to the correction below for q < 2^20).
+__device__ __forceinline__ void tri_pair(int q, int* k1, int* k2) {
+  int r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+  if ((r + 1) * (r + 2) / 2 <= q) ++r;
+  if (r * (r + 1) / 2 > q) --r;
+  *k1 = r + 1;
+  *k2 = q - r * (r + 1) / 2 + 1;
 }
 
 // Banded LDL^T with the active columns in a shared-memory ring: column c sits in slot
 // c % RB from its load (OV_LOOK + 1 steps before its first update, by cp.async) until it
-// is final and written to F (global) in place of the assembled column.  F holds the
-// assembled band on entry; status[0] = 1 on a non-positive pivot.  Ends with a block
-// barrier and no copy in flight.
-__device__ void ring_factor(double* F, const OvDesc& e, const OvSm& sm, int* status) {
-  const int tid = threadIdx.x, n = e.n, b = e.b, RB = sm.RB;
+// is final and written to F (global) in place of the assembled column: F[c*(b+1)] = 1 / d_c,
+// F[c*(b+1) + k] = L(c + k, c).  F holds the assembled band on entry.  When fwd is set the
+// forward substitution L y = r of the right-hand sides in sm.x runs inside the same column
+// loop.  status[0] = 1 on a non-positive pivot.  Ends with a block barrier and no copy in
+// flight.
+__device__ void ring_factor(double* F, const OvDesc& e, const OvSm& sm, int* status, bool fwd) {
+  const int tid = threadIdx.x, n = e.n, b = e.b, RB = sm.RB, nvs = e.nvs;
   const long long B1 = b + 1;
   for (long long q = tid; q < (long long)min(n, RB) * B1; q += OV_NT) sm.ring[q] = F[q];
+  if (tid == 0) {
+    const double d0 = F[0];
+    if (!(d0 > 0.0)) status[0] = 1;
+    sm.rpiv[0] = 1.0 / d0;
+  }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     const int kb = min(b, n - 1 - j);
-    double* slot = sm.ring + (long long)(j % RB) * B1;
-    for (int k = tid; k <= kb; k += OV_NT) sm.col[k] = slot[k];
+    const int s0 = j % RB;
+    double* slot = sm.ring + (long long)s0 * B1;
+    const double rd = sm.rpiv[0];
+    for (int k = tid; k <= kb; k += OV_NT) {
+      const double v = slot[k];
+      sm.col[k] = v;
+      sm.lcol[k] = v * rd;
+    }
     __syncthreads();
     // the slot is free: bring in column j + RB
     const int c = j + RB;
     if (c < n)
       for (int k = tid; k < (int)B1; k += OV_NT) ov_cp8(slot + k, F + (long long)c * B1 + k);
     ov_commit();
-    const double dj = sm.col[0];
-    if (tid == 0 && !(dj > 0.0)) status[0] = 1;
-    const double rd = 1.0 / dj;
-    // rank-1 update of the trailing triangle: warp w takes the columns k2 = 1 + w, 5 + w,
-    // ...; its lanes run down the rows k1 >= k2 of that column (consecutive addresses)
-    {
-      const int wid = tid >> 5, lane = tid & 31, s0 = j % RB;
-      for (int k2 = 1 + wid; k2 <= kb; k2 += OV_NT / 32) {
-        int sl = s0 + k2;
-        if (sl >= RB) sl -= RB;
-        double* cp = sm.ring + (long long)sl * B1 - k2;   // entry (j + k1, j + k2) at cp[k1]
-        const double l2 = sm.col[k2] * rd;
-        for (int k1 = k2 + lane; k1 <= kb; k1 += 32) cp[k1] = fma(-l2, sm.col[k1], cp[k1]);
+    // rank-1 update of the trailing triangle, entries packed 32 to a warp instruction;
+    // entry q = 0 is the next pivot, whose reciprocal thread 0 prepares
+    const int ntri = kb * (kb + 1) / 2;
+    for (int q = tid; q < ntri; q += OV_NT) {
+      int k1, k2;
+      tri_pair(q, &k1, &k2);
+      int sl = s0 + k2;
+      if (sl >= RB) sl -= RB;
+      double* f = sm.ring + (long long)sl * B1 + (k1 - k2);
+      const double v = fma(-sm.lcol[k2], sm.col[k1], *f);
+      *f = v;
+      if (q == 0) {
+        if (!(v > 0.0)) status[0] = 1;
+        sm.rpiv[0] = 1.0 / v;
+      }
+    }
+    if (fwd) {
+      const long long nk = (long long)nvs * kb;
+      for (long long q = tid; q < nk; q += OV_NT) {
+        const int r = (int)(q / kb), k = (int)(q - (long long)r * kb) + 1;
+        double* xr = sm.x + (long long)r * n;
+        xr[j + k] = fma(-sm.lcol[k], xr[j], xr[j + k]);
       }
     }
     double* Fj = F + (long long)j * B1;
-    for (int k = tid; k <= kb; k += OV_NT) Fj[k] = k ? sm.col[k] * rd : dj;
+    for (int k = tid; k <= kb; k += OV_NT) Fj[k] = k ? sm.lcol[k] : rd;
     // the column the next step's update reaches furthest was requested OV_LOOK + 1
     // steps ago
     ov_wait<OV_LOOK>();
@@ -260,15 +297,19 @@ __device__ void ring_factor(double* F, const OvDesc& e, const OvSm& sm, int* sta
   __syncthreads();
 }
 
-// L D L^T x = x for the nvs right-hand sides in shared memory, the factor read from F
-// (global) in chunks of C columns staged through the two halves of the ring (every
-// thread copies, one warp per right-hand side solves).  Ends with a block barrier.
-__device__ void staged_solve(const double* F, const OvDesc& e, const OvSm& sm) {
+// L D L^T x = x for the nvs right-hand sides in shared memory, the factor (the layout
+// ring_factor writes: reciprocal pivots) read from F in chunks of C columns staged
+// through the two halves of the ring by every thread; warp 0 solves all right-hand
+// sides at once, 32 / nvs lanes each.  fwd_done: the forward substitution already ran
+// (inside ring_factor).  Ends with a block barrier.
+__device__ void staged_solve(const double* F, const OvDesc& e, const OvSm& sm, bool fwd_done) {
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const int n = e.n, b = e.b;
+  const int n = e.n, b = e.b, nvs = e.nvs;
   const long long B1 = b + 1;
   const int C = max(1, sm.RB / 2);
   const int nch = (n + C - 1) / C;
+  const int Lg = 32 / nvs;                // lanes per right-hand side (nvs = 1, 2 or 4)
+  const int r = lane / Lg, t = lane - (lane / Lg) * Lg;
   // chunk m of a sweep: columns [j0, j1), ascending (down = false) or descending
   auto bounds = [&](int m, bool down, int* j0, int* j1) {
     if (!down) {
@@ -287,8 +328,12 @@ __device__ void staged_solve(const double* F, const OvDesc& e, const OvSm& sm) {
     for (long long q = tid; q < (long long)(j1 - j0) * B1; q += OV_NT) ov_cp8(dst + q, src + q);
     ov_commit();
   };
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = fwd_done ? 1 : 0; pass < 2; ++pass) {
     const bool down = pass == 1;
+    if (down) {   // D^{-1}: the stored reciprocal pivots
+      for (int q = tid; q < n * nvs; q += OV_NT) sm.x[q] *= F[(long long)(q % n) * B1];
+      __syncthreads();
+    }
     load(0, down);
     for (int m = 0; m < nch; ++m) {
       if (m + 1 < nch) {
@@ -301,14 +346,14 @@ __device__ void staged_solve(const double* F, const OvDesc& e, const OvSm& sm) {
       int j0, j1;
       bounds(m, down, &j0, &j1);
       const double* Fs = sm.ring + (long long)(m & 1) * C * B1;
-      if (wid < e.nvs) {
-        double* x = sm.x + (long long)wid * n;
+      if (wid == 0 && r < nvs) {
+        double* x = sm.x + (long long)r * n;
         if (!down) {
           for (int j = j0; j < j1; ++j) {
             const double xj = x[j];
             const int kb = min(b, n - 1 - j);
             const double* Fj = Fs + (long long)(j - j0) * B1;
-            for (int k = 1 + lane; k <= kb; k += 32) x[j + k] = fma(-Fj[k], xj, x[j + k]);
+            for (int k = 1 + t; k <= kb; k += Lg) x[j + k] = fma(-Fj[k], xj, x[j + k]);
             __syncwarp();
           }
         } else {
@@ -316,18 +361,13 @@ __device__ void staged_solve(const double* F, const OvDesc& e, const OvSm& sm) {
             const int kb = min(b, n - 1 - j);
             const double* Fj = Fs + (long long)(j - j0) * B1;
             double acc = 0.0;
-            for (int k = 1 + lane; k <= kb; k += 32) acc = fma(Fj[k], x[j + k], acc);
-            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) x[j] -= acc;
+            for (int k = 1 + t; k <= kb; k += Lg) acc = fma(Fj[k], x[j + k], acc);
+            for (int o = Lg >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (t == 0) x[j] -= acc;
             __syncwarp();
           }
         }
       }
-      __syncthreads();
-    }
-    if (!down) {
-      for (int q = tid; q < n * e.nvs; q += OV_NT)
-        sm.x[q] = sm.x[q] / F[(long long)(q % n) * B1];
       __syncthreads();
     }
   }
@@ -396,8 +436,8 @@ __global__ void __launch_bounds__(OV_NT) k_over_fwd(DevGeom g, OvLaunch L,
     }
     __syncthreads();
     if constexpr (SM) {
-      ring_factor(F, e, sm, status);
-      staged_solve(F, e, sm);
+      ring_factor(F, e, sm, status, true);
+      staged_solve(F, e, sm, true);
       for (int q = tid; q < e.n * e.nvs; q += OV_NT) L.sol[e.sol + q] = x[q];
     } else {
       band_factor(F, e.n, e.b, colg, status);
@@ -492,7 +532,7 @@ __global__ void __launch_bounds__(OV_NT) k_over_adj(DevGeom g, OvLaunch L,
     }
     __syncthreads();
     if constexpr (SM)
-      staged_solve(F, e, sm);
+      staged_solve(F, e, sm, false);
     else
       box_solve(e, F, mu);
     // private contributions: the gradient of every box face, and the seeds of the
@@ -604,7 +644,7 @@ __global__ void __launch_bounds__(OV_NT) k_over_tan(DevGeom g, OvLaunch L,
     }
     __syncthreads();
     if constexpr (SM)
-      staged_solve(F, e, sm);
+      staged_solve(F, e, sm, false);
     else
       box_solve(e, F, x);
     for (int p = tid; p < e.n; p += OV_NT) {
@@ -695,7 +735,8 @@ std::string over_plan(const DevGeom& g, const std::vector<EntDesc>& ents,
     e.b = (int)b;
     e.slots = pe.slots;
     e.nvs = __builtin_popcount((unsigned)pe.slots);
-    if (e.nvs < 1 || e.nvs > 4) return "an oversampled entity without 1 to 4 corners";
+    if (e.nvs != 1 && e.nvs != 2 && e.nvs != 4)
+      return "internal: an oversampled entity without 1, 2 or 4 corners";
     e.fac = fac;
     fac += (long long)e.n * (e.b + 1);
     e.sol = e.wrk = sol;
