@@ -54,6 +54,7 @@ def _desc(**kw):
     d.hbm_budget_bytes = kw.get("budget", 0)
     d.source_bases = kw.get("sb", 0)
     d.discretization = kw.get("disc", 0)
+    d.oversample = kw.get("ov", 0)
     d._keep = (pos, neg, rec, r)
     return d
 
@@ -77,6 +78,10 @@ def _desc(**kw):
     (dict(disc=1, sb=1), "not available for the nodal"),
     (dict(disc=1, fm=2), "stored local factors"),
     (dict(disc=1, budget=1000), "stored local factors"),
+    (dict(ov=-1), "oversample must be >= 0"),
+    (dict(ov=4), "oversample must be <= coarsen - 1"),
+    (dict(ov=1, sb=1), "source bases are not defined with oversampling"),
+    (dict(ov=1, disc=1), "oversampling is not available for the nodal"),
 ])
 def test_setup_rejects_bad_descriptors_on_the_host(lib, kw, frag):
     d = _desc(**kw)
@@ -114,6 +119,7 @@ def _desc3(n, c, pos, neg, rec, **kw):
     d.hbm_budget_bytes = kw.get("budget", 1000)
     d.source_bases = kw.get("sb", 0)
     d.discretization = kw.get("disc", 0)
+    d.oversample = kw.get("ov", 0)
     d._keep = (pos, neg, rec)
     return d
 
@@ -146,3 +152,40 @@ def test_host_tables_of_source_bases_and_nodal_variant_build_on_the_host(lib):
     d = _desc3(n, c, [17 ** 3], [0], [1], disc=1)
     assert lib.msfv_setup(ctypes.byref(d), None, ctypes.byref(h)) == 1
     assert "out of range" in lib.msfv_last_error(None).decode()
+
+
+@pytest.mark.parametrize("dim,n,c,w", [(3, (16, 16, 16), 4, 1), (3, (16, 16, 16), 4, 3),
+                                       (3, (24, 16, 8), 8, 7), (3, (32, 32, 32), 16, 5),
+                                       (2, (48, 40, 1), 8, 3), (2, (20, 15, 1), 5, 4)])
+def test_oversampling_plan_builds_on_the_host(lib, dim, n, c, w):
+    """Setup plans the oversampled edge and face boxes (widened boxes, offsets, receivers
+    re-indexed in the box, the fixed-order gathers of the face gradient and of the faces'
+    seeds of the edges, with their range checks) before it checks the budget: with a tiny
+    budget the whole plan runs on the CPU and setup stops with MSFV_ERR_OOM.  A plan that
+    failed would return MSFV_ERR_ARG with its reason."""
+    N = int(np.prod(n[:dim]))
+    rng = np.random.default_rng(7)
+    cells = rng.choice(N, 14, replace=False)
+    d = M._Desc()
+    d.dim = dim
+    for a in range(3):
+        d.n[a] = n[a]
+    d.coarsen = c
+    pos, neg, rec = (np.asarray(cells[:3], dtype=np.int64), np.asarray(cells[3:6], dtype=np.int64),
+                     np.asarray(cells[6:], dtype=np.int64))
+    d.n_src = 3
+    d.src_pos = pos.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.src_neg = neg.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.src_amp = None
+    d.n_rec = len(rec)
+    d.rec_cell = rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.factor_mode = 1
+    d.hbm_budget_bytes = 1000
+    d.source_bases = 0
+    d.discretization = 0
+    d.oversample = w
+    h = ctypes.c_void_p()
+    rc = lib.msfv_setup(ctypes.byref(d), None, ctypes.byref(h))
+    msg = lib.msfv_last_error(None).decode()
+    assert rc == 2 and not h.value, msg
+    assert "exceeds hbm_budget_bytes" in msg
