@@ -30,6 +30,7 @@
 // fixed order (deterministic, no atomics).
 #include <algorithm>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -885,7 +886,8 @@ cudaError_t ov_allow_smem(K kern, long long bytes) {
 
 cudaError_t over_configure(OvHost& H, bool force_global) {
   static std::mutex mu;
-  static long long allowed = 0;   // dynamic shared memory the kernels are set up for
+  static std::map<int, long long> allowed;   // per device: dynamic shared memory the
+                                             // kernels are set up for
   OvLaunch& L = H.L;
   long long need = 0;
   for (const OvDesc& e : H.h_ents)
@@ -900,12 +902,12 @@ cudaError_t over_configure(OvHost& H, bool force_global) {
   L.smem = use_sm ? need : 0;
   if (use_sm) {
     std::lock_guard<std::mutex> lk(mu);
-    if (need > allowed) {
+    if (need > allowed[dev]) {
       err = ov_allow_smem(k_over_fwd<true>, need);
       if (err == cudaSuccess) err = ov_allow_smem(k_over_adj<true>, need);
       if (err == cudaSuccess) err = ov_allow_smem(k_over_tan<true>, need);
       if (err != cudaSuccess) return err;
-      allowed = need;
+      allowed[dev] = need;
     }
     L.grid[0] = ov_grid(k_over_fwd<true>, L.smem, L.n_ents, dev, nsm);
     L.grid[1] = ov_grid(k_over_adj<true>, L.smem, L.n_ents, dev, nsm);
