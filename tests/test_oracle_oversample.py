@@ -24,7 +24,7 @@ from oracle.msfv_oracle import Oracle, fine_operator, transmissibility
 from paper_1707_07598_gb300 import workloads as W
 
 CASES = [((12, 12), 4, 1), ((12, 8), 4, 2), ((16, 12), 4, 5), ((8, 8, 8), 4, 1),
-         ((12, 8, 8), 4, 2)]
+         ((12, 8, 8), 4, 2), ((8, 6), 2, 1), ((9, 9, 6), 3, 2), ((10, 10, 5), 5, 3)]
 
 
 def _setup(n, c, w, seed=5, ns=2, nr=6):
