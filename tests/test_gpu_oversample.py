@@ -184,7 +184,8 @@ def test_oversampled_bench_configuration_properties(dev):
     prob.oversample = 2
     s = Session(prob)
     d_over = s.forward(m1)
-    assert rel(d_over.cpu().numpy(), d_plain.cpu().numpy()) < 1e-10
+    # the same basis up to rounding; the coarse solve amplifies rounding by its condition
+    assert rel(d_over.cpu().numpy(), d_plain.cpu().numpy()) < 1e-8
     m = torch.from_numpy(m_np).to(dev)
     d = s.forward(m)
     d_obs = d * 1.01
