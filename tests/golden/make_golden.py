@@ -1,5 +1,6 @@
 """Writes oracle_tiny.json: oracle outputs on tiny seeded cases (calls only oracle/):
-the cell-centred path, with source bases, and the nodal Galerkin variant.
+the cell-centred path, with source bases, with oversampled edges and faces, and the
+nodal Galerkin variant.
 
 Run from the repository root:  python tests/golden/make_golden.py
 """
@@ -21,13 +22,16 @@ CASES = [dict(n=[12, 8], c=4, ns=2, nr=6, seed=3, corr=0.3),
          dict(n=[12, 8], c=4, ns=2, nr=6, seed=5, corr=0.3, sb=True),
          dict(n=[8, 8, 8], c=4, ns=2, nr=7, seed=6, corr=0.3, sb=True),
          dict(n=[12, 8], c=4, ns=2, nr=6, seed=7, corr=0.3, nodal=True),
-         dict(n=[6, 6, 6], c=3, ns=2, nr=5, seed=8, corr=0.3, nodal=True)]
+         dict(n=[6, 6, 6], c=3, ns=2, nr=5, seed=8, corr=0.3, nodal=True),
+         dict(n=[12, 8], c=4, ns=2, nr=6, seed=9, corr=0.3, ov=2),
+         dict(n=[8, 8, 8], c=4, ns=2, nr=7, seed=10, corr=0.3, ov=1)]
 
 out = []
 for case in CASES:
     prob = W.make_problem(tuple(case['n']), case['c'], case['ns'], case['nr'],
                           seed=case['seed'], top_layer=False,
-                          source_bases=case.get('sb', False), nodal=case.get('nodal', False))
+                          source_bases=case.get('sb', False), nodal=case.get('nodal', False),
+                          oversample=case.get('ov', 0))
     m = W.gaussian_random_field(prob.n, case['corr'], case['seed'] + 2)
     o = NodalOracle(prob) if case.get('nodal') else Oracle(prob)
     st = o.forward(m)

@@ -363,11 +363,13 @@ def test_golden_oracle_outputs_are_reproduced():
     with open(os.path.join(GOLDEN, "oracle_tiny.json")) as f:
         gold = json.load(f)
     from oracle.galerkin_oracle import NodalOracle
-    assert len(gold) >= 6 and any(c.get('sb') for c in gold) and any(c.get('nodal') for c in gold)
+    assert len(gold) >= 8 and any(c.get('sb') for c in gold) and any(c.get('nodal') for c in gold)
+    assert any(c.get('ov') for c in gold)
     for case in gold:
         prob = W.make_problem(tuple(case['n']), case['c'], case['ns'], case['nr'],
                               seed=case['seed'], top_layer=False,
-                              source_bases=case.get('sb', False), nodal=case.get('nodal', False))
+                              source_bases=case.get('sb', False), nodal=case.get('nodal', False),
+                              oversample=case.get('ov', 0))
         m = W.gaussian_random_field(prob.n, case['corr'], case['seed'] + 2)
         o = NodalOracle(prob) if case.get('nodal') else Oracle(prob)
         st = o.forward(m)
