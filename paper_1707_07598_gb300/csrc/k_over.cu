@@ -673,21 +673,42 @@ __global__ void k_over_gather(OvGather G, const double* __restrict__ src, double
   }
 }
 
-// pairs (target, source) sorted by target, then source: rows of a gather
-void build_rows(std::vector<std::pair<long long, long long>>& pr, std::vector<long long>& ptr,
+// Rows of a gather: gen(emit) calls emit(target, source) for every contribution, targets
+// in [0, nkeys), sources increasing.  One row per target that occurs, in target order,
+// its sources in the order generated (a stable counting sort: gen runs twice, once to
+// count and once to fill, linear in the contributions).  Returns false when a target is
+// out of range or the sources do not increase.
+template <class Gen>
+bool build_rows(Gen&& gen, long long nkeys, std::vector<long long>& ptr,
                 std::vector<long long>& idx, std::vector<long long>& dst) {
-  std::sort(pr.begin(), pr.end());
   ptr.clear();
   idx.clear();
   dst.clear();
-  for (size_t k = 0; k < pr.size(); ++k) {
-    if (k == 0 || pr[k].first != pr[k - 1].first) {
-      dst.push_back(pr[k].first);
-      ptr.push_back((long long)k);
+  std::vector<int> row((size_t)std::max(1LL, nkeys), 0);   // count, then row number
+  bool ok = true;
+  long long prev = -1, total = 0;
+  gen([&](long long t, long long src) {
+    if (t < 0 || t >= nkeys || src <= prev) {
+      ok = false;
+      return;
     }
-    idx.push_back(pr[k].second);
+    prev = src;
+    ++total;
+    ++row[(size_t)t];
+  });
+  if (!ok) return false;
+  ptr.push_back(0);
+  for (long long key = 0; key < nkeys; ++key) {
+    const int c = row[(size_t)key];
+    if (!c) continue;
+    row[(size_t)key] = (int)dst.size();
+    dst.push_back(key);
+    ptr.push_back(ptr.back() + c);
   }
-  ptr.push_back((long long)pr.size());
+  std::vector<long long> cur(ptr.begin(), ptr.end() - 1);
+  idx.resize((size_t)total);
+  gen([&](long long t, long long src) { idx[(size_t)cur[(size_t)row[(size_t)t]]++] = src; });
+  return true;
 }
 
 }  // namespace
@@ -778,23 +799,25 @@ std::string over_plan(const DevGeom& g, const std::vector<EntDesc>& ents,
   H.n_sprv = sprv;
   H.n_seed = seed;
   // the face-gradient gather: every box face of every box
-  std::vector<std::pair<long long, long long>> pr;
-  for (const OvDesc& e : H.h_ents) {
-    if (e.nvs < 2) continue;   // no derivative: its slots stay zero and are not gathered
-    for (int p = 0; p < e.n; ++p) {
-      int xc[3];
-      box_coords(e, p, xc);
-      const long long xg = cell_of(g, xc);
-      for (int a = 0; a < d; ++a)
-        for (int dir = -1; dir <= 1; dir += 2) {
-          const int kind = face_kind(g, e, xc, a, dir);
-          if (!kind || (kind == 1 && dir < 0)) continue;
-          const long long lowr = dir > 0 ? xg : xg - g.st[a];
-          pr.push_back({(long long)a * g.N + lowr, e.prv + (long long)p * 6 + a * 2 + (dir > 0)});
-        }
+  auto faces = [&](auto&& emit) {
+    for (const OvDesc& e : H.h_ents) {
+      if (e.nvs < 2) continue;   // no derivative: its slots stay zero and are not gathered
+      for (int p = 0; p < e.n; ++p) {
+        int xc[3];
+        box_coords(e, p, xc);
+        const long long xg = cell_of(g, xc);
+        for (int a = 0; a < d; ++a)
+          for (int dir = -1; dir <= 1; dir += 2) {
+            const int kind = face_kind(g, e, xc, a, dir);
+            if (!kind || (kind == 1 && dir < 0)) continue;
+            const long long lowr = dir > 0 ? xg : xg - g.st[a];
+            emit((long long)a * g.N + lowr, e.prv + (long long)p * 6 + a * 2 + (dir > 0));
+          }
+      }
     }
-  }
-  build_rows(pr, H.g_ptr, H.g_idx, H.g_dst);
+  };
+  if (!build_rows(faces, (long long)d * g.N, H.g_ptr, H.g_idx, H.g_dst))
+    return "internal: face-gradient gather out of order or out of range";
   for (long long q : H.g_idx)
     if (q < 0 || q >= H.n_prv) return "internal: face-gradient gather out of range";
   for (long long q : H.g_dst)
@@ -813,34 +836,34 @@ std::string over_plan(const DevGeom& g, const std::vector<EntDesc>& ents,
         p_of[xg] = p;
       }
     }
-    pr.clear();
-    for (const OvDesc& e : H.h_ents) {
-      if (e.nvs < 2) continue;
-      for (int p = 0; p < e.n; ++p) {
-        int xc[3];
-        box_coords(e, p, xc);
-        for (int a = 0; a < d; ++a)
-          for (int dir = -1; dir <= 1; dir += 2) {
-            if (face_kind(g, e, xc, a, dir) != 2) continue;
-            int yc[3] = {xc[0], xc[1], xc[2]};
-            yc[a] += dir;
-            const long long yp = project(g, e, yc);
-            const int ie = ent_of[yp];
-            if (ie < 0) continue;   // a vertex: fixed values, no seed
-            const OvDesc& E2 = lower->h_ents[ie];
-            if (E2.nvs < 2) continue;
-            for (int i = 0; i < e.nvs; ++i) {
-              const int sp = map_slot(nth_slot_of(e.slots, i), a, dir);
-              if (sp < 0 || !((E2.slots >> sp) & 1)) continue;
-              const long long tgt =
-                  E2.seed + (long long)index_of_slot(E2.slots, sp) * E2.n + p_of[yp];
-              const long long src = e.sprv + ((long long)p * 6 + a * 2 + (dir > 0)) * e.nvs + i;
-              pr.push_back({tgt, src});
+    auto seeds = [&](auto&& emit) {
+      for (const OvDesc& e : H.h_ents) {
+        if (e.nvs < 2) continue;
+        for (int p = 0; p < e.n; ++p) {
+          int xc[3];
+          box_coords(e, p, xc);
+          for (int a = 0; a < d; ++a)
+            for (int dir = -1; dir <= 1; dir += 2) {
+              if (face_kind(g, e, xc, a, dir) != 2) continue;
+              int yc[3] = {xc[0], xc[1], xc[2]};
+              yc[a] += dir;
+              const long long yp = project(g, e, yc);
+              const int ie = ent_of[yp];
+              if (ie < 0) continue;   // a vertex: fixed values, no seed
+              const OvDesc& E2 = lower->h_ents[ie];
+              if (E2.nvs < 2) continue;
+              for (int i = 0; i < e.nvs; ++i) {
+                const int sp = map_slot(nth_slot_of(e.slots, i), a, dir);
+                if (sp < 0 || !((E2.slots >> sp) & 1)) continue;
+                emit(E2.seed + (long long)index_of_slot(E2.slots, sp) * E2.n + p_of[yp],
+                     e.sprv + ((long long)p * 6 + a * 2 + (dir > 0)) * e.nvs + i);
+              }
             }
-          }
+        }
       }
-    }
-    build_rows(pr, H.s_ptr, H.s_idx, H.s_dst);
+    };
+    if (!build_rows(seeds, lower->n_seed, H.s_ptr, H.s_idx, H.s_dst))
+      return "internal: seed gather out of order or out of range";
     for (long long q : H.s_idx)
       if (q < 0 || q >= H.n_sprv) return "internal: seed gather out of range";
     for (long long q : H.s_dst)
