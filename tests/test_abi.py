@@ -156,7 +156,8 @@ def test_host_tables_of_source_bases_and_nodal_variant_build_on_the_host(lib):
 
 @pytest.mark.parametrize("dim,n,c,w", [(3, (16, 16, 16), 4, 1), (3, (16, 16, 16), 4, 3),
                                        (3, (24, 16, 8), 8, 7), (3, (32, 32, 32), 16, 5),
-                                       (2, (48, 40, 1), 8, 3), (2, (20, 15, 1), 5, 4)])
+                                       (2, (48, 40, 1), 8, 3), (2, (20, 15, 1), 5, 4),
+                                       (3, (128, 128, 128), 8, 2)])
 def test_oversampling_plan_builds_on_the_host(lib, dim, n, c, w):
     """Setup plans the oversampled edge and face boxes (widened boxes, offsets, receivers
     re-indexed in the box, the fixed-order gathers of the face gradient and of the faces'
